@@ -1,0 +1,204 @@
+/* libhamlet -- C ABI of the GB300 HAMLET hot path.
+ *
+ * HAMLET (Valade, Hoffman & Libeskind) samples the posterior of the linear
+ * density field and of the true distances of a peculiar-velocity catalogue
+ * with Hamiltonian Monte Carlo.  This library evaluates the potential
+ * Psi = -ln(posterior) (eq. Psi) and its gradient on one GPU and runs the
+ * leapfrog / Metropolis chain, for one or many chains at once.
+ *
+ * Conventions (every entry point):
+ *  - Units: lengths Mpc/h, velocities km/s, H0 = 100 km/s/(Mpc/h).
+ *  - Grid: N^3 nodes at x = (i, j, l) * L/N, periodic, row-major [i][j][l]
+ *    (l fastest).  The whitened field w has one real value per node; the
+ *    density contrast is delta_k = sqrt(P(k)/Delta^3) DFT(w)_k (eq. prior-k
+ *    in whitened form), so the Fourier-mode prior is |w|^2/2.
+ *  - Spectra: [kx][ky][kz] complex, kz = 0..N/2, unnormalised forward DFT
+ *    with e^{-i k.x}.
+ *  - Field arrays are float (HM_FP32) or double (HM_FP64) as the problem's
+ *    precision says; distances, momenta of distances and all energies are
+ *    double.
+ *  - Pointers named *_dev are device pointers on the problem's device
+ *    (caller-owned, contiguous); *_host are host pointers (copied in or out
+ *    before the call returns, caller keeps ownership).
+ *  - Calls are ordered on the given CUDA stream (NULL = legacy default) and
+ *    return without synchronising unless stated.
+ *  - Return value: HM_OK or a negative HM_E* code; hm_last_error() gives a
+ *    text for the calling thread.  No C++ exception crosses this boundary.
+ */
+#ifndef HAMLET_H
+#define HAMLET_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  HM_OK = 0,
+  HM_EINVAL = -1,   /* bad argument: size, NaN, sigma <= 0, unsupported N */
+  HM_ENOMEM = -2,   /* device allocation failed */
+  HM_ECUDA = -3,    /* a CUDA runtime call failed */
+  HM_EDOMAIN = -4,  /* a distance left the prior support: Psi = +inf */
+  HM_ESTATE = -5    /* call order: e.g. no catalogue set yet */
+};
+
+enum { HM_FP32 = 0, HM_FP64 = 1 };
+enum { HM_PRIOR_TABLE = 0, HM_PRIOR_POWER = 1 };
+
+typedef struct hm_problem hm_problem;
+typedef struct hm_state hm_state;
+
+/* Problem description (section "Bayesian posterior PDF and likelihood
+ * function"; grid and mock geometry of section "Mock Catalogue
+ * construction").  All fields are read once by hm_init_problem. */
+typedef struct hm_problem_desc {
+  int32_t N;             /* grid nodes per side, power of two (see hm_supported) */
+  int32_t precision;     /* HM_FP32 (FP32 fields, FP64 energies) or HM_FP64 */
+  double L;              /* box side, Mpc/h */
+  double observer[3];    /* observer position; used when observer_set != 0 */
+  int32_t observer_set;  /* 0: observer at the box centre (L/2, L/2, L/2) */
+  int32_t prior_kind;    /* HM_PRIOR_TABLE or HM_PRIOR_POWER (eq. D) */
+  double omega_m, omega_b, h, n_s, sigma8, T_cmb; /* P(k): Eisenstein-Hu no-wiggle */
+  double f_growth;       /* linear growth rate; <= 0 means omega_m^0.55 */
+  double sigma_nl;       /* non-linear velocity dispersion sigma_NL, km/s (eq. kappa) */
+  /* HM_PRIOR_TABLE: ln pi_D(d) = prior_logdens[floor((d - d0)/bin)], -inf outside */
+  double prior_d0, prior_bin;
+  int32_t prior_nbins;
+  int32_t pad0;
+  const double* prior_logdens_host;
+  /* HM_PRIOR_POWER: ln pi_D(d) = alpha ln d on [dmin, dmax], -inf outside */
+  double prior_alpha, prior_dmin, prior_dmax;
+  int32_t device;        /* CUDA device ordinal */
+  int32_t pad1;
+} hm_problem_desc;
+
+/* Derived constants of a problem (host copy). */
+typedef struct hm_problem_info {
+  int32_t N, precision;
+  int64_t n_points;
+  double L, delta, f_growth, sigma_v, minv_d, pk_amplitude;
+  int64_t grid_bytes;      /* bytes of one real N^3 field */
+  int64_t spectrum_bytes;  /* bytes of one N*N*(N/2+1) complex spectrum */
+} hm_problem_info;
+
+/* One record per chain and trajectory written by hm_run_chain. */
+typedef struct hm_trace {
+  int64_t traj;      /* trajectory counter (Philox counter word 1) */
+  double H_old;      /* Hamiltonian at the start (eq. Hamiltonian) */
+  double H_new;      /* Hamiltonian at the end point */
+  double logu;       /* ln U of the Metropolis test, U in (0, 1] */
+  double psi;        /* Psi of the chain state after the decision */
+  int32_t accept;    /* 1 accepted, 0 rejected */
+  int32_t status;    /* bit 1: a distance left the support; bit 2: H not finite */
+} hm_trace;
+
+/* 1 if grids of side N at this precision are built into the library. */
+int hm_supported(int32_t N, int32_t precision);
+
+/* Create a problem: tabulates P(k) on the grid's |k| values, sigma_v and the
+ * velocity operator i aHf k_j/k^2 sqrt(P/Delta^3) (eq. vel-field with the
+ * colouring of eq. prior-k).  *out is owned by the library; free with
+ * hm_destroy_problem.  Errors: HM_EINVAL, HM_ENOMEM, HM_ECUDA. */
+int hm_init_problem(const hm_problem_desc* desc, hm_problem** out);
+void hm_destroy_problem(hm_problem* p);
+int hm_problem_get_info(const hm_problem* p, hm_problem_info* out);
+
+/* Upload the catalogue (section "Mock Catalogue construction": direction,
+ * distance modulus mu with error sigma_mu, redshift cz with error sigma_cz).
+ * rhat_host: n x 3 unit vectors (row-major), the direction r_i of eq. lvr;
+ * cz_host in km/s (z = cz/c); sigma_cz_host may be NULL (zeros).  Replaces a
+ * previous catalogue.  Errors: HM_EINVAL (n < 0, non-finite value,
+ * sigma_mu <= 0, |rhat| != 1 beyond 1e-6), HM_ENOMEM. */
+int hm_set_catalog(hm_problem* p, int64_t n, const double* rhat_host, const double* mu_host,
+                   const double* sigma_mu_host, const double* cz_host, const double* sigma_cz_host);
+
+/* Psi(w, d) and its gradient (eqs. covfefe:bay, likelihood, lmu, vrobs,
+ * vel-field, lvr, kappa, prior-k, D, Psi).  w_dev: N^3 field; d_dev: n
+ * distances.  Outputs: psi_dev (1 double, device), grad_w_dev (N^3 field),
+ * grad_d_dev (n doubles).  Psi omits additive constants independent of
+ * (w, d).  A distance outside the support gives Psi = +inf, a zero gradient
+ * for that point and return code HM_OK (read the status with
+ * hm_problem_last_status).  Uses a workspace owned by the problem: calls on
+ * one problem must not overlap. */
+int hm_logpost_grad(hm_problem* p, const void* w_dev, const double* d_dev, double* psi_dev,
+                    void* grad_w_dev, double* grad_d_dev, void* stream);
+
+/* Status bits of the last hm_logpost_grad (synchronises the stream). */
+int hm_problem_last_status(hm_problem* p, void* stream, int32_t* status_out);
+
+/* Linear velocity field v_j = IDFT(i aHf k_j/k^2 delta_k) of a whitened
+ * field (eq. vel-field): v_dev receives 3 N^3 grids (x, y, z). */
+int hm_velocity_field(hm_problem* p, const void* w_dev, void* v_dev, void* stream);
+
+/* Unnormalised 3D real-to-complex DFT of `count` contiguous N^3 grids into
+ * `count` spectra, and the inverse complex-to-real DFT (no 1/N^3).  The
+ * inverse reads only the half spectrum and treats it as Hermitian. */
+int hm_fft_r2c(hm_problem* p, const void* in_dev, void* out_dev, int32_t count, void* stream);
+int hm_fft_c2r(hm_problem* p, const void* in_dev, void* out_dev, int32_t count, void* stream);
+
+/* Cell index of each point at distances d_dev: (ix*N + iy)*N + iz of the
+ * lower corner of x = o + d rhat (one IEEE rounding per operation), and the
+ * stable order of the points by that index (perm_dev may be NULL). */
+int hm_cells(hm_problem* p, const double* d_dev, int32_t* cell_dev, int32_t* perm_dev, void* stream);
+
+/* Chains.  A state holds n_chains chains; chain c samples problem
+ * problems[chain_problem[c]] (all problems of one state share N and
+ * precision).  Chain c draws its random numbers with Philox key `seed` and
+ * chain counter word chain_ids[c] (NULL: c).  Positions start at w = 0 and
+ * d = d_init_host[c] (n doubles of that chain's problem, host; required when
+ * n > 0).  Psi and the gradient are evaluated there before the call returns.
+ * Owned by the library; free with hm_destroy_state. */
+int hm_state_create(hm_problem* p, uint64_t seed, const double* d_init_host, hm_state** out);
+/* (as above for one chain of one problem; chain counter word 0) */
+int hm_state_create_batch(hm_problem* const* problems, int32_t n_problems, int32_t n_chains,
+                          const int32_t* chain_problem, const int32_t* chain_ids, uint64_t seed,
+                          const double* const* d_init_host, hm_state** out);
+void hm_destroy_state(hm_state* s);
+
+/* Copy a chain's position (w, d) and/or momenta (p_w, p_d) in or out
+ * (device pointers; NULL leaves that part alone).  After setting positions,
+ * hm_state_refresh recomputes Psi and the gradient there. */
+int hm_state_set(hm_state* s, int32_t chain, const void* w_dev, const double* d_dev,
+                 const void* pw_dev, const double* pd_dev, void* stream);
+int hm_state_get(hm_state* s, int32_t chain, void* w_dev, double* d_dev, void* pw_dev,
+                 double* pd_dev, void* stream);
+int hm_state_get_grad(hm_state* s, int32_t chain, void* gw_dev, double* gd_dev, void* stream);
+int hm_state_refresh(hm_state* s, void* stream);
+/* Per-chain scalars: Psi at the current position, kinetic energy of the
+ * current momenta, trajectory counter (synchronises the stream). */
+int hm_state_scalars(hm_state* s, int32_t chain, double* psi, double* kinetic, int64_t* traj,
+                     void* stream);
+/* Trajectory counter of every chain (for resuming a chain bit-exactly). */
+int hm_state_set_traj(hm_state* s, int32_t chain, int64_t traj);
+
+/* n_steps kick-drift-kick leapfrog steps of every chain from its stored
+ * momenta (no refresh, no Metropolis test): sections "Hamiltonian
+ * trajectories in phase space" and "Integrating the HMC trajectories";
+ * eq. hamilton with the mass matrix of eq. M_ab (identity on w,
+ * (sigma_v/H0)^2 on d).  sample_distances = 0 holds d fixed. */
+int hm_leapfrog(hm_state* s, int32_t n_steps, double eps, int32_t sample_distances, void* stream);
+
+/* n_traj HMC transitions of every chain (section "Construction of HMC
+ * chains"): fresh momenta from Philox, n_leapfrog leapfrog steps of size
+ * eps_host[c] (one per chain), Metropolis test accept iff ln U < H_old -
+ * H_new, restore on rejection.  trace_host receives n_traj * n_chains
+ * records (trajectory-major) and the call synchronises the stream at the
+ * end; trace_host may be NULL.  use_graph != 0 replays one captured CUDA
+ * graph per trajectory. */
+int hm_run_chain(hm_state* s, int32_t n_traj, int32_t n_leapfrog, const double* eps_host,
+                 int32_t sample_distances, int32_t use_graph, hm_trace* trace_host, void* stream);
+
+/* Raw Philox-4x32-10 blocks for counters (q, c1, c2, c3), q = 0..n-1, key
+ * seed: out_dev receives 4 n uint32 words. */
+int hm_philox(uint64_t seed, int64_t n, uint32_t c1, uint32_t c2, uint32_t c3, uint32_t* out_dev,
+              void* stream);
+
+/* Text of the last error on the calling thread ("" if none). */
+const char* hm_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HAMLET_H */

@@ -1,0 +1,910 @@
+// Host side of libhamlet: problem and chain-state objects, the tables of the
+// linear velocity operator, the order of the kernel launches of one gradient
+// evaluation and of one HMC trajectory, and the C ABI of include/hamlet.h.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "hamlet.h"
+#include "hm_internal.h"
+
+using namespace hm;
+
+// ---------------------------------------------------------------------------
+// errors
+// ---------------------------------------------------------------------------
+static thread_local std::string g_err;
+
+static int fail(int code, const std::string& msg) {
+  g_err = msg;
+  return code;
+}
+
+#define HM_CUDA(call)                                                                      \
+  do {                                                                                     \
+    cudaError_t e_ = (call);                                                               \
+    if (e_ != cudaSuccess)                                                                 \
+      return fail(e_ == cudaErrorMemoryAllocation ? HM_ENOMEM : HM_ECUDA,                  \
+                  std::string(#call) + ": " + cudaGetErrorString(e_));                     \
+  } while (0)
+
+#define HM_TRY(call)            \
+  do {                          \
+    int r_ = (call);            \
+    if (r_ != HM_OK) return r_; \
+  } while (0)
+
+// ---------------------------------------------------------------------------
+// device buffers
+// ---------------------------------------------------------------------------
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+  DevBuf() = default;
+  DevBuf(const DevBuf&) = delete;
+  DevBuf& operator=(const DevBuf&) = delete;
+  ~DevBuf() { release(); }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    bytes = 0;
+  }
+  int alloc(size_t n) {
+    release();
+    if (n == 0) n = 16;
+    cudaError_t e = cudaMalloc(&p, n);
+    if (e != cudaSuccess) {
+      p = nullptr;
+      return fail(e == cudaErrorMemoryAllocation ? HM_ENOMEM : HM_ECUDA,
+                  std::string("cudaMalloc: ") + cudaGetErrorString(e));
+    }
+    bytes = n;
+    return HM_OK;
+  }
+  template <typename X> X* as() const { return static_cast<X*>(p); }
+};
+
+// ---------------------------------------------------------------------------
+// linear power spectrum (Eisenstein & Hu 1998 no-wiggle), sigma8 and sigma_v
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr double kPi = 3.14159265358979323846;
+constexpr double kE = 2.71828182845904523536;
+
+struct EH {
+  double om, ob, h, ns, Tcmb;
+  double A = 1.0;
+  // EH98 eqs. 26 and 28-31 (k in h/Mpc)
+  double transfer(double k) const {
+    const double omh2 = om * h * h, obh2 = ob * h * h, fb = ob / om, th = Tcmb / 2.7;
+    const double s = 44.5 * std::log(9.83 / omh2) / std::sqrt(1.0 + 10.0 * std::pow(obh2, 0.75));
+    const double ag = 1.0 - 0.328 * std::log(431.0 * omh2) * fb + 0.38 * std::log(22.3 * omh2) * fb * fb;
+    const double x = 0.43 * k * h * s;
+    const double geff = om * h * (ag + (1.0 - ag) / (1.0 + x * x * x * x));
+    const double q = k * th * th / geff;
+    const double L0 = std::log(2.0 * kE + 1.8 * q);
+    const double C0 = 14.2 + 731.0 / (1.0 + 62.5 * q);
+    return L0 / (L0 + C0 * q * q);
+  }
+  double pk(double k) const {
+    const double T = transfer(k);
+    return A * std::pow(k, ns) * T * T;
+  }
+};
+
+// composite Simpson rule in ln k on [1e-5, 1e2] h/Mpc with 16384 intervals
+template <typename F> double simpson_lnk(F f) {
+  const int n = 16384;
+  const double a = std::log(1e-5), b = std::log(1e2);
+  const double hstep = (b - a) / n;
+  double s = 0.0;
+  for (int i = 0; i <= n; ++i) {
+    const double lk = a + (b - a) * i / n;
+    const double wgt = (i == 0 || i == n) ? 1.0 : ((i & 1) ? 4.0 : 2.0);
+    s += wgt * f(std::exp(lk));
+  }
+  return s * hstep / 3.0;
+}
+
+double tophat(double x) { return 3.0 * (std::sin(x) - x * std::cos(x)) / (x * x * x); }
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// objects
+// ---------------------------------------------------------------------------
+struct hm_problem {
+  hm_problem_desc desc{};
+  int N = 0, prec = 0, device = 0;
+  double L = 0, delta = 0, obs[3] = {0, 0, 0};
+  double f = 0, aHf = 0, sigma_v = 0, minv_d = 0, pkA = 0;
+  size_t rsz = 4;            // bytes of one real
+  long long n3 = 0, nspec = 0;
+  DevBuf tw, amp, prior_logdens;
+  std::vector<double> prior_host;
+  // catalogue
+  long long n = 0;
+  DevBuf rx, ry, rz, mu, smu, zobs, scz;
+  // standalone workspace (one chain)
+  DevBuf S1, S2, V, r, cell, frac, hist, prior_part, pts_part, kin_part, pp, cs, chain_id;
+  long long ws_points = -1;
+};
+
+struct hm_state {
+  int C = 0, N = 0, prec = 0, device = 0;
+  long long n3 = 0, nspec = 0, ntot = 0;
+  int max_pts = 0, pts_blocks = 1;
+  int nparts_f = 1, nparts_p = 1;
+  unsigned long long seed = 0;
+  size_t rsz = 4;
+  hm_problem* p0 = nullptr;       // problem providing the tables (same N, prec)
+  std::vector<hm_problem*> chain_prob;
+  DevBuf w, pw, gw, w0, gw0, S1, S2, V;
+  DevBuf rx, ry, rz, mu, smu, zobs, scz, d, pd, gd, d0, gd0, r, cell, frac;
+  DevBuf prior_part, pts_part, kinb_f, kinb_p, kinl_f, kinl_p;
+  DevBuf pp, cs, chain_id, eps_dev, trace_dev;
+  size_t trace_cap = 0;
+  std::vector<PointParams> pp_host;
+  std::vector<double> eps_host;
+  // captured trajectory graph
+  cudaStream_t gstream = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  int g_L = -1, g_sd = -1;
+  ~hm_state() {
+    if (gexec) cudaGraphExecDestroy(gexec);
+    if (gstream) cudaStreamDestroy(gstream);
+  }
+};
+
+static PointArrays point_arrays(hm_state* s) {
+  PointArrays pa{};
+  pa.rx = s->rx.as<double>();
+  pa.ry = s->ry.as<double>();
+  pa.rz = s->rz.as<double>();
+  pa.mu = s->mu.as<double>();
+  pa.smu = s->smu.as<double>();
+  pa.zobs = s->zobs.as<double>();
+  pa.scz = s->scz.as<double>();
+  pa.d = s->d.as<double>();
+  pa.pd = s->pd.as<double>();
+  pa.gd = s->gd.as<double>();
+  pa.r = s->r.p;
+  pa.cell = s->cell.as<int>();
+  pa.frac = s->frac.p;
+  pa.ntot = s->ntot;
+  return pa;
+}
+
+static PointParams point_params(const hm_problem* p, long long off) {
+  PointParams P{};
+  for (int j = 0; j < 3; ++j) P.obs[j] = p->obs[j];
+  P.delta = p->delta;
+  P.omega_m = p->desc.omega_m;
+  P.h = p->desc.h;
+  P.sigma_nl2 = p->desc.sigma_nl * p->desc.sigma_nl;
+  P.minv_d = p->minv_d;
+  P.N = p->N;
+  P.prior_kind = p->desc.prior_kind;
+  P.prior_nbins = p->desc.prior_nbins;
+  P.prior_d0 = p->desc.prior_d0;
+  P.prior_bin = p->desc.prior_bin;
+  P.prior_logdens = p->prior_logdens.as<double>();
+  P.prior_alpha = p->desc.prior_alpha;
+  P.prior_dmin = p->desc.prior_dmin;
+  P.prior_dmax = p->desc.prior_dmax;
+  P.pt_off = off;
+  P.pt_n = p->n;
+  return P;
+}
+
+// ---------------------------------------------------------------------------
+// one gradient evaluation of C chains (forward operator, likelihood, adjoint)
+// ---------------------------------------------------------------------------
+struct GradArgs {
+  int prec, N, C;
+  long long n3, nspec;
+  const void* tw;
+  const void* amp;
+  void *w, *pw, *gw;
+  void *S1, *S2, *V;
+  PointArrays pa;
+  const PointParams* pp;
+  int max_pts, pts_blocks;
+  double *prior_part, *pts_part, *kinl_f, *kinl_p;
+  ChainScal* cs;
+};
+
+static int grad_eval(const GradArgs& a, int mode, cudaStream_t st) {
+  const size_t rsz = a.prec == HM_FP32 ? 4 : 8;
+  // forward: w -> w_k -> v_k (x, y, z) -> v grids
+  HM_CUDA(launch_plane_r2c(a.prec, a.N, a.w, a.n3, a.S1, a.nspec, a.C, a.tw, st));
+  HM_CUDA(launch_pencil(a.prec, a.N, PM_VEL, a.S1, a.nspec, a.S2, a.nspec, a.C, a.tw, a.amp, st));
+  HM_CUDA(launch_plane_c2r(a.prec, a.N, a.S2, a.nspec, a.V, a.n3, 3 * a.C, a.tw, nullptr, st));
+  // likelihood at the points, residuals and distance gradient
+  HM_CUDA(launch_points_gather(a.prec, a.C, a.max_pts, a.pp, a.pa, a.V, 3 * a.n3, a.pts_part,
+                               a.pts_blocks, a.cs, st));
+  // adjoint: residuals -> CIC scatter into the v grids (reused) -> spectra
+  HM_CUDA(cudaMemsetAsync(a.V, 0, rsz * 3 * (size_t)a.n3 * a.C, st));
+  HM_CUDA(launch_points_scatter(a.prec, a.C, a.max_pts, a.pp, a.pa, a.V, 3 * a.n3, st));
+  if (mode != GM_GRAD)
+    HM_CUDA(launch_points_kick(a.C, a.max_pts, a.pp, a.pa, mode, a.kinl_p, a.pts_blocks, a.cs, nullptr, st));
+  HM_CUDA(launch_plane_r2c(a.prec, a.N, a.V, a.n3, a.S1, a.nspec, 3 * a.C, a.tw, st));
+  HM_CUDA(launch_pencil(a.prec, a.N, PM_ADJ, a.S1, a.nspec, a.S2, a.nspec, a.C, a.tw, a.amp, st));
+  FieldEpi epi{};
+  epi.w = a.w;
+  epi.pw = a.pw;
+  epi.gw = a.gw;
+  epi.prior_part = a.prior_part;
+  epi.kin_part = a.kinl_f;
+  epi.cs = a.cs;
+  epi.grid_stride = a.n3;
+  epi.mode = mode;
+  HM_CUDA(launch_plane_c2r(a.prec, a.N, a.S2, a.nspec, nullptr, 0, a.C, a.tw, &epi, st));
+  return HM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+extern "C" {
+
+const char* hm_last_error(void) { return g_err.c_str(); }
+
+int hm_supported(int32_t N, int32_t precision) { return fft_supported(precision, N) ? 1 : 0; }
+
+static int check_finite(const double* x, long long n, const char* what) {
+  for (long long i = 0; i < n; ++i)
+    if (!std::isfinite(x[i])) return fail(HM_EINVAL, std::string(what) + " has a non-finite value");
+  return HM_OK;
+}
+
+int hm_init_problem(const hm_problem_desc* desc, hm_problem** out) {
+  if (!desc || !out) return fail(HM_EINVAL, "null argument");
+  *out = nullptr;
+  const hm_problem_desc& d = *desc;
+  if (d.precision != HM_FP32 && d.precision != HM_FP64) return fail(HM_EINVAL, "precision must be HM_FP32 or HM_FP64");
+  if (!fft_supported(d.precision, d.N)) return fail(HM_EINVAL, "unsupported grid size N for this precision");
+  if (!(d.L > 0) || !(d.omega_m > 0) || !(d.omega_b > 0) || !(d.h > 0) || !(d.sigma8 > 0) ||
+      !(d.T_cmb > 0) || !std::isfinite(d.n_s) || !(d.sigma_nl >= 0))
+    return fail(HM_EINVAL, "bad cosmology or box parameters");
+  if (d.prior_kind == HM_PRIOR_TABLE) {
+    if (d.prior_nbins <= 0 || !d.prior_logdens_host || !(d.prior_bin > 0))
+      return fail(HM_EINVAL, "table prior needs prior_nbins > 0, prior_bin > 0 and prior_logdens_host");
+  } else if (d.prior_kind == HM_PRIOR_POWER) {
+    if (!(d.prior_dmax > d.prior_dmin)) return fail(HM_EINVAL, "power prior needs dmax > dmin");
+  } else {
+    return fail(HM_EINVAL, "unknown prior_kind");
+  }
+  HM_CUDA(cudaSetDevice(d.device));
+  auto p = std::make_unique<hm_problem>();
+  p->desc = d;
+  p->N = d.N;
+  p->prec = d.precision;
+  p->device = d.device;
+  p->L = d.L;
+  p->delta = d.L / d.N;
+  for (int j = 0; j < 3; ++j) p->obs[j] = d.observer_set ? d.observer[j] : 0.5 * d.L;
+  p->rsz = d.precision == HM_FP32 ? 4 : 8;
+  p->n3 = (long long)d.N * d.N * d.N;
+  p->nspec = (long long)d.N * d.N * (d.N / 2 + 1);
+  // power spectrum normalised to sigma8 (top-hat R = 8 Mpc/h), sigma_v
+  EH eh{d.omega_m, d.omega_b, d.h, d.n_s, d.T_cmb};
+  const double s2 = simpson_lnk([&](double k) {
+                      const double W = tophat(8.0 * k);
+                      return k * k * k * eh.pk(k) * W * W;
+                    }) / (2.0 * kPi * kPi);
+  eh.A = d.sigma8 * d.sigma8 / s2;
+  p->pkA = eh.A;
+  p->f = d.f_growth > 0 ? d.f_growth : std::pow(d.omega_m, 0.55);
+  p->aHf = 1.0 * kH0 * p->f;
+  const double Iv = simpson_lnk([&](double k) { return k * eh.pk(k); });
+  p->sigma_v = std::sqrt((kH0 * p->f) * (kH0 * p->f) * Iv / (6.0 * kPi * kPi));
+  p->minv_d = (p->sigma_v / kH0) * (p->sigma_v / kH0);
+  // amp[n2] = (2 pi/L) aHf sqrt(P/Delta^3) / (k^2 N^3): velocity weights with
+  // the 1/N^3 of the inverse DFT folded in
+  const int N = d.N;
+  const int nmax = 3 * (N / 2) * (N / 2);
+  std::vector<double> ampd(nmax + 1, 0.0);
+  const double kf = 2.0 * kPi / d.L;
+  const double d3 = p->delta * p->delta * p->delta;
+  const double n3d = (double)N * N * N;
+  for (int n2 = 1; n2 <= nmax; ++n2) {
+    const double k = kf * std::sqrt((double)n2);
+    ampd[n2] = kf * p->aHf * std::sqrt(eh.pk(k) / d3) / (k * k * n3d);
+  }
+  std::vector<double> twd(2 * N);
+  for (int e = 0; e < N; ++e) {
+    twd[2 * e] = std::cos(2.0 * kPi * e / N);
+    twd[2 * e + 1] = -std::sin(2.0 * kPi * e / N);
+  }
+  if (p->prec == HM_FP32) {
+    std::vector<float> af(ampd.begin(), ampd.end()), tf(twd.begin(), twd.end());
+    HM_TRY(p->amp.alloc(af.size() * 4));
+    HM_CUDA(cudaMemcpy(p->amp.p, af.data(), af.size() * 4, cudaMemcpyHostToDevice));
+    HM_TRY(p->tw.alloc(tf.size() * 4));
+    HM_CUDA(cudaMemcpy(p->tw.p, tf.data(), tf.size() * 4, cudaMemcpyHostToDevice));
+  } else {
+    HM_TRY(p->amp.alloc(ampd.size() * 8));
+    HM_CUDA(cudaMemcpy(p->amp.p, ampd.data(), ampd.size() * 8, cudaMemcpyHostToDevice));
+    HM_TRY(p->tw.alloc(twd.size() * 8));
+    HM_CUDA(cudaMemcpy(p->tw.p, twd.data(), twd.size() * 8, cudaMemcpyHostToDevice));
+  }
+  if (d.prior_kind == HM_PRIOR_TABLE) {
+    p->prior_host.assign(d.prior_logdens_host, d.prior_logdens_host + d.prior_nbins);
+    HM_TRY(p->prior_logdens.alloc(p->prior_host.size() * 8));
+    HM_CUDA(cudaMemcpy(p->prior_logdens.p, p->prior_host.data(), p->prior_host.size() * 8, cudaMemcpyHostToDevice));
+  }
+  p->desc.prior_logdens_host = nullptr;
+  HM_CUDA(fft_prepare(p->prec, N));
+  *out = p.release();
+  return HM_OK;
+}
+
+void hm_destroy_problem(hm_problem* p) {
+  if (!p) return;
+  cudaSetDevice(p->device);
+  delete p;
+}
+
+int hm_problem_get_info(const hm_problem* p, hm_problem_info* out) {
+  if (!p || !out) return fail(HM_EINVAL, "null argument");
+  out->N = p->N;
+  out->precision = p->prec;
+  out->n_points = p->n;
+  out->L = p->L;
+  out->delta = p->delta;
+  out->f_growth = p->f;
+  out->sigma_v = p->sigma_v;
+  out->minv_d = p->minv_d;
+  out->pk_amplitude = p->pkA;
+  out->grid_bytes = (int64_t)(p->rsz * p->n3);
+  out->spectrum_bytes = (int64_t)(2 * p->rsz * p->nspec);
+  return HM_OK;
+}
+
+static int upload(DevBuf& b, const double* src, long long n) {
+  HM_TRY(b.alloc(sizeof(double) * (size_t)std::max<long long>(n, 1)));
+  if (n > 0) HM_CUDA(cudaMemcpy(b.p, src, sizeof(double) * n, cudaMemcpyHostToDevice));
+  return HM_OK;
+}
+
+int hm_set_catalog(hm_problem* p, int64_t n, const double* rhat, const double* mu, const double* smu,
+                   const double* cz, const double* scz) {
+  if (!p) return fail(HM_EINVAL, "null problem");
+  if (n < 0) return fail(HM_EINVAL, "n < 0");
+  if (n > (1ll << 30)) return fail(HM_EINVAL, "catalogue larger than 2^30 points");
+  if (n > 0 && (!rhat || !mu || !smu || !cz)) return fail(HM_EINVAL, "null catalogue array");
+  HM_TRY(check_finite(rhat, 3 * n, "rhat"));
+  HM_TRY(check_finite(mu, n, "mu"));
+  HM_TRY(check_finite(smu, n, "sigma_mu"));
+  HM_TRY(check_finite(cz, n, "cz"));
+  if (scz) HM_TRY(check_finite(scz, n, "sigma_cz"));
+  std::vector<double> rx(n), ry(n), rz(n), z(n), sc(n, 0.0);
+  for (long long i = 0; i < n; ++i) {
+    if (!(smu[i] > 0)) return fail(HM_EINVAL, "sigma_mu must be > 0");
+    if (scz && !(scz[i] >= 0)) return fail(HM_EINVAL, "sigma_cz must be >= 0");
+    rx[i] = rhat[3 * i];
+    ry[i] = rhat[3 * i + 1];
+    rz[i] = rhat[3 * i + 2];
+    const double nn = rx[i] * rx[i] + ry[i] * ry[i] + rz[i] * rz[i];
+    if (std::fabs(nn - 1.0) > 2e-6) return fail(HM_EINVAL, "rhat must be unit vectors");
+    z[i] = cz[i] / kC;
+    if (scz) sc[i] = scz[i];
+  }
+  HM_CUDA(cudaSetDevice(p->device));
+  HM_TRY(upload(p->rx, rx.data(), n));
+  HM_TRY(upload(p->ry, ry.data(), n));
+  HM_TRY(upload(p->rz, rz.data(), n));
+  HM_TRY(upload(p->mu, mu, n));
+  HM_TRY(upload(p->smu, smu, n));
+  HM_TRY(upload(p->zobs, z.data(), n));
+  HM_TRY(upload(p->scz, sc.data(), n));
+  p->n = n;
+  return HM_OK;
+}
+
+// standalone workspace of a problem (one chain)
+static int ensure_ws(hm_problem* p) {
+  if (p->ws_points == p->n && p->S1.p) return HM_OK;
+  const int N = p->N;
+  HM_TRY(p->S1.alloc(2 * p->rsz * 3 * p->nspec));
+  HM_TRY(p->S2.alloc(2 * p->rsz * 3 * p->nspec));
+  HM_TRY(p->V.alloc(p->rsz * 3 * p->n3));
+  HM_TRY(p->r.alloc(p->rsz * std::max<long long>(p->n, 1)));
+  HM_TRY(p->cell.alloc(4 * std::max<long long>(p->n, 1)));
+  HM_TRY(p->frac.alloc(p->rsz * 3 * std::max<long long>(p->n, 1)));
+  HM_TRY(p->prior_part.alloc(8 * N));
+  const int pb = (int)std::max<long long>(1, (p->n + 255) / 256);
+  HM_TRY(p->pts_part.alloc(8 * pb));
+  HM_TRY(p->kin_part.alloc(8 * std::max(N, pb)));
+  HM_TRY(p->pp.alloc(sizeof(PointParams)));
+  HM_TRY(p->cs.alloc(sizeof(ChainScal)));
+  HM_TRY(p->chain_id.alloc(sizeof(int)));
+  PointParams P = point_params(p, 0);
+  HM_CUDA(cudaMemcpy(p->pp.p, &P, sizeof(P), cudaMemcpyHostToDevice));
+  ChainScal S{};
+  HM_CUDA(cudaMemcpy(p->cs.p, &S, sizeof(S), cudaMemcpyHostToDevice));
+  int z = 0;
+  HM_CUDA(cudaMemcpy(p->chain_id.p, &z, sizeof(z), cudaMemcpyHostToDevice));
+  p->ws_points = p->n;
+  return HM_OK;
+}
+
+int hm_logpost_grad(hm_problem* p, const void* w_dev, const double* d_dev, double* psi_dev,
+                    void* grad_w_dev, double* grad_d_dev, void* stream) {
+  if (!p || !w_dev || !psi_dev || !grad_w_dev) return fail(HM_EINVAL, "null argument");
+  if (p->n > 0 && (!d_dev || !grad_d_dev)) return fail(HM_EINVAL, "null distance argument");
+  if (p->ws_points < 0 && !p->rx.p) return fail(HM_ESTATE, "no catalogue set");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  HM_CUDA(cudaSetDevice(p->device));
+  HM_TRY(ensure_ws(p));
+  PointArrays pa{};
+  pa.rx = p->rx.as<double>();
+  pa.ry = p->ry.as<double>();
+  pa.rz = p->rz.as<double>();
+  pa.mu = p->mu.as<double>();
+  pa.smu = p->smu.as<double>();
+  pa.zobs = p->zobs.as<double>();
+  pa.scz = p->scz.as<double>();
+  pa.d = const_cast<double*>(d_dev);
+  pa.pd = nullptr;
+  pa.gd = grad_d_dev;
+  pa.r = p->r.p;
+  pa.cell = p->cell.as<int>();
+  pa.frac = p->frac.p;
+  pa.ntot = p->n;
+  ChainScal* cs = p->cs.as<ChainScal>();
+  HM_CUDA(cudaMemsetAsync(&cs->status, 0, sizeof(int), st));
+  GradArgs a{};
+  a.prec = p->prec;
+  a.N = p->N;
+  a.C = 1;
+  a.n3 = p->n3;
+  a.nspec = p->nspec;
+  a.tw = p->tw.p;
+  a.amp = p->amp.p;
+  a.w = const_cast<void*>(w_dev);
+  a.pw = nullptr;
+  a.gw = grad_w_dev;
+  a.S1 = p->S1.p;
+  a.S2 = p->S2.p;
+  a.V = p->V.p;
+  a.pa = pa;
+  a.pp = p->pp.as<PointParams>();
+  a.max_pts = (int)p->n;
+  a.pts_blocks = (int)std::max<long long>(1, (p->n + 255) / 256);
+  a.prior_part = p->prior_part.as<double>();
+  a.pts_part = p->pts_part.as<double>();
+  a.kinl_f = p->kin_part.as<double>();
+  a.kinl_p = p->kin_part.as<double>();
+  a.cs = cs;
+  HM_TRY(grad_eval(a, GM_GRAD, st));
+  HM_CUDA(launch_finalize(1, a.prior_part, p->N, a.pts_part, a.pts_blocks, nullptr, 0, nullptr, 0, FIN_PSI,
+                          0ull, p->chain_id.as<int>(), cs, nullptr, st));
+  HM_CUDA(cudaMemcpyAsync(psi_dev, &cs->psi, sizeof(double), cudaMemcpyDeviceToDevice, st));
+  return HM_OK;
+}
+
+int hm_problem_last_status(hm_problem* p, void* stream, int32_t* status_out) {
+  if (!p || !status_out) return fail(HM_EINVAL, "null argument");
+  if (!p->cs.p) {
+    *status_out = 0;
+    return HM_OK;
+  }
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  HM_CUDA(cudaSetDevice(p->device));
+  int v = 0;
+  HM_CUDA(cudaMemcpyAsync(&v, &p->cs.as<ChainScal>()->status, sizeof(int), cudaMemcpyDeviceToHost, st));
+  HM_CUDA(cudaStreamSynchronize(st));
+  *status_out = v;
+  return HM_OK;
+}
+
+int hm_velocity_field(hm_problem* p, const void* w_dev, void* v_dev, void* stream) {
+  if (!p || !w_dev || !v_dev) return fail(HM_EINVAL, "null argument");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  HM_CUDA(cudaSetDevice(p->device));
+  HM_TRY(ensure_ws(p));
+  HM_CUDA(launch_plane_r2c(p->prec, p->N, w_dev, p->n3, p->S1.p, p->nspec, 1, p->tw.p, st));
+  HM_CUDA(launch_pencil(p->prec, p->N, PM_VEL, p->S1.p, p->nspec, p->S2.p, p->nspec, 1, p->tw.p, p->amp.p, st));
+  HM_CUDA(launch_plane_c2r(p->prec, p->N, p->S2.p, p->nspec, v_dev, p->n3, 3, p->tw.p, nullptr, st));
+  return HM_OK;
+}
+
+int hm_fft_r2c(hm_problem* p, const void* in_dev, void* out_dev, int32_t count, void* stream) {
+  if (!p || !in_dev || !out_dev || count < 0) return fail(HM_EINVAL, "bad argument");
+  if (count == 0) return HM_OK;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  HM_CUDA(cudaSetDevice(p->device));
+  HM_CUDA(launch_plane_r2c(p->prec, p->N, in_dev, p->n3, out_dev, p->nspec, count, p->tw.p, st));
+  HM_CUDA(launch_pencil(p->prec, p->N, PM_FWD, out_dev, p->nspec, out_dev, p->nspec, count, p->tw.p, p->amp.p, st));
+  return HM_OK;
+}
+
+int hm_fft_c2r(hm_problem* p, const void* in_dev, void* out_dev, int32_t count, void* stream) {
+  if (!p || !in_dev || !out_dev || count < 0) return fail(HM_EINVAL, "bad argument");
+  if (count == 0) return HM_OK;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  HM_CUDA(cudaSetDevice(p->device));
+  HM_TRY(ensure_ws(p));
+  // x pass into the workspace (input untouched), then planes
+  for (int c = 0; c < count; ++c) {
+    const char* src = static_cast<const char*>(in_dev) + (size_t)c * 2 * p->rsz * p->nspec;
+    char* dst = static_cast<char*>(out_dev) + (size_t)c * p->rsz * p->n3;
+    HM_CUDA(launch_pencil(p->prec, p->N, PM_INV, src, p->nspec, p->S1.p, p->nspec, 1, p->tw.p, p->amp.p, st));
+    HM_CUDA(launch_plane_c2r(p->prec, p->N, p->S1.p, p->nspec, dst, p->n3, 1, p->tw.p, nullptr, st));
+  }
+  return HM_OK;
+}
+
+int hm_cells(hm_problem* p, const double* d_dev, int32_t* cell_dev, int32_t* perm_dev, void* stream) {
+  if (!p || !cell_dev || (p->n > 0 && !d_dev)) return fail(HM_EINVAL, "null argument");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  HM_CUDA(cudaSetDevice(p->device));
+  HM_TRY(ensure_ws(p));
+  PointArrays pa{};
+  pa.rx = p->rx.as<double>();
+  pa.ry = p->ry.as<double>();
+  pa.rz = p->rz.as<double>();
+  pa.ntot = p->n;
+  HM_CUDA(launch_cells(1, (int)p->n, p->pp.as<PointParams>(), d_dev, pa, cell_dev, st));
+  if (perm_dev) {
+    if (!p->hist.p) HM_TRY(p->hist.alloc(4 * (size_t)p->n3));
+    HM_CUDA(launch_cell_sort((int)p->n3, p->n, cell_dev, perm_dev, p->hist.as<int>(), st));
+  }
+  return HM_OK;
+}
+
+int hm_philox(uint64_t seed, int64_t n, uint32_t c1, uint32_t c2, uint32_t c3, uint32_t* out_dev, void* stream) {
+  if (n < 0 || (n > 0 && !out_dev)) return fail(HM_EINVAL, "bad argument");
+  HM_CUDA(launch_philox_raw(seed, n, c1, c2, c3, out_dev, static_cast<cudaStream_t>(stream)));
+  return HM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// chain states
+// ---------------------------------------------------------------------------
+static GradArgs state_args(hm_state* s) {
+  GradArgs a{};
+  a.prec = s->prec;
+  a.N = s->N;
+  a.C = s->C;
+  a.n3 = s->n3;
+  a.nspec = s->nspec;
+  a.tw = s->p0->tw.p;
+  a.amp = s->p0->amp.p;
+  a.w = s->w.p;
+  a.pw = s->pw.p;
+  a.gw = s->gw.p;
+  a.S1 = s->S1.p;
+  a.S2 = s->S2.p;
+  a.V = s->V.p;
+  a.pa = point_arrays(s);
+  a.pp = s->pp.as<PointParams>();
+  a.max_pts = s->max_pts;
+  a.pts_blocks = s->pts_blocks;
+  a.prior_part = s->prior_part.as<double>();
+  a.pts_part = s->pts_part.as<double>();
+  a.kinl_f = s->kinl_f.as<double>();
+  a.kinl_p = s->kinl_p.as<double>();
+  a.cs = s->cs.as<ChainScal>();
+  return a;
+}
+
+static int state_refresh(hm_state* s, cudaStream_t st) {
+  GradArgs a = state_args(s);
+  HM_TRY(grad_eval(a, GM_GRAD, st));
+  HM_CUDA(launch_finalize(s->C, a.prior_part, s->N, a.pts_part, s->pts_blocks, nullptr, 0, nullptr, 0, FIN_PSI,
+                          s->seed, s->chain_id.as<int>(), a.cs, nullptr, st));
+  return HM_OK;
+}
+
+int hm_state_create_batch(hm_problem* const* problems, int32_t n_problems, int32_t n_chains,
+                          const int32_t* chain_problem, const int32_t* chain_ids, uint64_t seed,
+                          const double* const* d_init_host, hm_state** out) {
+  if (!problems || n_problems <= 0 || n_chains <= 0 || !out) return fail(HM_EINVAL, "bad argument");
+  *out = nullptr;
+  hm_problem* p0 = problems[0];
+  for (int i = 0; i < n_problems; ++i) {
+    if (!problems[i]) return fail(HM_EINVAL, "null problem");
+    if (problems[i]->N != p0->N || problems[i]->prec != p0->prec || problems[i]->device != p0->device)
+      return fail(HM_EINVAL, "problems of one state must share N, precision and device");
+    if (std::fabs(problems[i]->L - p0->L) > 0 || problems[i]->aHf != p0->aHf || problems[i]->pkA != p0->pkA)
+      return fail(HM_EINVAL, "problems of one state must share the box and the power spectrum");
+  }
+  auto s = std::make_unique<hm_state>();
+  s->C = n_chains;
+  s->N = p0->N;
+  s->prec = p0->prec;
+  s->device = p0->device;
+  s->n3 = p0->n3;
+  s->nspec = p0->nspec;
+  s->rsz = p0->rsz;
+  s->seed = seed;
+  s->p0 = p0;
+  HM_CUDA(cudaSetDevice(s->device));
+  std::vector<long long> off(n_chains);
+  long long tot = 0;
+  int maxp = 0;
+  for (int c = 0; c < n_chains; ++c) {
+    const int pi = chain_problem ? chain_problem[c] : 0;
+    if (pi < 0 || pi >= n_problems) return fail(HM_EINVAL, "chain_problem out of range");
+    hm_problem* p = problems[pi];
+    if (p->n > 0 && (!d_init_host || !d_init_host[c])) return fail(HM_EINVAL, "d_init_host required");
+    s->chain_prob.push_back(p);
+    off[c] = tot;
+    tot += p->n;
+    maxp = (int)std::max<long long>(maxp, p->n);
+  }
+  s->ntot = tot;
+  s->max_pts = maxp;
+  s->pts_blocks = std::max(1, (maxp + 255) / 256);
+  s->nparts_f = (int)std::min<long long>(256, std::max<long long>(1, (s->n3 / 2 + 255) / 256));
+  s->nparts_p = std::max(1, std::min(64, (maxp / 2 + 255) / 256));
+  const size_t C = n_chains, rs = s->rsz;
+  HM_TRY(s->w.alloc(rs * C * s->n3));
+  HM_TRY(s->pw.alloc(rs * C * s->n3));
+  HM_TRY(s->gw.alloc(rs * C * s->n3));
+  HM_TRY(s->w0.alloc(rs * C * s->n3));
+  HM_TRY(s->gw0.alloc(rs * C * s->n3));
+  HM_TRY(s->V.alloc(rs * 3 * C * s->n3));
+  HM_TRY(s->S1.alloc(2 * rs * 3 * C * s->nspec));
+  HM_TRY(s->S2.alloc(2 * rs * 3 * C * s->nspec));
+  HM_CUDA(cudaMemset(s->w.p, 0, rs * C * s->n3));
+  HM_CUDA(cudaMemset(s->pw.p, 0, rs * C * s->n3));
+  const size_t nt = (size_t)std::max<long long>(tot, 1);
+  DevBuf* dbl[] = {&s->rx, &s->ry, &s->rz, &s->mu, &s->smu, &s->zobs, &s->scz, &s->d, &s->pd, &s->gd, &s->d0, &s->gd0};
+  for (DevBuf* b : dbl) HM_TRY(b->alloc(8 * nt));
+  HM_CUDA(cudaMemset(s->pd.p, 0, 8 * nt));
+  HM_TRY(s->r.alloc(rs * nt));
+  HM_TRY(s->cell.alloc(4 * nt));
+  HM_TRY(s->frac.alloc(rs * 3 * nt));
+  for (int c = 0; c < n_chains; ++c) {
+    hm_problem* p = s->chain_prob[c];
+    const long long n = p->n;
+    if (n == 0) continue;
+    const size_t b = 8 * (size_t)n, o = 8 * (size_t)off[c];
+    HM_CUDA(cudaMemcpy((char*)s->rx.p + o, p->rx.p, b, cudaMemcpyDeviceToDevice));
+    HM_CUDA(cudaMemcpy((char*)s->ry.p + o, p->ry.p, b, cudaMemcpyDeviceToDevice));
+    HM_CUDA(cudaMemcpy((char*)s->rz.p + o, p->rz.p, b, cudaMemcpyDeviceToDevice));
+    HM_CUDA(cudaMemcpy((char*)s->mu.p + o, p->mu.p, b, cudaMemcpyDeviceToDevice));
+    HM_CUDA(cudaMemcpy((char*)s->smu.p + o, p->smu.p, b, cudaMemcpyDeviceToDevice));
+    HM_CUDA(cudaMemcpy((char*)s->zobs.p + o, p->zobs.p, b, cudaMemcpyDeviceToDevice));
+    HM_CUDA(cudaMemcpy((char*)s->scz.p + o, p->scz.p, b, cudaMemcpyDeviceToDevice));
+    HM_TRY(check_finite(d_init_host[c], n, "d_init"));
+    HM_CUDA(cudaMemcpy((char*)s->d.p + o, d_init_host[c], b, cudaMemcpyHostToDevice));
+    s->pp_host.push_back(point_params(p, off[c]));
+  }
+  // point params for chains without points too
+  s->pp_host.clear();
+  for (int c = 0; c < n_chains; ++c) s->pp_host.push_back(point_params(s->chain_prob[c], off[c]));
+  HM_TRY(s->pp.alloc(sizeof(PointParams) * C));
+  HM_CUDA(cudaMemcpy(s->pp.p, s->pp_host.data(), sizeof(PointParams) * C, cudaMemcpyHostToDevice));
+  HM_TRY(s->cs.alloc(sizeof(ChainScal) * C));
+  std::vector<ChainScal> csh(C);
+  for (auto& x : csh) {
+    x = ChainScal{};
+    x.sample_d = 1;
+  }
+  HM_CUDA(cudaMemcpy(s->cs.p, csh.data(), sizeof(ChainScal) * C, cudaMemcpyHostToDevice));
+  std::vector<int> ids(C);
+  for (int c = 0; c < n_chains; ++c) ids[c] = chain_ids ? chain_ids[c] : c;
+  HM_TRY(s->chain_id.alloc(sizeof(int) * C));
+  HM_CUDA(cudaMemcpy(s->chain_id.p, ids.data(), sizeof(int) * C, cudaMemcpyHostToDevice));
+  HM_TRY(s->prior_part.alloc(8 * C * s->N));
+  HM_TRY(s->pts_part.alloc(8 * C * s->pts_blocks));
+  HM_TRY(s->kinb_f.alloc(8 * C * s->nparts_f));
+  HM_TRY(s->kinb_p.alloc(8 * C * s->nparts_p));
+  HM_TRY(s->kinl_f.alloc(8 * C * s->N));
+  HM_TRY(s->kinl_p.alloc(8 * C * s->pts_blocks));
+  HM_CUDA(cudaMemset(s->kinl_p.p, 0, 8 * C * s->pts_blocks));
+  HM_CUDA(cudaMemset(s->kinb_p.p, 0, 8 * C * s->nparts_p));
+  HM_TRY(s->eps_dev.alloc(8 * C));
+  s->eps_host.assign(C, 0.0);
+  HM_TRY(state_refresh(s.get(), nullptr));
+  HM_CUDA(cudaDeviceSynchronize());
+  *out = s.release();
+  return HM_OK;
+}
+
+int hm_state_create(hm_problem* p, uint64_t seed, const double* d_init_host, hm_state** out) {
+  hm_problem* ps[1] = {p};
+  const double* di[1] = {d_init_host};
+  return hm_state_create_batch(ps, 1, 1, nullptr, nullptr, seed, di, out);
+}
+
+void hm_destroy_state(hm_state* s) {
+  if (!s) return;
+  cudaSetDevice(s->device);
+  delete s;
+}
+
+static int chain_ok(hm_state* s, int chain) {
+  if (!s) return fail(HM_EINVAL, "null state");
+  if (chain < 0 || chain >= s->C) return fail(HM_EINVAL, "chain out of range");
+  return HM_OK;
+}
+
+int hm_state_set(hm_state* s, int32_t chain, const void* w, const double* d, const void* pw, const double* pd,
+                 void* stream) {
+  HM_TRY(chain_ok(s, chain));
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  HM_CUDA(cudaSetDevice(s->device));
+  const size_t gb = s->rsz * s->n3;
+  const PointParams& P = s->pp_host[chain];
+  if (w) HM_CUDA(cudaMemcpyAsync((char*)s->w.p + gb * chain, w, gb, cudaMemcpyDeviceToDevice, st));
+  if (pw) HM_CUDA(cudaMemcpyAsync((char*)s->pw.p + gb * chain, pw, gb, cudaMemcpyDeviceToDevice, st));
+  if (d && P.pt_n) HM_CUDA(cudaMemcpyAsync(s->d.as<double>() + P.pt_off, d, 8 * P.pt_n, cudaMemcpyDeviceToDevice, st));
+  if (pd && P.pt_n) HM_CUDA(cudaMemcpyAsync(s->pd.as<double>() + P.pt_off, pd, 8 * P.pt_n, cudaMemcpyDeviceToDevice, st));
+  return HM_OK;
+}
+
+int hm_state_get(hm_state* s, int32_t chain, void* w, double* d, void* pw, double* pd, void* stream) {
+  HM_TRY(chain_ok(s, chain));
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  HM_CUDA(cudaSetDevice(s->device));
+  const size_t gb = s->rsz * s->n3;
+  const PointParams& P = s->pp_host[chain];
+  if (w) HM_CUDA(cudaMemcpyAsync(w, (char*)s->w.p + gb * chain, gb, cudaMemcpyDeviceToDevice, st));
+  if (pw) HM_CUDA(cudaMemcpyAsync(pw, (char*)s->pw.p + gb * chain, gb, cudaMemcpyDeviceToDevice, st));
+  if (d && P.pt_n) HM_CUDA(cudaMemcpyAsync(d, s->d.as<double>() + P.pt_off, 8 * P.pt_n, cudaMemcpyDeviceToDevice, st));
+  if (pd && P.pt_n) HM_CUDA(cudaMemcpyAsync(pd, s->pd.as<double>() + P.pt_off, 8 * P.pt_n, cudaMemcpyDeviceToDevice, st));
+  return HM_OK;
+}
+
+int hm_state_get_grad(hm_state* s, int32_t chain, void* gw, double* gd, void* stream) {
+  HM_TRY(chain_ok(s, chain));
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  HM_CUDA(cudaSetDevice(s->device));
+  const size_t gb = s->rsz * s->n3;
+  const PointParams& P = s->pp_host[chain];
+  if (gw) HM_CUDA(cudaMemcpyAsync(gw, (char*)s->gw.p + gb * chain, gb, cudaMemcpyDeviceToDevice, st));
+  if (gd && P.pt_n) HM_CUDA(cudaMemcpyAsync(gd, s->gd.as<double>() + P.pt_off, 8 * P.pt_n, cudaMemcpyDeviceToDevice, st));
+  return HM_OK;
+}
+
+int hm_state_refresh(hm_state* s, void* stream) {
+  if (!s) return fail(HM_EINVAL, "null state");
+  HM_CUDA(cudaSetDevice(s->device));
+  return state_refresh(s, static_cast<cudaStream_t>(stream));
+}
+
+int hm_state_scalars(hm_state* s, int32_t chain, double* psi, double* kinetic, int64_t* traj, void* stream) {
+  HM_TRY(chain_ok(s, chain));
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  HM_CUDA(cudaSetDevice(s->device));
+  ChainScal S{};
+  HM_CUDA(cudaMemcpyAsync(&S, s->cs.as<ChainScal>() + chain, sizeof(S), cudaMemcpyDeviceToHost, st));
+  HM_CUDA(cudaStreamSynchronize(st));
+  if (psi) *psi = S.psi;
+  if (kinetic) *kinetic = S.kin;
+  if (traj) *traj = S.traj;
+  return HM_OK;
+}
+
+int hm_state_set_traj(hm_state* s, int32_t chain, int64_t traj) {
+  HM_TRY(chain_ok(s, chain));
+  HM_CUDA(cudaSetDevice(s->device));
+  long long t = traj;
+  HM_CUDA(cudaMemcpy(&(s->cs.as<ChainScal>() + chain)->traj, &t, sizeof(t), cudaMemcpyHostToDevice));
+  return HM_OK;
+}
+
+static int set_run(hm_state* s, const double* eps, int sample_d, cudaStream_t st) {
+  for (int c = 0; c < s->C; ++c) {
+    if (!(eps[c] > 0) || !std::isfinite(eps[c])) return fail(HM_EINVAL, "eps must be finite and > 0");
+    s->eps_host[c] = eps[c];
+  }
+  HM_CUDA(cudaMemcpyAsync(s->eps_dev.p, s->eps_host.data(), 8 * s->C, cudaMemcpyHostToDevice, st));
+  HM_CUDA(launch_set_run(s->C, s->eps_dev.as<double>(), sample_d ? 1 : 0, s->cs.as<ChainScal>(), st));
+  return HM_OK;
+}
+
+// leapfrog body: first half kick + drift from the stored gradient, then
+// n_steps gradient evaluations with fused kick (+ drift)
+static int leapfrog_body(hm_state* s, int n_steps, int draw, cudaStream_t st) {
+  GradArgs a = state_args(s);
+  PointArrays pa = a.pa;
+  HM_CUDA(launch_traj_begin_field(s->prec, s->C, s->n3, s->w.p, s->pw.p, s->gw.p, s->w0.p, s->gw0.p, s->seed,
+                                  s->chain_id.as<int>(), s->kinb_f.as<double>(), s->nparts_f, draw, a.cs, st));
+  if (s->max_pts > 0)
+    HM_CUDA(launch_traj_begin_points(s->C, s->max_pts, a.pp, pa, s->d0.as<double>(), s->gd0.as<double>(), s->seed,
+                                     s->chain_id.as<int>(), s->kinb_p.as<double>(), s->nparts_p, draw, a.cs, st));
+  HM_CUDA(launch_finalize(s->C, nullptr, 0, nullptr, 0, s->kinb_f.as<double>(), s->nparts_f,
+                          s->kinb_p.as<double>(), s->max_pts > 0 ? s->nparts_p : 0, FIN_HOLD, s->seed,
+                          s->chain_id.as<int>(), a.cs, nullptr, st));
+  for (int l = 1; l <= n_steps; ++l) HM_TRY(grad_eval(a, l < n_steps ? GM_KICK_DRIFT : GM_KICK_LAST, st));
+  return HM_OK;
+}
+
+int hm_leapfrog(hm_state* s, int32_t n_steps, double eps, int32_t sample_distances, void* stream) {
+  if (!s) return fail(HM_EINVAL, "null state");
+  if (n_steps <= 0) return fail(HM_EINVAL, "n_steps must be > 0");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  HM_CUDA(cudaSetDevice(s->device));
+  std::vector<double> e(s->C, eps);
+  HM_TRY(set_run(s, e.data(), sample_distances, st));
+  HM_TRY(leapfrog_body(s, n_steps, 0, st));
+  GradArgs a = state_args(s);
+  HM_CUDA(launch_finalize(s->C, a.prior_part, s->N, a.pts_part, s->pts_blocks, a.kinl_f, s->N, a.kinl_p,
+                          s->max_pts > 0 ? s->pts_blocks : 0, FIN_PSI | FIN_KIN, s->seed, s->chain_id.as<int>(),
+                          a.cs, nullptr, st));
+  return HM_OK;
+}
+
+static int trajectory(hm_state* s, int n_leapfrog, cudaStream_t st) {
+  HM_TRY(leapfrog_body(s, n_leapfrog, 1, st));
+  GradArgs a = state_args(s);
+  HM_CUDA(launch_finalize(s->C, a.prior_part, s->N, a.pts_part, s->pts_blocks, a.kinl_f, s->N, a.kinl_p,
+                          s->max_pts > 0 ? s->pts_blocks : 0, FIN_PSI | FIN_ACCEPT, s->seed,
+                          s->chain_id.as<int>(), a.cs, s->trace_dev.p, st));
+  HM_CUDA(launch_restore(s->prec, s->C, s->n3, s->w.p, s->gw.p, s->w0.p, s->gw0.p, s->max_pts, a.pp, a.pa,
+                         s->d0.as<double>(), s->gd0.as<double>(), a.cs, st));
+  return HM_OK;
+}
+
+int hm_run_chain(hm_state* s, int32_t n_traj, int32_t n_leapfrog, const double* eps_host, int32_t sample_distances,
+                 int32_t use_graph, hm_trace* trace_host, void* stream) {
+  if (!s || !eps_host) return fail(HM_EINVAL, "null argument");
+  if (n_traj < 0 || n_leapfrog <= 0) return fail(HM_EINVAL, "n_traj >= 0 and n_leapfrog > 0 required");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  HM_CUDA(cudaSetDevice(s->device));
+  const size_t need = sizeof(hm_trace) * (size_t)std::max(1, n_traj) * s->C;
+  if (s->trace_cap < need) {
+    HM_TRY(s->trace_dev.alloc(need));
+    s->trace_cap = need;
+    if (s->gexec) {
+      cudaGraphExecDestroy(s->gexec);
+      s->gexec = nullptr;
+    }
+  }
+  HM_TRY(set_run(s, eps_host, sample_distances, st));
+  if (!use_graph) {
+    for (int t = 0; t < n_traj; ++t) HM_TRY(trajectory(s, n_leapfrog, st));
+  } else if (n_traj > 0) {
+    if (!s->gstream) HM_CUDA(cudaStreamCreateWithFlags(&s->gstream, cudaStreamNonBlocking));
+    if (!s->gexec || s->g_L != n_leapfrog || s->g_sd != sample_distances) {
+      if (s->gexec) {
+        cudaGraphExecDestroy(s->gexec);
+        s->gexec = nullptr;
+      }
+      cudaGraph_t g = nullptr;
+      HM_CUDA(cudaStreamBeginCapture(s->gstream, cudaStreamCaptureModeThreadLocal));
+      int rc = trajectory(s, n_leapfrog, s->gstream);
+      cudaError_t ce = cudaStreamEndCapture(s->gstream, &g);
+      if (rc != HM_OK) {
+        if (g) cudaGraphDestroy(g);
+        return rc;
+      }
+      if (ce != cudaSuccess) return fail(HM_ECUDA, std::string("graph capture: ") + cudaGetErrorString(ce));
+      ce = cudaGraphInstantiate(&s->gexec, g, 0);
+      cudaGraphDestroy(g);
+      if (ce != cudaSuccess) return fail(HM_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(ce));
+      s->g_L = n_leapfrog;
+      s->g_sd = sample_distances;
+    }
+    cudaEvent_t ev;
+    HM_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    HM_CUDA(cudaEventRecord(ev, st));
+    HM_CUDA(cudaStreamWaitEvent(s->gstream, ev, 0));
+    for (int t = 0; t < n_traj; ++t) HM_CUDA(cudaGraphLaunch(s->gexec, s->gstream));
+    HM_CUDA(cudaEventRecord(ev, s->gstream));
+    HM_CUDA(cudaStreamWaitEvent(st, ev, 0));
+    HM_CUDA(cudaEventDestroy(ev));
+  }
+  if (trace_host && n_traj > 0) {
+    HM_CUDA(cudaMemcpyAsync(trace_host, s->trace_dev.p, sizeof(hm_trace) * (size_t)n_traj * s->C,
+                            cudaMemcpyDeviceToHost, st));
+    HM_CUDA(cudaStreamSynchronize(st));
+  }
+  return HM_OK;
+}
+
+}  // extern "C"

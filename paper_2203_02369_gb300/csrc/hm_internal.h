@@ -1,0 +1,154 @@
+// Internal declarations shared by the HAMLET CUDA translation units.
+#pragma once
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <cstddef>
+
+namespace hm {
+
+constexpr double kC = 299792.458;  // speed of light, km/s
+constexpr double kH0 = 100.0;      // km/s/(Mpc/h)
+
+enum PriorKind : int { PRIOR_TABLE = 0, PRIOR_POWER = 1 };
+
+// Per-chain constants of the point likelihood (device resident).
+struct PointParams {
+  double obs[3];
+  double delta;          // grid spacing L/N
+  double omega_m, h;
+  double sigma_nl2;      // sigma_NL^2
+  double minv_d;         // (sigma_v/H0)^2, inverse mass of a distance
+  int N;
+  int prior_kind;
+  int prior_nbins;
+  int pad0;
+  double prior_d0, prior_bin;
+  const double* prior_logdens;
+  double prior_alpha, prior_dmin, prior_dmax;
+  long long pt_off, pt_n;  // this chain's slice of the point arrays
+};
+
+// Per-chain scalars (device resident, FP64 energies).
+struct ChainScal {
+  double eps;            // leapfrog step
+  double psi;            // Psi at the current position q
+  double psi_prior;      // |w|^2/2 at q
+  double psi_pts;        // sum of point terms at q
+  double kin;            // kinetic energy of the current momenta
+  double H_old, H_new, logu;
+  double psi0;           // Psi at the trajectory start
+  long long traj;        // trajectory counter (Philox counter word 1)
+  long long traj_run0;   // counter at the start of the current run (trace row 0)
+  int accept;            // last decision
+  int status;            // bit flags, see STATUS_*
+  int n_bad;             // points outside the support at the last evaluation
+  int sample_d;          // 1: distances move, 0: held fixed
+};
+
+enum : int { STATUS_DOMAIN = 1, STATUS_NONFINITE = 2 };
+
+// Epilogue modes of the last c2r pass of the gradient.
+enum GradMode : int {
+  GM_GRAD = 0,        // grad_w = w + g, prior partials (no momentum update)
+  GM_KICK_DRIFT = 1,  // p -= eps*grad; w += eps*p
+  GM_KICK_LAST = 2,   // p -= eps/2*grad; store grad; kinetic partials
+  GM_KICK_HALF_DRIFT = 3  // p -= eps/2*grad; w += eps*p (reverse use / tests)
+};
+
+struct FieldEpi {
+  void* w;          // T [C][N^3] position (read; written when drifting)
+  void* pw;         // T [C][N^3] momenta
+  void* gw;         // T [C][N^3] gradient out (GM_GRAD, GM_KICK_LAST)
+  double* prior_part;  // [C][N] partial sums of w^2/2 (one per x-plane)
+  double* kin_part;    // [C][N] partial sums of p^2/2
+  ChainScal* cs;
+  long long grid_stride;  // elements between chains
+  int mode;
+};
+
+// ---- FFT passes (hm_fft_kernels.cu) ----
+// Spectrum layout: [x][y][z], z in 0..N/2 (NH = N/2+1 entries), complex.
+enum PencilMode : int { PM_FWD = 0, PM_INV = 1, PM_VEL = 2, PM_ADJ = 3 };
+
+// count grids, real [count][N^3] -> partially transformed planes.
+cudaError_t launch_plane_r2c(int prec, int N, const void* in, long long in_stride, void* out,
+                             long long out_stride, int count, const void* tw, cudaStream_t st);
+// count spectra -> real grids (plain store), or the gradient epilogue.
+cudaError_t launch_plane_c2r(int prec, int N, const void* in, long long in_stride, void* out,
+                             long long out_stride, int count, const void* tw, const FieldEpi* epi,
+                             cudaStream_t st);
+// x-axis pass over count chains.  PM_VEL: 1 spectrum -> 3; PM_ADJ: 3 -> 1.
+cudaError_t launch_pencil(int prec, int N, int mode, const void* in, long long in_stride, void* out,
+                          long long out_stride, int count, const void* tw, const void* amp,
+                          cudaStream_t st);
+bool fft_supported(int prec, int N);
+// Raise the dynamic shared-memory limit of every FFT kernel for (prec, N) on
+// the current device; call once per device before any launch or capture.
+cudaError_t fft_prepare(int prec, int N);
+
+// ---- points (hm_points.cu) ----
+struct PointArrays {
+  const double* rx;
+  const double* ry;
+  const double* rz;
+  const double* mu;
+  const double* smu;
+  const double* zobs;
+  const double* scz;
+  double* d;
+  double* pd;
+  double* gd;
+  void* r;        // T residual dPsi/du per point
+  int* cell;      // linear lower-corner cell index
+  void* frac;     // T [3][ntot] fractional offsets
+  long long ntot;
+};
+
+cudaError_t launch_points_gather(int prec, int n_chains, int max_pts, const PointParams* pp,
+                                 PointArrays pa, const void* vgrid, long long grid_stride,
+                                 double* pts_part, int part_stride, ChainScal* cs, cudaStream_t st);
+cudaError_t launch_points_scatter(int prec, int n_chains, int max_pts, const PointParams* pp,
+                                  PointArrays pa, void* sgrid, long long grid_stride,
+                                  cudaStream_t st);
+// p_d/d update after the scatter (mode as GradMode) and kinetic partials.
+cudaError_t launch_points_kick(int n_chains, int max_pts, const PointParams* pp, PointArrays pa,
+                               int mode, double* kin_part, int part_stride, ChainScal* cs,
+                               double* gd_store, cudaStream_t st);
+cudaError_t launch_cells(int n_chains, int max_pts, const PointParams* pp, const double* d,
+                         PointArrays pa, int* cell_out, cudaStream_t st);
+cudaError_t launch_cell_sort(int N3, long long n, const int* cell, int* perm, int* hist_ws,
+                             cudaStream_t st);
+
+// ---- HMC elementwise / scalar kernels (hm_hmc.cu) ----
+// draw != 0: fresh momenta from Philox; draw == 0: keep the stored momenta.
+cudaError_t launch_traj_begin_field(int prec, int n_chains, long long n3, void* w, void* pw,
+                                    const void* gw, void* w0, void* gw0, unsigned long long seed,
+                                    const int* chain_id, double* kin_part, int nparts, int draw,
+                                    ChainScal* cs, cudaStream_t st);
+cudaError_t launch_traj_begin_points(int n_chains, int max_pts, const PointParams* pp,
+                                     PointArrays pa, double* d0, double* gd0,
+                                     unsigned long long seed, const int* chain_id,
+                                     double* kin_part, int nparts, int draw, ChainScal* cs,
+                                     cudaStream_t st);
+// Set eps and sample_d of every chain from a device array of eps values.
+cudaError_t launch_set_run(int n_chains, const double* eps, int sample_d, ChainScal* cs,
+                           cudaStream_t st);
+cudaError_t launch_finalize(int n_chains, const double* prior_part, int n_prior, const double* pts_part,
+                            int n_pts, const double* kin_part, int n_kin, const double* kin_pts_part,
+                            int n_kin_pts, int what, unsigned long long seed, const int* chain_id,
+                            ChainScal* cs, void* trace_dev, cudaStream_t st);
+cudaError_t launch_restore(int prec, int n_chains, long long n3, void* w, void* gw, const void* w0,
+                           const void* gw0, int max_pts, const PointParams* pp, PointArrays pa,
+                           const double* d0, const double* gd0, const ChainScal* cs,
+                           cudaStream_t st);
+cudaError_t launch_philox_raw(unsigned long long seed, long long n, unsigned int c1, unsigned int c2,
+                              unsigned int c3, unsigned int* out, cudaStream_t st);
+
+enum FinalizeWhat : int {
+  FIN_PSI = 1,       // psi = prior + pts
+  FIN_HOLD = 2,      // H_old = psi + kin(begin)
+  FIN_ACCEPT = 4,    // H_new, Metropolis test, traj++
+  FIN_KIN = 8,       // kin = sum of the kinetic partials given
+};
+
+}  // namespace hm

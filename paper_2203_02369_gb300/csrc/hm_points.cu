@@ -1,0 +1,374 @@
+// Point-side kernels of the HAMLET posterior: positions and cells, the
+// cloud-in-cell gather of the linear velocity field at each point's sampled
+// distance, the FP64 likelihood terms with their gradients (eqs. lmu, vrobs,
+// lvr, kappa, D), the adjoint CIC scatter of the residuals, and the leapfrog
+// update of the distances (mass matrix eq. M_ab: (sigma_v/H0)^2 for d).
+#include "hm_fft.cuh"
+#include "hm_internal.h"
+
+namespace hm {
+
+constexpr int kPtsNT = 256;
+
+// Lower-corner cell and fractional offsets of x = o + d rhat, formed as
+// t = (o + d*r)/Delta with one IEEE rounding per operation (no contraction),
+// so that the cell indices are reproducible bit for bit on any IEEE host.
+struct CellPos {
+  int ix, iy, iz;
+  double fx, fy, fz;
+};
+
+__device__ __forceinline__ void cell_axis(double o, double d, double r, double delta, int N, int& i,
+                                          double& f) {
+  const double t = __ddiv_rn(__dadd_rn(o, __dmul_rn(d, r)), delta);
+  const double fl = floor(t);
+  f = __dadd_rn(t, -fl);
+  long long ii = (long long)fl;
+  ii %= N;
+  if (ii < 0) ii += N;
+  i = (int)ii;
+}
+
+__device__ __forceinline__ CellPos cell_of(const PointParams& P, double d, double rx, double ry, double rz) {
+  CellPos c;
+  cell_axis(P.obs[0], d, rx, P.delta, P.N, c.ix, c.fx);
+  cell_axis(P.obs[1], d, ry, P.delta, P.N, c.iy, c.fy);
+  cell_axis(P.obs[2], d, rz, P.delta, P.N, c.iz, c.fz);
+  return c;
+}
+
+// ln pi_D(d) and its derivative; returns false outside the support.
+__device__ __forceinline__ bool log_prior(const PointParams& P, double d, double& lp, double& dlp) {
+  if (P.prior_kind == PRIOR_TABLE) {
+    const double b = floor((d - P.prior_d0) / P.prior_bin);
+    if (!(b >= 0.0 && b < (double)P.prior_nbins)) return false;
+    lp = P.prior_logdens[(int)b];
+    dlp = 0.0;
+    return true;
+  }
+  if (!(d >= P.prior_dmin && d <= P.prior_dmax)) return false;
+  lp = P.prior_alpha * log(d);
+  dlp = P.prior_alpha / d;
+  return true;
+}
+
+template <typename T>
+__device__ __forceinline__ double block_sum(double v, double* red) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) red[wid] = v;
+  __syncthreads();
+  double s = 0.0;
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) s += red[i];
+  }
+  return s;
+}
+
+// ---------------------------------------------------------------------------
+// Gather + likelihood.  vgrid holds v_x, v_y, v_z for every chain:
+// vgrid[c*grid_stride + j*N^3 + (ix*N + iy)*N + iz].
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(kPtsNT)
+k_points_gather(const PointParams* __restrict__ pp, PointArrays pa, const T* __restrict__ vgrid,
+                long long grid_stride, double* __restrict__ pts_part, int part_stride,
+                ChainScal* __restrict__ cs) {
+  __shared__ double red[kPtsNT / 32];
+  const int c = blockIdx.y;
+  const PointParams& P = pp[c];
+  const long long il = (long long)blockIdx.x * kPtsNT + threadIdx.x;
+  double psi_i = 0.0;
+  int bad = 0;
+  if (il < P.pt_n) {
+    const long long i = P.pt_off + il;
+    const double d = pa.d[i];
+    const double rx = pa.rx[i], ry = pa.ry[i], rz = pa.rz[i];
+    const CellPos cp = cell_of(P, d, rx, ry, rz);
+    const int N = P.N;
+    const long long N3 = (long long)N * N * N;
+    T* frac = static_cast<T*>(pa.frac);
+    pa.cell[i] = (cp.ix * N + cp.iy) * N + cp.iz;
+    frac[i] = (T)cp.fx;
+    frac[pa.ntot + i] = (T)cp.fy;
+    frac[2 * pa.ntot + i] = (T)cp.fz;
+    // domain of the second-order zbar(d) and of the distance prior
+    const double om = P.omega_m;
+    const double x = 1.0 - 3.0 * om * kH0 * d / kC;
+    double lp = 0.0, dlp = 0.0;
+    const bool ok = d > 0.0 && x > 0.0 && log_prior(P, d, lp, dlp);
+    T* rres = static_cast<T*>(pa.r);
+    if (!ok) {
+      psi_i = __longlong_as_double(0x7ff0000000000000LL);  // +inf
+      rres[i] = (T)0;
+      pa.gd[i] = 0.0;
+      bad = 1;
+    } else {
+      // CIC gather of the three components and their spatial gradients
+      const T fx = (T)cp.fx, fy = (T)cp.fy, fz = (T)cp.fz;
+      const T wx[2] = {(T)1 - fx, fx}, wy[2] = {(T)1 - fy, fy}, wz[2] = {(T)1 - fz, fz};
+      const int xs[2] = {cp.ix, cp.ix + 1 == N ? 0 : cp.ix + 1};
+      const int ys[2] = {cp.iy, cp.iy + 1 == N ? 0 : cp.iy + 1};
+      const int zs[2] = {cp.iz, cp.iz + 1 == N ? 0 : cp.iz + 1};
+      const T* vb = vgrid + (long long)c * grid_stride;
+      T val[3] = {0, 0, 0}, gx[3] = {0, 0, 0}, gy[3] = {0, 0, 0}, gz[3] = {0, 0, 0};
+#pragma unroll
+      for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int b = 0; b < 2; ++b)
+#pragma unroll
+          for (int e = 0; e < 2; ++e) {
+            const long long idx = ((long long)xs[a] * N + ys[b]) * N + zs[e];
+            const T wxyz = wx[a] * wy[b] * wz[e];
+            const T dx = (a ? (T)1 : (T)-1) * wy[b] * wz[e];
+            const T dy = (b ? (T)1 : (T)-1) * wx[a] * wz[e];
+            const T dz = (e ? (T)1 : (T)-1) * wx[a] * wy[b];
+#pragma unroll
+            for (int j = 0; j < 3; ++j) {
+              const T g = __ldg(&vb[j * N3 + idx]);
+              val[j] += wxyz * g;
+              gx[j] += dx * g;
+              gy[j] += dy * g;
+              gz[j] += dz * g;
+            }
+          }
+      const double r3[3] = {rx, ry, rz};
+      double u = 0.0, du = 0.0;
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        u += r3[j] * (double)val[j];
+        du += r3[j] * ((double)gx[j] * rx + (double)gy[j] * ry + (double)gz[j] * rz);
+      }
+      du /= P.delta;
+      // point likelihood terms, FP64
+      const double sq = sqrt(x);
+      const double zb = 2.0 / (3.0 * om) * (1.0 - sq);
+      const double zbp = (kH0 / kC) / sq;
+      const double opz = 1.0 + zb;
+      const double mu_d = 5.0 * log10(d * opz / P.h) + 25.0;
+      const double mup = 5.0 / log(10.0) * (1.0 / d + zbp / opz);
+      const double z = pa.zobs[i];
+      const double vo = kC * (z - zb) / opz;
+      const double vop = -kC * zbp * (1.0 + z) / (opz * opz);
+      const double scz = pa.scz[i];
+      const double k2 = P.sigma_nl2 + scz * scz / (opz * opz);
+      const double k2p = -2.0 * scz * scz * zbp / (opz * opz * opz);
+      const double smu = pa.smu[i];
+      const double res_mu = pa.mu[i] - mu_d;
+      const double res_v = vo - u;
+      psi_i = res_mu * res_mu / (2.0 * smu * smu) + res_v * res_v / (2.0 * k2) + 0.5 * log(k2) - lp;
+      rres[i] = (T)(-res_v / k2);
+      pa.gd[i] = -res_mu * mup / (smu * smu) + res_v * (vop - du) / k2 -
+                 res_v * res_v * k2p / (2.0 * k2 * k2) + k2p / (2.0 * k2) - dlp;
+    }
+  }
+  const double s = block_sum<T>(psi_i, red);
+  if (threadIdx.x == 0) pts_part[(long long)c * part_stride + blockIdx.x] = s;
+  if (bad) atomicOr(&cs[c].status, STATUS_DOMAIN);
+}
+
+// ---------------------------------------------------------------------------
+// Adjoint CIC scatter: s_j(corner) += r_i rhat_ij W(corner).
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(kPtsNT)
+k_points_scatter(const PointParams* __restrict__ pp, PointArrays pa, T* __restrict__ sgrid,
+                 long long grid_stride) {
+  const int c = blockIdx.y;
+  const PointParams& P = pp[c];
+  const long long il = (long long)blockIdx.x * kPtsNT + threadIdx.x;
+  if (il >= P.pt_n) return;
+  const long long i = P.pt_off + il;
+  const T r = static_cast<const T*>(pa.r)[i];
+  if (r == (T)0) return;
+  const int N = P.N;
+  const long long N3 = (long long)N * N * N;
+  const int lin = pa.cell[i];
+  const int iz = lin % N, iy = (lin / N) % N, ix = lin / (N * N);
+  const T* frac = static_cast<const T*>(pa.frac);
+  const T fx = frac[i], fy = frac[pa.ntot + i], fz = frac[2 * pa.ntot + i];
+  const T wx[2] = {(T)1 - fx, fx}, wy[2] = {(T)1 - fy, fy}, wz[2] = {(T)1 - fz, fz};
+  const int xs[2] = {ix, ix + 1 == N ? 0 : ix + 1};
+  const int ys[2] = {iy, iy + 1 == N ? 0 : iy + 1};
+  const int zs[2] = {iz, iz + 1 == N ? 0 : iz + 1};
+  const T rj[3] = {r * (T)pa.rx[i], r * (T)pa.ry[i], r * (T)pa.rz[i]};
+  T* sb = sgrid + (long long)c * grid_stride;
+#pragma unroll
+  for (int a = 0; a < 2; ++a)
+#pragma unroll
+    for (int b = 0; b < 2; ++b)
+#pragma unroll
+      for (int e = 0; e < 2; ++e) {
+        const long long idx = ((long long)xs[a] * N + ys[b]) * N + zs[e];
+        const T wxyz = wx[a] * wy[b] * wz[e];
+#pragma unroll
+        for (int j = 0; j < 3; ++j) atomicAdd(&sb[j * N3 + idx], rj[j] * wxyz);
+      }
+}
+
+// ---------------------------------------------------------------------------
+// Leapfrog update of the distances after the gradient at q_l is known.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kPtsNT)
+k_points_kick(const PointParams* __restrict__ pp, PointArrays pa, int mode, double* __restrict__ kin_part,
+              int part_stride, ChainScal* __restrict__ cs) {
+  __shared__ double red[kPtsNT / 32];
+  const int c = blockIdx.y;
+  const PointParams& P = pp[c];
+  const long long il = (long long)blockIdx.x * kPtsNT + threadIdx.x;
+  double k = 0.0;
+  const double eps = cs[c].eps;
+  if (il < P.pt_n && cs[c].sample_d) {
+    const long long i = P.pt_off + il;
+    const double ck = (mode == GM_KICK_DRIFT) ? eps : 0.5 * eps;
+    double p = pa.pd[i] - ck * pa.gd[i];
+    pa.pd[i] = p;
+    if (mode == GM_KICK_DRIFT || mode == GM_KICK_HALF_DRIFT) pa.d[i] = pa.d[i] + eps * P.minv_d * p;
+    k = 0.5 * P.minv_d * p * p;
+  }
+  if (mode == GM_KICK_LAST) {
+    const double s = block_sum<double>(k, red);
+    if (threadIdx.x == 0) kin_part[(long long)c * part_stride + blockIdx.x] = s;
+  }
+}
+
+// Cells only (bit-exact index work), for the sort and for tests.
+__global__ void k_cells(const PointParams* __restrict__ pp, PointArrays pa, const double* __restrict__ d,
+                        int* __restrict__ cell_out) {
+  const int c = blockIdx.y;
+  const PointParams& P = pp[c];
+  const long long il = (long long)blockIdx.x * kPtsNT + threadIdx.x;
+  if (il >= P.pt_n) return;
+  const long long i = P.pt_off + il;
+  const CellPos cp = cell_of(P, d[i], pa.rx[i], pa.ry[i], pa.rz[i]);
+  cell_out[i] = (cp.ix * P.N + cp.iy) * P.N + cp.iz;
+}
+
+// ---------------------------------------------------------------------------
+// Stable counting sort of n points by cell index (one CTA; keys < N3).
+// Pass 1 histograms, pass 2 an exclusive scan over cells, pass 3 walks the
+// points in index order in chunks of blockDim, ranking equal keys inside a
+// chunk with warp match masks so that equal cells keep their index order.
+// ---------------------------------------------------------------------------
+constexpr int kSortNT = 1024;
+
+__global__ void __launch_bounds__(kSortNT) k_cell_sort(int N3, long long n, const int* __restrict__ cell,
+                                                       int* __restrict__ perm, int* __restrict__ hist) {
+  __shared__ int wsum[kSortNT / 32];
+  __shared__ int carry;
+  for (int k = threadIdx.x; k < N3; k += kSortNT) hist[k] = 0;
+  __syncthreads();
+  for (long long i = threadIdx.x; i < n; i += kSortNT) atomicAdd(&hist[cell[i]], 1);
+  __syncthreads();
+  // exclusive scan of hist over N3 entries, chunks of kSortNT
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  for (int base = 0; base < N3; base += kSortNT) {
+    const int k = base + threadIdx.x;
+    int v = k < N3 ? hist[k] : 0;
+    int x = v;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      int y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) wsum[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+      int s = wsum[lane];
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        int y = __shfl_up_sync(0xffffffffu, s, o);
+        if (lane >= o) s += y;
+      }
+      wsum[lane] = s;
+    }
+    __syncthreads();
+    const int excl = carry + (wid > 0 ? wsum[wid - 1] : 0) + x - v;
+    if (k < N3) hist[k] = excl;
+    __syncthreads();
+    if (threadIdx.x == kSortNT - 1) carry = excl + v;
+    __syncthreads();
+  }
+  // stable placement
+  for (long long base = 0; base < n; base += kSortNT) {
+    const long long i = base + threadIdx.x;
+    const bool valid = i < n;
+    const int key = valid ? cell[i] : -1;
+    const int lane = threadIdx.x & 31;
+    const unsigned act = __ballot_sync(0xffffffffu, valid);
+    const unsigned peers = __match_any_sync(0xffffffffu, key) & act;
+    const int rank_in_warp = __popc(peers & ((1u << lane) - 1u));
+    const int leader_last = 31 - __clz(peers);  // highest lane with this key
+    // warps go one after another so that earlier indices are placed first
+    for (int w = 0; w < kSortNT / 32; ++w) {
+      if ((int)(threadIdx.x >> 5) == w && valid) {
+        const int pos = hist[key] + rank_in_warp;
+        perm[pos] = (int)i;
+        __syncwarp(peers);
+        if (lane == leader_last) hist[key] += __popc(peers);
+      }
+      __syncthreads();
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Launchers.
+// ---------------------------------------------------------------------------
+static inline dim3 pts_grid(int n_chains, int max_pts) {
+  return dim3((unsigned)((max_pts + kPtsNT - 1) / kPtsNT > 0 ? (max_pts + kPtsNT - 1) / kPtsNT : 1), n_chains);
+}
+
+cudaError_t launch_points_gather(int prec, int n_chains, int max_pts, const PointParams* pp,
+                                 PointArrays pa, const void* vgrid, long long grid_stride,
+                                 double* pts_part, int part_stride, ChainScal* cs, cudaStream_t st) {
+  dim3 g = pts_grid(n_chains, max_pts);
+  if (prec == 0)
+    k_points_gather<float><<<g, kPtsNT, 0, st>>>(pp, pa, static_cast<const float*>(vgrid), grid_stride,
+                                                 pts_part, part_stride, cs);
+  else
+    k_points_gather<double><<<g, kPtsNT, 0, st>>>(pp, pa, static_cast<const double*>(vgrid), grid_stride,
+                                                  pts_part, part_stride, cs);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_points_scatter(int prec, int n_chains, int max_pts, const PointParams* pp,
+                                  PointArrays pa, void* sgrid, long long grid_stride,
+                                  cudaStream_t st) {
+  if (max_pts <= 0) return cudaSuccess;
+  dim3 g = pts_grid(n_chains, max_pts);
+  if (prec == 0)
+    k_points_scatter<float><<<g, kPtsNT, 0, st>>>(pp, pa, static_cast<float*>(sgrid), grid_stride);
+  else
+    k_points_scatter<double><<<g, kPtsNT, 0, st>>>(pp, pa, static_cast<double*>(sgrid), grid_stride);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_points_kick(int n_chains, int max_pts, const PointParams* pp, PointArrays pa,
+                               int mode, double* kin_part, int part_stride, ChainScal* cs,
+                               double* /*gd_store*/, cudaStream_t st) {
+  dim3 g = pts_grid(n_chains, max_pts);
+  k_points_kick<<<g, kPtsNT, 0, st>>>(pp, pa, mode, kin_part, part_stride, cs);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_cells(int n_chains, int max_pts, const PointParams* pp, const double* d,
+                         PointArrays pa, int* cell_out, cudaStream_t st) {
+  if (max_pts <= 0) return cudaSuccess;
+  dim3 g = pts_grid(n_chains, max_pts);
+  k_cells<<<g, kPtsNT, 0, st>>>(pp, pa, d, cell_out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_cell_sort(int N3, long long n, const int* cell, int* perm, int* hist_ws,
+                             cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  k_cell_sort<<<1, kSortNT, 0, st>>>(N3, n, cell, perm, hist_ws);
+  return cudaGetLastError();
+}
+
+}  // namespace hm

@@ -1,0 +1,262 @@
+"""Python face of libhamlet: problems and chain states over torch tensors.
+
+PyTorch supplies device memory and the current CUDA stream; every step of the
+posterior, its gradient and the HMC chain runs in libhamlet's kernels.
+"""
+from __future__ import annotations
+
+import ctypes as ct
+from dataclasses import asdict
+
+import numpy as np
+import torch
+
+from . import _lib
+from ._lib import check
+from .mock import Cosmology, MockSpec
+
+_FT = {0: torch.float32, 1: torch.float64}
+_CT = {0: torch.complex64, 1: torch.complex128}
+
+
+def _ptr(t):
+    return ct.c_void_p(t.data_ptr()) if t is not None else ct.c_void_p(0)
+
+
+def _stream():
+    return ct.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _dptr(a):
+    return a.ctypes.data_as(_lib.c_double_p)
+
+
+class Problem:
+    """One reconstruction problem: grid, cosmology, catalogue, distance prior.
+
+    prior: ("table", d0, bin_width, logdens) or ("power", alpha, dmin, dmax).
+    """
+
+    def __init__(self, N, L, cosmo=None, sigma_nl=250.0, precision="fp32", prior=None,
+                 observer=None, device=0):
+        self.lib = _lib.load()
+        cosmo = cosmo or Cosmology()
+        c = asdict(cosmo) if isinstance(cosmo, Cosmology) else dict(cosmo)
+        d = _lib.hm_problem_desc()
+        d.N = int(N)
+        d.precision = 0 if precision == "fp32" else 1
+        d.L = float(L)
+        if observer is not None:
+            d.observer_set = 1
+            for j in range(3):
+                d.observer[j] = float(observer[j])
+        d.omega_m = c.get("omega_m", 0.3)
+        d.omega_b = c.get("omega_b", 0.05)
+        d.h = c.get("h", 0.7)
+        d.n_s = c.get("n_s", 0.96)
+        d.sigma8 = c.get("sigma8", 0.8)
+        d.T_cmb = c.get("T_cmb", 2.7255)
+        d.f_growth = c.get("f_growth", -1.0)
+        d.sigma_nl = float(sigma_nl)
+        prior = prior or ("power", 2.0, 0.5, 0.45 * L)
+        self._prior_keep = None
+        if prior[0] == "table":
+            d.prior_kind = _lib.HM_PRIOR_TABLE
+            d.prior_d0 = float(prior[1])
+            d.prior_bin = float(prior[2])
+            ld = np.ascontiguousarray(prior[3], dtype=np.float64)
+            self._prior_keep = ld
+            d.prior_nbins = ld.shape[0]
+            d.prior_logdens_host = _dptr(ld)
+        else:
+            d.prior_kind = _lib.HM_PRIOR_POWER
+            d.prior_alpha, d.prior_dmin, d.prior_dmax = map(float, prior[1:4])
+        d.device = int(device)
+        self.N = int(N)
+        self.L = float(L)
+        self.prec = d.precision
+        self.device = torch.device("cuda", int(device))
+        self.dtype = _FT[self.prec]
+        self.cdtype = _CT[self.prec]
+        self.h = ct.c_void_p()
+        check(self.lib.hm_init_problem(ct.byref(d), ct.byref(self.h)))
+        self.n = 0
+
+    @classmethod
+    def from_mock(cls, spec: MockSpec, cat: dict, device=0, prior=None):
+        p = cls(spec.N, spec.L, spec.cosmo, spec.sigma_nl, spec.precision,
+                prior or ("table", cat["prior_d0"], cat["prior_bin"], cat["prior_logdens"]),
+                device=device)
+        p.set_catalog(cat["rhat"], cat["mu"], cat["sigma_mu"], cat["cz"], cat["sigma_cz"])
+        return p
+
+    def close(self):
+        if self.h:
+            self.lib.hm_destroy_problem(self.h)
+            self.h = ct.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_catalog(self, rhat, mu, sigma_mu, cz, sigma_cz=None):
+        rhat = np.ascontiguousarray(rhat, dtype=np.float64).reshape(-1, 3)
+        n = rhat.shape[0]
+        arrs = [np.ascontiguousarray(a, dtype=np.float64) for a in (mu, sigma_mu, cz)]
+        scz = None if sigma_cz is None else np.ascontiguousarray(sigma_cz, dtype=np.float64)
+        check(self.lib.hm_set_catalog(self.h, n, _dptr(rhat), _dptr(arrs[0]), _dptr(arrs[1]),
+                                      _dptr(arrs[2]), _dptr(scz) if scz is not None else None))
+        self.n = n
+
+    @property
+    def info(self):
+        i = _lib.hm_problem_info()
+        check(self.lib.hm_problem_get_info(self.h, ct.byref(i)))
+        return {k: getattr(i, k) for k, _ in i._fields_}
+
+    def field(self, value=None):
+        t = torch.zeros((self.N,) * 3, dtype=self.dtype, device=self.device)
+        if value is not None:
+            t.copy_(torch.as_tensor(value))
+        return t
+
+    def logpost_grad(self, w, d):
+        """(Psi, dPsi/dw, dPsi/dd) at (w, d); Psi is a 0-d float64 tensor."""
+        w = w.to(self.device, self.dtype).contiguous()
+        d = d.to(self.device, torch.float64).contiguous()
+        psi = torch.empty((), dtype=torch.float64, device=self.device)
+        gw = torch.empty_like(w)
+        gd = torch.empty_like(d)
+        check(self.lib.hm_logpost_grad(self.h, _ptr(w), _ptr(d), _ptr(psi), _ptr(gw), _ptr(gd), _stream()))
+        return psi, gw, gd
+
+    def last_status(self):
+        v = ct.c_int32()
+        check(self.lib.hm_problem_last_status(self.h, _stream(), ct.byref(v)))
+        return v.value
+
+    def velocity_field(self, w):
+        w = w.to(self.device, self.dtype).contiguous()
+        v = torch.empty((3,) + (self.N,) * 3, dtype=self.dtype, device=self.device)
+        check(self.lib.hm_velocity_field(self.h, _ptr(w), _ptr(v), _stream()))
+        return v
+
+    def fft_r2c(self, x):
+        x = x.to(self.device, self.dtype).contiguous()
+        cnt = x.numel() // self.N ** 3
+        out = torch.empty((cnt, self.N, self.N, self.N // 2 + 1), dtype=self.cdtype, device=self.device)
+        check(self.lib.hm_fft_r2c(self.h, _ptr(x), _ptr(out), cnt, _stream()))
+        return out
+
+    def fft_c2r(self, X):
+        X = X.to(self.device, self.cdtype).contiguous()
+        cnt = X.numel() // (self.N * self.N * (self.N // 2 + 1))
+        out = torch.empty((cnt,) + (self.N,) * 3, dtype=self.dtype, device=self.device)
+        check(self.lib.hm_fft_c2r(self.h, _ptr(X), _ptr(out), cnt, _stream()))
+        return out
+
+    def cells(self, d, sort=True):
+        d = d.to(self.device, torch.float64).contiguous()
+        cell = torch.empty(d.shape[0], dtype=torch.int32, device=self.device)
+        perm = torch.empty(d.shape[0], dtype=torch.int32, device=self.device) if sort else None
+        check(self.lib.hm_cells(self.h, _ptr(d), _ptr(cell), _ptr(perm), _stream()))
+        return cell, perm
+
+
+TRACE_DTYPE = np.dtype([("traj", np.int64), ("H_old", np.float64), ("H_new", np.float64),
+                        ("logu", np.float64), ("psi", np.float64), ("accept", np.int32),
+                        ("status", np.int32)])
+
+
+class State:
+    """n_chains HMC chains over one or several problems of the same grid."""
+
+    def __init__(self, problems, d_init, seed=0, chain_problem=None, chain_ids=None):
+        if isinstance(problems, Problem):
+            problems = [problems]
+        self.problems = list(problems)
+        self.lib = self.problems[0].lib
+        nch = len(d_init)
+        self.C = nch
+        cp = list(chain_problem) if chain_problem is not None else [0] * nch
+        self.chain_problem = cp
+        self._d = [np.ascontiguousarray(x, dtype=np.float64) for x in d_init]
+        harr = (ct.c_void_p * len(self.problems))(*[p.h.value for p in self.problems])
+        cparr = (ct.c_int32 * nch)(*cp)
+        idarr = (ct.c_int32 * nch)(*(chain_ids if chain_ids is not None else range(nch)))
+        darr = (_lib.c_double_p * nch)(*[_dptr(x) for x in self._d])
+        self.h = ct.c_void_p()
+        check(self.lib.hm_state_create_batch(harr, len(self.problems), nch, cparr, idarr,
+                                             ct.c_uint64(int(seed)), darr, ct.byref(self.h)))
+        p0 = self.problems[0]
+        self.N, self.dtype, self.device = p0.N, p0.dtype, p0.device
+
+    def close(self):
+        if self.h:
+            self.lib.hm_destroy_state(self.h)
+            self.h = ct.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _n(self, c):
+        return self.problems[self.chain_problem[c]].n
+
+    def set(self, chain=0, w=None, d=None, pw=None, pd=None):
+        conv = lambda t, dt: None if t is None else t.to(self.device, dt).contiguous()
+        w, pw = conv(w, self.dtype), conv(pw, self.dtype)
+        d, pd = conv(d, torch.float64), conv(pd, torch.float64)
+        check(self.lib.hm_state_set(self.h, chain, _ptr(w), _ptr(d), _ptr(pw), _ptr(pd), _stream()))
+        self._keep = (w, d, pw, pd)
+
+    def get(self, chain=0):
+        N = self.N
+        w = torch.empty((N,) * 3, dtype=self.dtype, device=self.device)
+        pw = torch.empty_like(w)
+        n = self._n(chain)
+        d = torch.empty(n, dtype=torch.float64, device=self.device)
+        pd = torch.empty_like(d)
+        check(self.lib.hm_state_get(self.h, chain, _ptr(w), _ptr(d), _ptr(pw), _ptr(pd), _stream()))
+        return dict(w=w, d=d, pw=pw, pd=pd)
+
+    def grad(self, chain=0):
+        gw = torch.empty((self.N,) * 3, dtype=self.dtype, device=self.device)
+        gd = torch.empty(self._n(chain), dtype=torch.float64, device=self.device)
+        check(self.lib.hm_state_get_grad(self.h, chain, _ptr(gw), _ptr(gd), _stream()))
+        return gw, gd
+
+    def refresh(self):
+        check(self.lib.hm_state_refresh(self.h, _stream()))
+
+    def scalars(self, chain=0):
+        psi, kin, traj = ct.c_double(), ct.c_double(), ct.c_int64()
+        check(self.lib.hm_state_scalars(self.h, chain, ct.byref(psi), ct.byref(kin), ct.byref(traj), _stream()))
+        return dict(psi=psi.value, kinetic=kin.value, traj=traj.value)
+
+    def set_traj(self, chain, traj):
+        check(self.lib.hm_state_set_traj(self.h, chain, int(traj)))
+
+    def leapfrog(self, n_steps, eps, sample_distances=True):
+        check(self.lib.hm_leapfrog(self.h, int(n_steps), float(eps), int(bool(sample_distances)), _stream()))
+
+    def run_chain(self, n_traj, n_leapfrog, eps, sample_distances=True, use_graph=False, trace=True):
+        eps_arr = np.ascontiguousarray(np.broadcast_to(np.asarray(eps, dtype=np.float64), (self.C,)))
+        tr = (_lib.hm_trace * (max(n_traj, 1) * self.C))() if trace else None
+        check(self.lib.hm_run_chain(self.h, int(n_traj), int(n_leapfrog), _dptr(eps_arr),
+                                    int(bool(sample_distances)), int(bool(use_graph)), tr, _stream()))
+        if not trace:
+            return None
+        out = np.frombuffer(tr, dtype=TRACE_DTYPE, count=n_traj * self.C).copy()
+        return out.reshape(n_traj, self.C)
+
+
+def philox(seed, n, c1, c2, c3, device=0):
+    lib = _lib.load()
+    out = torch.empty(4 * n, dtype=torch.int32, device=torch.device("cuda", device))
+    check(lib.hm_philox(ct.c_uint64(int(seed)), int(n), c1, c2, c3, _ptr(out), _stream()))
+    return out.view(torch.int32)
