@@ -1,0 +1,417 @@
+#!/usr/bin/env python
+"""HAMLET hot-path benchmark: HMC gradient evaluations per second (and ESS/s)
+on the paper-scale reconstruction -- 128^3 grid, box 500 Mpc/h, 3e4 points,
+FP32 fields with FP64 energies, one chain, trajectories of 20 leapfrog steps.
+
+One step = one HMC trajectory (momentum refresh, 20 gradient evaluations with
+fused kick/drift, energy, Metropolis test).  Inputs are synthetic (seeded mock
+catalogue with the paper's shapes).  L2 is flushed (a 512 MiB write) before
+every timed step; each step is timed with CUDA events on the launching stream.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+With N > 1 (torchrun) every rank runs an independent replica chain (no
+collective on the data path) and value = all ranks' gradient evaluations /
+the slowest rank's time.  --impl reference times the FP64 CPU oracle on the
+same workload (rank 0 only).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2203_02369_gb300 import mock  # noqa: E402
+
+METRIC = "HMC grad evals/s & ESS/s at 128³, 3e4 pts vs plain; served p50/p99 latency"
+UNIT = "grad_evals/s"
+WORKLOAD = "paper-scale plain HMC: 128^3 grid, L=500 Mpc/h, 3e4 points, 1 chain, 20 leapfrog steps/trajectory"
+N_LEAPFROG = 20
+EPS = 0.0125          # frozen step size (acceptance ~0.65 on this workload)
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--eps", type=float, default=EPS)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-ess", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-graph", action="store_true")
+    ap.add_argument("--tune-eps", action="store_true", help="print acceptance for a sweep of eps and exit")
+    return ap.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+# --------------------------------------------------------------------------
+# clocks sampler (nvidia-smi during the timed region)
+# --------------------------------------------------------------------------
+class Clocks:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.p = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except Exception:
+            self.p.kill()
+        self.fh.close()
+        sm, smax, reasons, power = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+                power.append(float(f[3]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm), "power_w_max": max(power) if power else None}
+
+
+# --------------------------------------------------------------------------
+# algorithmic bytes per launch of each kernel kind (FP32, one chain)
+# --------------------------------------------------------------------------
+def algorithmic_bytes(N, n, C=1, rsz=4):
+    R = rsz * N ** 3
+    S = 2 * rsz * N * N * (N // 2 + 1)
+    return {
+        "plane_r2c_field": C * (R + S),
+        "pencil_velocity": C * (S + 3 * S),
+        "plane_c2r_velocity": 3 * C * (S + R),
+        "points_gather_likelihood": C * n * 188,
+        "memset_scatter_grids": 3 * C * R,
+        "points_scatter": C * n * 236,
+        "points_kick_drift": C * n * 40,
+        "plane_r2c_adjoint": 3 * C * (R + S),
+        "pencil_adjoint": C * (3 * S + S),
+        "plane_c2r_gradient_kick": C * (S + 4 * R),
+        "trajectory_begin": C * (6 * R + 56 * n),
+        "finalize_energy": 0,
+        "restore_rejected": 0,
+    }
+
+
+# kernels launched inside one profiled pair of events
+KERNELS_PER_PAIR = {"memset_scatter_grids": 0, "trajectory_begin": 3, "restore_rejected": 2}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+def ncu_traffic(kind):
+    """dram bytes per launch of a kernel kind from the committed ncu summary,
+    or None when the kernel sources changed since that capture."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    try:
+        with open(path) as fh:
+            data = json.load(fh)
+    except Exception:
+        return None
+    ent = data.get("kernels", {}).get(kind)
+    if not ent:
+        return None
+    src = os.path.join(ROOT, "paper_2203_02369_gb300", "csrc", ent.get("source", ""))
+    try:
+        with open(src, "rb") as fh:
+            h = hashlib.sha256(fh.read()).hexdigest()
+    except Exception:
+        return None
+    if h != ent.get("source_sha256"):
+        return None
+    return ent.get("dram_bytes_per_launch")
+
+
+# --------------------------------------------------------------------------
+# reference arm: the FP64 oracle on the host cores
+# --------------------------------------------------------------------------
+def oracle_problem():
+    from oracle import hamlet_oracle as O
+    spec = mock.PRESETS["cfg3_128"]
+    cat = mock.make_catalog(spec)
+    op = O.problem_from_catalog(spec.N, spec.L, mock.spec_dict(spec)["cosmo"], spec.sigma_nl, cat)
+    return O, spec, cat, op
+
+
+def run_oracle_steps(n_steps, eps):
+    """n_steps oracle leapfrog steps (one gradient evaluation each) from the
+    mock start state; returns (seconds, evaluations)."""
+    O, spec, cat, op = oracle_problem()
+    w = np.zeros((spec.N,) * 3)
+    d = cat["d_init"].copy()
+    pw, pd = O.draw_momenta(op, 2, 0, 0)
+    psi, gw, gd = O.logpost_grad(op, w, d)
+    t0 = time.perf_counter()
+    for _ in range(n_steps):
+        pw -= 0.5 * eps * gw
+        pd -= 0.5 * eps * gd
+        w += eps * pw
+        d += eps * op.minv_d * pd
+        psi, gw, gd = O.logpost_grad(op, w, d)
+        pw -= 0.5 * eps * gw
+        pd -= 0.5 * eps * gd
+    return time.perf_counter() - t0, n_steps
+
+
+def reference_arm(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    # warm-up (import, FFT plans, page-in) then the timed steps
+    run_oracle_steps(max(1, min(args.warmup, 2)), args.eps)
+    secs, ev = run_oracle_steps(args.steps, args.eps)
+    val = ev / secs
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "grid": 128, "box": 500.0, "points": 30000,
+                       "step": "one oracle leapfrog step (one gradient evaluation)"},
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"{args.steps} oracle leapfrog steps (numpy FP64, 1 thread)"},
+            "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# --------------------------------------------------------------------------
+# our arm
+# --------------------------------------------------------------------------
+def main():
+    args = parse()
+    if args.impl == "reference":
+        reference_arm(args)
+        return
+    import torch
+    import torch.distributed as dist
+    from paper_2203_02369_gb300.hamlet import Problem, State
+    from paper_2203_02369_gb300.ess import ess
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", init_method="env://")
+    dev = torch.cuda.current_device()
+    spec = mock.PRESETS["cfg3_128"]
+    cat = mock.make_catalog(spec)
+    prob = Problem.from_mock(spec, cat, device=dev)
+    state = State(prob, [cat["d_init"]], seed=1000 + rank, chain_ids=[rank])
+    L = N_LEAPFROG
+    use_graph = not args.no_graph
+
+    if args.tune_eps:
+        for e in (0.005, 0.0075, 0.01, 0.0125, 0.015, 0.02, 0.03):
+            s2 = State(prob, [cat["d_init"]], seed=7)
+            s2.run_chain(30, L, e, use_graph=use_graph, trace=False)
+            tr = s2.run_chain(40, L, e, use_graph=use_graph)
+            print(json.dumps({"eps": e, "accept": float(tr["accept"].mean()),
+                              "dH_median": float(np.median(np.abs(tr["H_new"] - tr["H_old"])))}), flush=True)
+            s2.close()
+        return
+
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def barrier():
+        if ws > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    # warm-up (also burns the chain in)
+    state.run_chain(args.warmup, L, args.eps, use_graph=use_graph, trace=False)
+    state.profile(True)
+    state.run_chain(1, L, args.eps, use_graph=use_graph, trace=False)   # capture the profiled graph
+    barrier()
+    state.profile(True)                                                  # reset the totals
+
+    clocks = Clocks(dev)
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    clocks.start()
+    barrier()
+    t_wall = time.perf_counter()
+    acc = []
+    for k in range(args.steps):
+        flush.zero_()
+        starts[k].record(stream)
+        state.run_chain(1, L, args.eps, use_graph=use_graph, trace=False)
+        ends[k].record(stream)
+        torch.cuda.synchronize()
+        state.profile_collect()
+    barrier()
+    t_wall = time.perf_counter() - t_wall
+    clk = clocks.stop()
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    my_ms = float(np.sum(step_ms))
+    prof = state.profile_read()
+    state.profile(False)
+
+    # unprofiled steps, same loop, to show the cost of the kernel events
+    nu = min(args.steps, 30)
+    s_u = [torch.cuda.Event(enable_timing=True) for _ in range(nu)]
+    e_u = [torch.cuda.Event(enable_timing=True) for _ in range(nu)]
+    state.run_chain(1, L, args.eps, use_graph=use_graph, trace=False)
+    for k in range(nu):
+        torch.cuda.synchronize()
+        flush.zero_()
+        s_u[k].record(stream)
+        state.run_chain(1, L, args.eps, use_graph=use_graph, trace=False)
+        e_u[k].record(stream)
+    torch.cuda.synchronize()
+    ms_unprof = float(np.mean([s.elapsed_time(e) for s, e in zip(s_u, e_u)]))
+
+    # max over ranks of the timed device time
+    tot = torch.tensor([my_ms], dtype=torch.float64, device=dev)
+    if ws > 1:
+        dist.all_reduce(tot, op=dist.ReduceOp.MAX)
+    max_ms = float(tot.item())
+    evals = ws * args.steps * L
+    value = evals / (max_ms / 1e3)
+
+    # ESS/s on the Psi trace of a continuing chain (no flush between trajectories)
+    ess_info = None
+    if not args.no_ess:
+        M = 400
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        tr = state.run_chain(M, L, args.eps, use_graph=use_graph, trace=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        secs = e0.elapsed_time(e1) / 1e3
+        psi = tr[:, 0]["psi"]
+        e_psi = ess(psi)
+        ess_info = {"trajectories": M, "ess_psi": e_psi, "ess_per_s": e_psi / secs,
+                    "accept_rate": float(tr[:, 0]["accept"].mean()), "seconds": secs,
+                    "note": "Geyer initial-monotone ESS of the Psi trace after the warm-up and timed trajectories"}
+
+    # end to end through the public API: H2D of the chain state from pinned
+    # memory, set + refresh, one trajectory, D2H of the new state and trace
+    e2e = None
+    if not args.no_e2e:
+        g = state.get(0)
+        w_h = g["w"].cpu().pin_memory()
+        d_h = g["d"].cpu().pin_memory()
+        w_o = torch.empty_like(w_h).pin_memory()
+        d_o = torch.empty_like(d_h).pin_memory()
+        ne = min(args.steps, 30)
+        s_e = [torch.cuda.Event(enable_timing=True) for _ in range(ne)]
+        e_e = [torch.cuda.Event(enable_timing=True) for _ in range(ne)]
+        for k in range(ne):
+            torch.cuda.synchronize()
+            flush.zero_()
+            s_e[k].record(stream)
+            w_d = w_h.to(dev, non_blocking=True)
+            d_d = d_h.to(dev, non_blocking=True)
+            state.set(0, w=w_d, d=d_d)
+            state.refresh()
+            trk = state.run_chain(1, L, args.eps, use_graph=use_graph, trace=True)
+            gg = state.get(0)
+            w_o.copy_(gg["w"], non_blocking=True)
+            d_o.copy_(gg["d"], non_blocking=True)
+            e_e[k].record(stream)
+        torch.cuda.synchronize()
+        ms_e = float(np.mean([s.elapsed_time(e) for s, e in zip(s_e, e_e)]))
+        bi = w_h.numel() * w_h.element_size() + d_h.numel() * 8
+        bo = bi + 48
+        e2e = {"value": ws * L / (ms_e / 1e3), "unit": UNIT, "h2d_bytes_per_step": bi,
+               "d2h_bytes_per_step": bo, "ms_per_step": ms_e,
+               "note": "per step: pinned H2D of (w, d), hm_state_set + hm_state_refresh (one extra gradient "
+                       "evaluation, not counted), one trajectory, D2H of (w, d) and the trace record"}
+
+    # roofline of the dominant kernel (live CUDA-event times from the timed region)
+    N, n = spec.N, spec.n_points
+    ab = algorithmic_bytes(N, n)
+    total_k = sum(v[0] for v in prof.values())
+    dom = max(prof.items(), key=lambda kv: kv[1][0])
+    dname, (dms, dl) = dom
+    peaks, src = measured_peaks()
+    avg_s = dms / max(dl, 1) / 1e3
+    achieved = ab[dname] / avg_s / 1e9 if avg_s > 0 else None
+    peak = peaks.get("hbm_gbs", 6800.0)
+    kernels = {k: {"ms_total": v[0], "launches": v[1], "share": v[0] / total_k if total_k else None,
+                   "us_per_launch": 1e3 * v[0] / v[1] if v[1] else None,
+                   "gbs_algorithmic": (ab[k] / (v[0] / v[1] / 1e3) / 1e9) if v[1] and v[0] > 0 and ab[k] else None}
+               for k, v in prof.items()}
+    roofline = {"bound": "hbm", "kernel": dname, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak if achieved else None, "traffic": ncu_traffic(dname),
+                "algorithmic_bytes_per_launch": ab[dname], "peak_source": f"{src} hbm_gbs (copy bandwidth)"}
+
+    # CPU baseline: the oracle on a bounded sample, rank 0, N = 1 only
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        secs, nev = run_oracle_steps(6, args.eps)
+        cpu = {"value": nev / secs, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"{nev} oracle leapfrog steps (one gradient evaluation each) of this workload, "
+                         "numpy FP64, 1 thread"}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": max_ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": WORKLOAD, "grid": N, "box": spec.L, "points": n,
+                           "leapfrog_steps": L, "eps": args.eps, "chains_per_gpu": 1,
+                           "parallelism": f"replicas{ws}" if ws > 1 else "single",
+                           "l2": "flushed (512 MiB write) before every timed step",
+                           "graph": use_graph, "energy_dtype": "f64",
+                           "ms_per_step_unprofiled": ms_unprof},
+                "gpu_launches": int(sum(v[1] * KERNELS_PER_PAIR.get(k, 1) for k, v in prof.items())),
+                "clocks": clk, "roofline": roofline, "kernels": kernels, "ess": ess_info,
+                "e2e": e2e, "cpu_baseline": cpu, "wall_s_timed": t_wall}
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

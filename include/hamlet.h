@@ -189,6 +189,26 @@ int hm_leapfrog(hm_state* s, int32_t n_steps, double eps, int32_t sample_distanc
 int hm_run_chain(hm_state* s, int32_t n_traj, int32_t n_leapfrog, const double* eps_host,
                  int32_t sample_distances, int32_t use_graph, hm_trace* trace_host, void* stream);
 
+/* Per-kernel timing of hm_run_chain: with profiling enabled, every kernel
+ * launch of a trajectory is bracketed by a pair of CUDA events on the
+ * launching stream (recorded as graph nodes when the trajectory is
+ * replayed as a graph).  A run of several trajectories synchronises after
+ * each one to accumulate the elapsed times per kernel kind; a run of one
+ * trajectory returns without synchronising and leaves its events pending
+ * until hm_state_profile_collect (which synchronises the stream the
+ * trajectory ran on), the next run_chain or hm_state_profile_read.
+ * enable != 0 on a profiled state resets the totals; enable = 0 frees the
+ * events (and a trajectory graph captured with them).
+ * hm_state_profile_read fills ms_out[k] (total milliseconds) and
+ * launches_out[k] for k < min(max_kinds, *n_kinds); kind names come from
+ * hm_kernel_kind_name (empty string for an unknown kind).  Errors:
+ * HM_ESTATE when profiling is off. */
+int hm_state_profile(hm_state* s, int32_t enable);
+int hm_state_profile_collect(hm_state* s);
+int hm_state_profile_read(hm_state* s, int32_t max_kinds, double* ms_out, int64_t* launches_out,
+                          int32_t* n_kinds);
+const char* hm_kernel_kind_name(int32_t kind);
+
 /* Raw Philox-4x32-10 blocks for counters (q, c1, c2, c3), q = 0..n-1, key
  * seed: out_dev receives 4 n uint32 words. */
 int hm_philox(uint64_t seed, int64_t n, uint32_t c1, uint32_t c2, uint32_t c3, uint32_t* out_dev,

@@ -71,6 +71,78 @@ struct DevBuf {
 };
 
 // ---------------------------------------------------------------------------
+// per-kernel event timing of the trajectory launches (stream or graph)
+// ---------------------------------------------------------------------------
+enum KernelKind : int {
+  KK_R2C_FIELD = 0, KK_PENCIL_VEL, KK_C2R_VEL, KK_GATHER, KK_MEMSET, KK_SCATTER, KK_KICK_PTS,
+  KK_R2C_ADJ, KK_PENCIL_ADJ, KK_C2R_GRAD, KK_BEGIN, KK_FINALIZE, KK_RESTORE, KK_COUNT
+};
+static const char* kKindNames[KK_COUNT] = {
+    "plane_r2c_field", "pencil_velocity", "plane_c2r_velocity", "points_gather_likelihood",
+    "memset_scatter_grids", "points_scatter", "points_kick_drift", "plane_r2c_adjoint",
+    "pencil_adjoint", "plane_c2r_gradient_kick", "trajectory_begin", "finalize_energy",
+    "restore_rejected"};
+
+struct Prof {
+  std::vector<cudaEvent_t> ev;
+  std::vector<int> kind;
+  int idx = 0;
+  bool overflow = false;
+  double ms[KK_COUNT] = {0};
+  long long launches[KK_COUNT] = {0};
+  ~Prof() {
+    for (auto e : ev) cudaEventDestroy(e);
+  }
+  int reserve(int pairs) {
+    while ((int)ev.size() < 2 * pairs) {
+      cudaEvent_t e;
+      if (cudaEventCreate(&e) != cudaSuccess) return fail(HM_ECUDA, "cudaEventCreate failed");
+      ev.push_back(e);
+    }
+    kind.resize(pairs);
+    return HM_OK;
+  }
+  static cudaError_t rec(cudaEvent_t e, cudaStream_t st) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaStreamIsCapturing(st, &cs);
+    return cs == cudaStreamCaptureStatusActive ? cudaEventRecordWithFlags(e, st, cudaEventRecordExternal)
+                                                : cudaEventRecord(e, st);
+  }
+  cudaError_t begin(int k, cudaStream_t st) {
+    if (2 * idx + 1 >= (int)ev.size()) {
+      overflow = true;
+      return cudaSuccess;
+    }
+    kind[idx] = k;
+    return rec(ev[2 * idx], st);
+  }
+  cudaError_t end(cudaStream_t st) {
+    if (2 * idx + 1 >= (int)ev.size()) return cudaSuccess;
+    cudaError_t e = rec(ev[2 * idx + 1], st);
+    ++idx;
+    return e;
+  }
+  // after the recorded work has completed
+  int collect(int n_pairs) {
+    for (int i = 0; i < n_pairs; ++i) {
+      float t = 0.f;
+      cudaError_t e = cudaEventElapsedTime(&t, ev[2 * i], ev[2 * i + 1]);
+      if (e != cudaSuccess) return fail(HM_ECUDA, std::string("cudaEventElapsedTime: ") + cudaGetErrorString(e));
+      ms[kind[i]] += t;
+      launches[kind[i]] += 1;
+    }
+    return HM_OK;
+  }
+};
+
+#define HM_PROF(prof, k, st, call)                \
+  do {                                           \
+    if (prof) HM_CUDA((prof)->begin((k), (st))); \
+    HM_CUDA(call);                               \
+    if (prof) HM_CUDA((prof)->end((st)));        \
+  } while (0)
+
+// ---------------------------------------------------------------------------
 // linear power spectrum (Eisenstein & Hu 1998 no-wiggle), sigma8 and sigma_v
 // ---------------------------------------------------------------------------
 namespace {
@@ -153,10 +225,14 @@ struct hm_state {
   size_t trace_cap = 0;
   std::vector<PointParams> pp_host;
   std::vector<double> eps_host;
+  std::unique_ptr<Prof> prof;
+  int prof_pairs = 0;      // event pairs recorded by one trajectory
+  int prof_pending = 0;    // pairs recorded by the last single-trajectory run, not yet read
+  cudaStream_t prof_stream = nullptr;
   // captured trajectory graph
   cudaStream_t gstream = nullptr;
   cudaGraphExec_t gexec = nullptr;
-  int g_L = -1, g_sd = -1;
+  int g_L = -1, g_sd = -1, g_prof = 0;
   ~hm_state() {
     if (gexec) cudaGraphExecDestroy(gexec);
     if (gstream) cudaStreamDestroy(gstream);
@@ -219,24 +295,31 @@ struct GradArgs {
   int max_pts, pts_blocks;
   double *prior_part, *pts_part, *kinl_f, *kinl_p;
   ChainScal* cs;
+  Prof* prof;
 };
 
 static int grad_eval(const GradArgs& a, int mode, cudaStream_t st) {
   const size_t rsz = a.prec == HM_FP32 ? 4 : 8;
+  Prof* pf = a.prof;
   // forward: w -> w_k -> v_k (x, y, z) -> v grids
-  HM_CUDA(launch_plane_r2c(a.prec, a.N, a.w, a.n3, a.S1, a.nspec, a.C, a.tw, st));
-  HM_CUDA(launch_pencil(a.prec, a.N, PM_VEL, a.S1, a.nspec, a.S2, a.nspec, a.C, a.tw, a.amp, st));
-  HM_CUDA(launch_plane_c2r(a.prec, a.N, a.S2, a.nspec, a.V, a.n3, 3 * a.C, a.tw, nullptr, st));
+  HM_PROF(pf, KK_R2C_FIELD, st, launch_plane_r2c(a.prec, a.N, a.w, a.n3, a.S1, a.nspec, a.C, a.tw, st));
+  HM_PROF(pf, KK_PENCIL_VEL, st,
+          launch_pencil(a.prec, a.N, PM_VEL, a.S1, a.nspec, a.S2, a.nspec, a.C, a.tw, a.amp, st));
+  HM_PROF(pf, KK_C2R_VEL, st,
+          launch_plane_c2r(a.prec, a.N, a.S2, a.nspec, a.V, a.n3, 3 * a.C, a.tw, nullptr, st));
   // likelihood at the points, residuals and distance gradient
-  HM_CUDA(launch_points_gather(a.prec, a.C, a.max_pts, a.pp, a.pa, a.V, 3 * a.n3, a.pts_part,
-                               a.pts_blocks, a.cs, st));
+  HM_PROF(pf, KK_GATHER, st,
+          launch_points_gather(a.prec, a.C, a.max_pts, a.pp, a.pa, a.V, 3 * a.n3, a.pts_part, a.pts_blocks,
+                               a.cs, st));
   // adjoint: residuals -> CIC scatter into the v grids (reused) -> spectra
-  HM_CUDA(cudaMemsetAsync(a.V, 0, rsz * 3 * (size_t)a.n3 * a.C, st));
-  HM_CUDA(launch_points_scatter(a.prec, a.C, a.max_pts, a.pp, a.pa, a.V, 3 * a.n3, st));
+  HM_PROF(pf, KK_MEMSET, st, cudaMemsetAsync(a.V, 0, rsz * 3 * (size_t)a.n3 * a.C, st));
+  HM_PROF(pf, KK_SCATTER, st, launch_points_scatter(a.prec, a.C, a.max_pts, a.pp, a.pa, a.V, 3 * a.n3, st));
   if (mode != GM_GRAD)
-    HM_CUDA(launch_points_kick(a.C, a.max_pts, a.pp, a.pa, mode, a.kinl_p, a.pts_blocks, a.cs, nullptr, st));
-  HM_CUDA(launch_plane_r2c(a.prec, a.N, a.V, a.n3, a.S1, a.nspec, 3 * a.C, a.tw, st));
-  HM_CUDA(launch_pencil(a.prec, a.N, PM_ADJ, a.S1, a.nspec, a.S2, a.nspec, a.C, a.tw, a.amp, st));
+    HM_PROF(pf, KK_KICK_PTS, st,
+            launch_points_kick(a.C, a.max_pts, a.pp, a.pa, mode, a.kinl_p, a.pts_blocks, a.cs, nullptr, st));
+  HM_PROF(pf, KK_R2C_ADJ, st, launch_plane_r2c(a.prec, a.N, a.V, a.n3, a.S1, a.nspec, 3 * a.C, a.tw, st));
+  HM_PROF(pf, KK_PENCIL_ADJ, st,
+          launch_pencil(a.prec, a.N, PM_ADJ, a.S1, a.nspec, a.S2, a.nspec, a.C, a.tw, a.amp, st));
   FieldEpi epi{};
   epi.w = a.w;
   epi.pw = a.pw;
@@ -246,7 +329,7 @@ static int grad_eval(const GradArgs& a, int mode, cudaStream_t st) {
   epi.cs = a.cs;
   epi.grid_stride = a.n3;
   epi.mode = mode;
-  HM_CUDA(launch_plane_c2r(a.prec, a.N, a.S2, a.nspec, nullptr, 0, a.C, a.tw, &epi, st));
+  HM_PROF(pf, KK_C2R_GRAD, st, launch_plane_c2r(a.prec, a.N, a.S2, a.nspec, nullptr, 0, a.C, a.tw, &epi, st));
   return HM_OK;
 }
 
@@ -809,9 +892,11 @@ static int set_run(hm_state* s, const double* eps, int sample_d, cudaStream_t st
 
 // leapfrog body: first half kick + drift from the stored gradient, then
 // n_steps gradient evaluations with fused kick (+ drift)
-static int leapfrog_body(hm_state* s, int n_steps, int draw, cudaStream_t st) {
+static int leapfrog_body(hm_state* s, int n_steps, int draw, cudaStream_t st, Prof* pf) {
   GradArgs a = state_args(s);
+  a.prof = pf;
   PointArrays pa = a.pa;
+  if (pf) HM_CUDA(pf->begin(KK_BEGIN, st));
   HM_CUDA(launch_traj_begin_field(s->prec, s->C, s->n3, s->w.p, s->pw.p, s->gw.p, s->w0.p, s->gw0.p, s->seed,
                                   s->chain_id.as<int>(), s->kinb_f.as<double>(), s->nparts_f, draw, a.cs, st));
   if (s->max_pts > 0)
@@ -820,6 +905,7 @@ static int leapfrog_body(hm_state* s, int n_steps, int draw, cudaStream_t st) {
   HM_CUDA(launch_finalize(s->C, nullptr, 0, nullptr, 0, s->kinb_f.as<double>(), s->nparts_f,
                           s->kinb_p.as<double>(), s->max_pts > 0 ? s->nparts_p : 0, FIN_HOLD, s->seed,
                           s->chain_id.as<int>(), a.cs, nullptr, st));
+  if (pf) HM_CUDA(pf->end(st));
   for (int l = 1; l <= n_steps; ++l) HM_TRY(grad_eval(a, l < n_steps ? GM_KICK_DRIFT : GM_KICK_LAST, st));
   return HM_OK;
 }
@@ -831,7 +917,7 @@ int hm_leapfrog(hm_state* s, int32_t n_steps, double eps, int32_t sample_distanc
   HM_CUDA(cudaSetDevice(s->device));
   std::vector<double> e(s->C, eps);
   HM_TRY(set_run(s, e.data(), sample_distances, st));
-  HM_TRY(leapfrog_body(s, n_steps, 0, st));
+  HM_TRY(leapfrog_body(s, n_steps, 0, st, nullptr));
   GradArgs a = state_args(s);
   HM_CUDA(launch_finalize(s->C, a.prior_part, s->N, a.pts_part, s->pts_blocks, a.kinl_f, s->N, a.kinl_p,
                           s->max_pts > 0 ? s->pts_blocks : 0, FIN_PSI | FIN_KIN, s->seed, s->chain_id.as<int>(),
@@ -839,13 +925,23 @@ int hm_leapfrog(hm_state* s, int32_t n_steps, double eps, int32_t sample_distanc
   return HM_OK;
 }
 
-static int trajectory(hm_state* s, int n_leapfrog, cudaStream_t st) {
-  HM_TRY(leapfrog_body(s, n_leapfrog, 1, st));
+static int profile_collect(hm_state* s) {
+  if (!s->prof || s->prof_pending == 0) return HM_OK;
+  HM_CUDA(cudaStreamSynchronize(s->prof_stream));
+  const int n = s->prof_pending;
+  s->prof_pending = 0;
+  return s->prof->collect(n);
+}
+
+static int trajectory(hm_state* s, int n_leapfrog, cudaStream_t st, Prof* pf) {
+  HM_TRY(leapfrog_body(s, n_leapfrog, 1, st, pf));
   GradArgs a = state_args(s);
-  HM_CUDA(launch_finalize(s->C, a.prior_part, s->N, a.pts_part, s->pts_blocks, a.kinl_f, s->N, a.kinl_p,
+  HM_PROF(pf, KK_FINALIZE, st,
+          launch_finalize(s->C, a.prior_part, s->N, a.pts_part, s->pts_blocks, a.kinl_f, s->N, a.kinl_p,
                           s->max_pts > 0 ? s->pts_blocks : 0, FIN_PSI | FIN_ACCEPT, s->seed,
                           s->chain_id.as<int>(), a.cs, s->trace_dev.p, st));
-  HM_CUDA(launch_restore(s->prec, s->C, s->n3, s->w.p, s->gw.p, s->w0.p, s->gw0.p, s->max_pts, a.pp, a.pa,
+  HM_PROF(pf, KK_RESTORE, st,
+          launch_restore(s->prec, s->C, s->n3, s->w.p, s->gw.p, s->w0.p, s->gw0.p, s->max_pts, a.pp, a.pa,
                          s->d0.as<double>(), s->gd0.as<double>(), a.cs, st));
   return HM_OK;
 }
@@ -866,18 +962,41 @@ int hm_run_chain(hm_state* s, int32_t n_traj, int32_t n_leapfrog, const double* 
     }
   }
   HM_TRY(set_run(s, eps_host, sample_distances, st));
+  Prof* pf = s->prof.get();
+  if (pf) {
+    HM_TRY(profile_collect(s));
+    HM_TRY(pf->reserve(12 * n_leapfrog + 8));
+    pf->idx = 0;
+  }
+  // With profiling, a single-trajectory call leaves its events pending (read
+  // by hm_state_profile_collect after the caller synchronises); longer runs
+  // synchronise after every trajectory to read them before they are reused.
   if (!use_graph) {
-    for (int t = 0; t < n_traj; ++t) HM_TRY(trajectory(s, n_leapfrog, st));
+    for (int t = 0; t < n_traj; ++t) {
+      if (pf) pf->idx = 0;
+      HM_TRY(trajectory(s, n_leapfrog, st, pf));
+      if (pf) {
+        if (n_traj == 1) {
+          s->prof_pending = pf->idx;
+          s->prof_stream = st;
+        } else {
+          HM_CUDA(cudaStreamSynchronize(st));
+          HM_TRY(pf->collect(pf->idx));
+        }
+      }
+    }
   } else if (n_traj > 0) {
     if (!s->gstream) HM_CUDA(cudaStreamCreateWithFlags(&s->gstream, cudaStreamNonBlocking));
-    if (!s->gexec || s->g_L != n_leapfrog || s->g_sd != sample_distances) {
+    const int want_prof = pf ? 1 : 0;
+    if (!s->gexec || s->g_L != n_leapfrog || s->g_sd != sample_distances || s->g_prof != want_prof) {
       if (s->gexec) {
         cudaGraphExecDestroy(s->gexec);
         s->gexec = nullptr;
       }
       cudaGraph_t g = nullptr;
+      if (pf) pf->idx = 0;
       HM_CUDA(cudaStreamBeginCapture(s->gstream, cudaStreamCaptureModeThreadLocal));
-      int rc = trajectory(s, n_leapfrog, s->gstream);
+      int rc = trajectory(s, n_leapfrog, s->gstream, pf);
       cudaError_t ce = cudaStreamEndCapture(s->gstream, &g);
       if (rc != HM_OK) {
         if (g) cudaGraphDestroy(g);
@@ -889,12 +1008,25 @@ int hm_run_chain(hm_state* s, int32_t n_traj, int32_t n_leapfrog, const double* 
       if (ce != cudaSuccess) return fail(HM_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(ce));
       s->g_L = n_leapfrog;
       s->g_sd = sample_distances;
+      s->g_prof = want_prof;
+      if (pf) s->prof_pairs = pf->idx;
     }
     cudaEvent_t ev;
     HM_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
     HM_CUDA(cudaEventRecord(ev, st));
     HM_CUDA(cudaStreamWaitEvent(s->gstream, ev, 0));
-    for (int t = 0; t < n_traj; ++t) HM_CUDA(cudaGraphLaunch(s->gexec, s->gstream));
+    for (int t = 0; t < n_traj; ++t) {
+      HM_CUDA(cudaGraphLaunch(s->gexec, s->gstream));
+      if (pf) {
+        if (n_traj == 1) {
+          s->prof_pending = s->prof_pairs;
+          s->prof_stream = s->gstream;
+        } else {
+          HM_CUDA(cudaStreamSynchronize(s->gstream));
+          HM_TRY(pf->collect(s->prof_pairs));
+        }
+      }
+    }
     HM_CUDA(cudaEventRecord(ev, s->gstream));
     HM_CUDA(cudaStreamWaitEvent(st, ev, 0));
     HM_CUDA(cudaEventDestroy(ev));
@@ -905,6 +1037,51 @@ int hm_run_chain(hm_state* s, int32_t n_traj, int32_t n_leapfrog, const double* 
     HM_CUDA(cudaStreamSynchronize(st));
   }
   return HM_OK;
+}
+
+int hm_state_profile(hm_state* s, int32_t enable) {
+  if (!s) return fail(HM_EINVAL, "null state");
+  HM_CUDA(cudaSetDevice(s->device));
+  if (enable) {
+    if (!s->prof) s->prof = std::make_unique<Prof>();
+    for (int k = 0; k < KK_COUNT; ++k) {
+      s->prof->ms[k] = 0.0;
+      s->prof->launches[k] = 0;
+    }
+  } else {
+    HM_TRY(profile_collect(s));
+    // a graph captured with profiling holds these events: drop it first
+    if (s->gexec && s->g_prof) {
+      cudaGraphExecDestroy(s->gexec);
+      s->gexec = nullptr;
+    }
+    s->prof.reset();
+  }
+  return HM_OK;
+}
+
+int hm_state_profile_collect(hm_state* s) {
+  if (!s) return fail(HM_EINVAL, "null state");
+  HM_CUDA(cudaSetDevice(s->device));
+  return profile_collect(s);
+}
+
+int hm_state_profile_read(hm_state* s, int32_t max_kinds, double* ms_out, int64_t* launches_out, int32_t* n_kinds) {
+  if (!s) return fail(HM_EINVAL, "null state");
+  if (n_kinds) *n_kinds = KK_COUNT;
+  if (!s->prof) return fail(HM_ESTATE, "profiling is not enabled on this state");
+  HM_CUDA(cudaSetDevice(s->device));
+  HM_TRY(profile_collect(s));
+  for (int k = 0; k < KK_COUNT && k < max_kinds; ++k) {
+    if (ms_out) ms_out[k] = s->prof->ms[k];
+    if (launches_out) launches_out[k] = s->prof->launches[k];
+  }
+  return HM_OK;
+}
+
+const char* hm_kernel_kind_name(int32_t kind) {
+  if (kind < 0 || kind >= KK_COUNT) return "";
+  return kKindNames[kind];
 }
 
 }  // extern "C"

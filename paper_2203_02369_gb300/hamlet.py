@@ -241,6 +241,20 @@ class State:
     def set_traj(self, chain, traj):
         check(self.lib.hm_state_set_traj(self.h, chain, int(traj)))
 
+    def profile(self, enable=True):
+        check(self.lib.hm_state_profile(self.h, int(bool(enable))))
+
+    def profile_collect(self):
+        check(self.lib.hm_state_profile_collect(self.h))
+
+    def profile_read(self):
+        """{kernel kind: (total ms, launches)} accumulated by run_chain."""
+        nk = ct.c_int32()
+        ms = (ct.c_double * 64)()
+        ln = (ct.c_int64 * 64)()
+        check(self.lib.hm_state_profile_read(self.h, 64, ms, ln, ct.byref(nk)))
+        return {self.lib.hm_kernel_kind_name(k).decode(): (ms[k], ln[k]) for k in range(nk.value)}
+
     def leapfrog(self, n_steps, eps, sample_distances=True):
         check(self.lib.hm_leapfrog(self.h, int(n_steps), float(eps), int(bool(sample_distances)), _stream()))
 
