@@ -62,7 +62,9 @@ typedef struct hm_problem_desc {
   double omega_m, omega_b, h, n_s, sigma8, T_cmb; /* P(k): Eisenstein-Hu no-wiggle */
   double f_growth;       /* linear growth rate; <= 0 means omega_m^0.55 */
   double sigma_nl;       /* non-linear velocity dispersion sigma_NL, km/s (eq. kappa) */
-  /* HM_PRIOR_TABLE: ln pi_D(d) = prior_logdens[floor((d - d0)/bin)], -inf outside */
+  /* HM_PRIOR_TABLE: eq. D's histogram as ln pi_D at the bin centres
+   * d0 + (b + 1/2) bin, interpolated linearly between centres (flat in the
+   * outer half bins); support [d0, d0 + nbins * bin), -inf outside */
   double prior_d0, prior_bin;
   int32_t prior_nbins;
   int32_t pad0;

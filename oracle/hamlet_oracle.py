@@ -25,7 +25,10 @@ Readings of points the paper leaves open (each one is listed in the design doc):
     observer sits at the box centre; a point on a face belongs to the upper cell.
   * mu(d) = 5 log10(d (1+zbar)/h) + 25 with d in Mpc/h; zbar is the
     second-order relation of section "The Likelihood function: distances".
-  * The distance prior (eq. D) is a caller-given histogram table or a power law.
+  * The distance prior (eq. D) is a caller-given histogram table or a power law;
+    the table's ln pi is interpolated linearly between bin centres (a
+    piecewise-constant histogram puts a jump in H at every bin crossing that
+    the leapfrog cannot see).
   * Psi omits every additive constant independent of (w, d).
   * Leapfrog is kick-drift-kick with merged half kicks; Metropolis accepts iff
     ln U < H_old - H_new with U in (0, 1].
@@ -423,16 +426,30 @@ def cic_scatter(prob, values, cell, frac):
 # Distance prior (eq. D).
 # ----------------------------------------------------------------------------
 def log_prior_d(prob, d):
-    """ln pi_D(d) and its derivative; -inf outside the support."""
+    """ln pi_D(d) and its derivative; -inf outside the support.
+
+    "table": the histogram of eq. D, read as ln pi given at the bin centres
+    d0 + (b + 1/2) bin and interpolated linearly between them (flat in the
+    outer half bins), so that the potential is continuous in d; the support
+    is [d0, d0 + nbins * bin).  "power": ln pi = alpha ln d on [dmin, dmax].
+    """
     kind = prob.prior[0]
     if kind == "table":
         _, d0, bw, logdens = prob.prior
         logdens = np.asarray(logdens, float)
-        b = np.floor((d - d0) / bw)
-        ok = (b >= 0) & (b < logdens.shape[0])
-        lp = np.full(d.shape, -np.inf)
-        lp[ok] = logdens[b[ok].astype(np.int64)]
-        return lp, np.zeros(d.shape)
+        nb = logdens.shape[0]
+        ok = (d >= d0) & (d < d0 + nb * bw)
+        t = (d - d0) / bw - 0.5
+        b = np.floor(t)
+        f = t - b
+        lo = np.clip(b, 0, nb - 1).astype(np.int64)
+        hi = np.clip(b + 1, 0, nb - 1).astype(np.int64)
+        inner = (b >= 0) & (b < nb - 1)
+        lp = np.where(inner, (1.0 - f) * logdens[lo] + f * logdens[hi], logdens[np.where(b < 0, 0, nb - 1)])
+        dl = np.where(inner, (logdens[hi] - logdens[lo]) / bw, 0.0)
+        lp = np.where(ok, lp, -np.inf)
+        dl = np.where(ok, dl, 0.0)
+        return lp, dl
     if kind == "power":
         _, alpha, dmin, dmax = prob.prior
         ok = (d >= dmin) & (d <= dmax)

@@ -37,13 +37,29 @@ __device__ __forceinline__ CellPos cell_of(const PointParams& P, double d, doubl
   return c;
 }
 
-// ln pi_D(d) and its derivative; returns false outside the support.
+// ln pi_D(d) and its derivative; returns false outside the support.  The
+// table (eq. D's histogram) gives ln pi at the bin centres d0 + (b + 1/2) bin,
+// interpolated linearly in between and flat in the outer half bins, so the
+// potential stays continuous across bins.
 __device__ __forceinline__ bool log_prior(const PointParams& P, double d, double& lp, double& dlp) {
   if (P.prior_kind == PRIOR_TABLE) {
-    const double b = floor((d - P.prior_d0) / P.prior_bin);
-    if (!(b >= 0.0 && b < (double)P.prior_nbins)) return false;
-    lp = P.prior_logdens[(int)b];
-    dlp = 0.0;
+    const int nb = P.prior_nbins;
+    if (!(d >= P.prior_d0 && d < P.prior_d0 + nb * P.prior_bin)) return false;
+    const double t = (d - P.prior_d0) / P.prior_bin - 0.5;
+    const double b = floor(t);
+    const double f = t - b;
+    if (b < 0.0) {
+      lp = P.prior_logdens[0];
+      dlp = 0.0;
+    } else if (b >= (double)(nb - 1)) {
+      lp = P.prior_logdens[nb - 1];
+      dlp = 0.0;
+    } else {
+      const int ib = (int)b;
+      const double a0 = P.prior_logdens[ib], a1 = P.prior_logdens[ib + 1];
+      lp = (1.0 - f) * a0 + f * a1;
+      dlp = (a1 - a0) / P.prior_bin;
+    }
     return true;
   }
   if (!(d >= P.prior_dmin && d <= P.prior_dmax)) return false;

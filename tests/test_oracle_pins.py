@@ -324,15 +324,39 @@ def test_gradient_central_differences():
         assert abs(fd - gd[i]) < 1e-5 * max(1.0, abs(gd[i]))
 
 
-def test_table_prior_lookup_and_zero_gradient():
+def test_table_prior_interpolation():
     logdens = np.log(np.array([0.1, 0.3, 0.2, 0.4]))
     p, _ = tiny_problem(N=8, L=80.0, n=4, prior=("table", 5.0, 10.0, logdens))
-    d = np.array([5.0, 14.999, 30.0, 44.9])
-    lp, dl = O.log_prior_d(p, d)
-    assert np.array_equal(lp, logdens[[0, 0, 2, 3]])
-    assert np.all(dl == 0)
+    # bin centres return the table values exactly; outer half bins are flat
+    c = 5.0 + 10.0 * (np.arange(4) + 0.5)
+    lp, dl = O.log_prior_d(p, c)
+    assert np.array_equal(lp, logdens)
+    lp, dl = O.log_prior_d(p, np.array([5.0, 44.999]))
+    assert lp[0] == logdens[0] and lp[1] == logdens[3] and np.all(dl == 0)
+    # linear in between with the slope as derivative; continuous across centres
+    x = np.array([12.5, 20.0, 27.5])
+    lp, dl = O.log_prior_d(p, x)
+    assert abs(lp[0] - 0.75 * logdens[0] - 0.25 * logdens[1]) < 1e-15
+    assert abs(lp[1] - logdens[1]) < 1e-15
+    assert abs(lp[2] - 0.25 * logdens[1] - 0.75 * logdens[2]) < 1e-15
+    assert abs(dl[0] - (logdens[1] - logdens[0]) / 10.0) < 1e-15
+    eps = 1e-9
+    for cc in c[1:3]:
+        a, _ = O.log_prior_d(p, np.array([cc - eps, cc + eps]))
+        assert abs(a[1] - a[0]) < 1e-8
     lp2, _ = O.log_prior_d(p, np.array([4.9, 45.0]))
     assert np.all(np.isneginf(lp2))
+
+
+def test_table_prior_gradient_central_differences():
+    rng = np.random.default_rng(4)
+    logdens = np.log(rng.uniform(0.1, 1.0, 12))
+    p, _ = tiny_problem(N=8, L=80.0, n=6, prior=("table", 0.0, 4.0, logdens))
+    d = np.array([3.1, 7.7, 13.3, 22.9, 31.7, 41.2])
+    lp, dl = O.log_prior_d(p, d)
+    h = 1e-6
+    fd = (O.log_prior_d(p, d + h)[0] - O.log_prior_d(p, d - h)[0]) / (2 * h)
+    assert np.max(np.abs(fd - dl)) < 1e-7
 
 
 def test_out_of_domain_is_infinite():
