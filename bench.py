@@ -119,19 +119,23 @@ class Clocks:
 # algorithmic bytes per launch of each kernel kind (FP32, one chain)
 # --------------------------------------------------------------------------
 def algorithmic_bytes(N, n, C=1, rsz=4):
+    """Bytes each kernel kind must move per launch if every array it touches
+    is read or written once: R = one real N^3 grid, S = one half spectrum,
+    plus the per-point records (32 B), partials and catalogue fields."""
     R = rsz * N ** 3
     S = 2 * rsz * N * N * (N // 2 + 1)
     return {
         "plane_r2c_field": C * (R + S),
         "pencil_velocity": C * (S + 3 * S),
-        "plane_c2r_velocity": 3 * C * (S + R),
-        "points_gather_likelihood": C * n * 188,
-        "memset_scatter_grids": 3 * C * R,
-        "points_scatter": C * n * 236,
-        "points_kick_drift": C * n * 40,
-        "plane_r2c_adjoint": 3 * C * (R + S),
+        "plane_c2r_velocity_gather": C * (3 * S + 3 * 2 * n * (32 + 8)),
+        "memset_bucket_counts": 0,
+        "points_bucket_count": C * n * 24,
+        "points_bucket_place": C * n * 72,
+        "points_likelihood": C * n * 104,
+        "plane_r2c_scatter_adjoint": C * (3 * S + 3 * 2 * n * 32),
         "pencil_adjoint": C * (3 * S + S),
         "plane_c2r_gradient_kick": C * (S + 4 * R),
+        "points_kick_drift": C * n * 40,
         "trajectory_begin": C * (6 * R + 56 * n),
         "finalize_energy": 0,
         "restore_rejected": 0,
@@ -139,7 +143,7 @@ def algorithmic_bytes(N, n, C=1, rsz=4):
 
 
 # kernels launched inside one profiled pair of events
-KERNELS_PER_PAIR = {"memset_scatter_grids": 0, "trajectory_begin": 3, "restore_rejected": 2}
+KERNELS_PER_PAIR = {"memset_bucket_counts": 0, "trajectory_begin": 3, "restore_rejected": 2}
 
 
 def measured_peaks():

@@ -74,13 +74,14 @@ struct DevBuf {
 // per-kernel event timing of the trajectory launches (stream or graph)
 // ---------------------------------------------------------------------------
 enum KernelKind : int {
-  KK_R2C_FIELD = 0, KK_PENCIL_VEL, KK_C2R_VEL, KK_GATHER, KK_MEMSET, KK_SCATTER, KK_KICK_PTS,
-  KK_R2C_ADJ, KK_PENCIL_ADJ, KK_C2R_GRAD, KK_BEGIN, KK_FINALIZE, KK_RESTORE, KK_COUNT
+  KK_R2C_FIELD = 0, KK_PENCIL_VEL, KK_C2R_GATHER, KK_MEMSET_CNT, KK_PREP, KK_PLACE, KK_LIK,
+  KK_R2C_SCATTER, KK_PENCIL_ADJ, KK_C2R_GRAD, KK_KICK_PTS, KK_BEGIN, KK_FINALIZE, KK_RESTORE, KK_COUNT
 };
 static const char* kKindNames[KK_COUNT] = {
-    "plane_r2c_field", "pencil_velocity", "plane_c2r_velocity", "points_gather_likelihood",
-    "memset_scatter_grids", "points_scatter", "points_kick_drift", "plane_r2c_adjoint",
-    "pencil_adjoint", "plane_c2r_gradient_kick", "trajectory_begin", "finalize_energy",
+    "plane_r2c_field", "pencil_velocity", "plane_c2r_velocity_gather", "memset_bucket_counts",
+    "points_bucket_count",
+    "points_bucket_place", "points_likelihood", "plane_r2c_scatter_adjoint", "pencil_adjoint",
+    "plane_c2r_gradient_kick", "points_kick_drift", "trajectory_begin", "finalize_energy",
     "restore_rejected"};
 
 struct Prof {
@@ -192,6 +193,49 @@ double tophat(double x) { return 3.0 * (std::sin(x) - x * std::cos(x)) / (x * x 
 // ---------------------------------------------------------------------------
 // objects
 // ---------------------------------------------------------------------------
+// Per-evaluation point workspace (bucketing, records, partials) and the
+// side stream on which the bucketing overlaps the first FFT passes.
+struct PtWork {
+  DevBuf cx, slot, pos, cnt, off, rec, part;
+  cudaStream_t aux = nullptr;
+  cudaEvent_t fork = nullptr, join = nullptr;
+  ~PtWork() {
+    if (fork) cudaEventDestroy(fork);
+    if (join) cudaEventDestroy(join);
+    if (aux) cudaStreamDestroy(aux);
+  }
+  int alloc(int prec, int C, int N, long long ntot) {
+    const size_t nt = (size_t)std::max<long long>(ntot, 1);
+    const size_t rsz = prec == HM_FP32 ? 4 : 8;
+    const size_t recsz = prec == HM_FP32 ? sizeof(PtRec<float>) : sizeof(PtRec<double>);
+    HM_TRY(cx.alloc(4 * nt));
+    HM_TRY(slot.alloc(4 * nt));
+    HM_TRY(pos.alloc(4 * nt));
+    HM_TRY(cnt.alloc(4 * (size_t)C * N));
+    HM_TRY(off.alloc(4 * (size_t)C * (N + 1)));
+    HM_TRY(rec.alloc(recsz * nt));
+    HM_TRY(part.alloc(rsz * 12 * nt));
+    if (cudaMemset(cnt.p, 0, 4 * (size_t)C * N) != cudaSuccess) return fail(HM_ECUDA, "cudaMemset failed");
+    if (!aux) {
+      if (cudaStreamCreateWithFlags(&aux, cudaStreamNonBlocking) != cudaSuccess ||
+          cudaEventCreateWithFlags(&fork, cudaEventDisableTiming) != cudaSuccess ||
+          cudaEventCreateWithFlags(&join, cudaEventDisableTiming) != cudaSuccess)
+        return fail(HM_ECUDA, "stream/event creation failed");
+    }
+    return HM_OK;
+  }
+  void fill(PointArrays& pa, long long ntot) const {
+    pa.cx = cx.as<int>();
+    pa.slot = slot.as<int>();
+    pa.pos = pos.as<int>();
+    pa.cnt = cnt.as<int>();
+    pa.off = off.as<int>();
+    pa.rec = rec.p;
+    pa.part = part.p;
+    pa.ntot = ntot;
+  }
+};
+
 struct hm_problem {
   hm_problem_desc desc{};
   int N = 0, prec = 0, device = 0;
@@ -205,7 +249,8 @@ struct hm_problem {
   long long n = 0;
   DevBuf rx, ry, rz, mu, smu, zobs, scz;
   // standalone workspace (one chain)
-  DevBuf S1, S2, V, r, cell, frac, hist, prior_part, pts_part, kin_part, pp, cs, chain_id;
+  DevBuf S1, S2, hist, prior_part, pts_part, kin_part, pp, cs, chain_id;
+  PtWork pw;
   long long ws_points = -1;
 };
 
@@ -218,8 +263,9 @@ struct hm_state {
   size_t rsz = 4;
   hm_problem* p0 = nullptr;       // problem providing the tables (same N, prec)
   std::vector<hm_problem*> chain_prob;
-  DevBuf w, pw, gw, w0, gw0, S1, S2, V;
-  DevBuf rx, ry, rz, mu, smu, zobs, scz, d, pd, gd, d0, gd0, r, cell, frac;
+  DevBuf w, pw, gw, w0, gw0, S1, S2;
+  DevBuf rx, ry, rz, mu, smu, zobs, scz, d, pd, gd, d0, gd0;
+  PtWork work;
   DevBuf prior_part, pts_part, kinb_f, kinb_p, kinl_f, kinl_p;
   DevBuf pp, cs, chain_id, eps_dev, trace_dev;
   size_t trace_cap = 0;
@@ -251,10 +297,7 @@ static PointArrays point_arrays(hm_state* s) {
   pa.d = s->d.as<double>();
   pa.pd = s->pd.as<double>();
   pa.gd = s->gd.as<double>();
-  pa.r = s->r.p;
-  pa.cell = s->cell.as<int>();
-  pa.frac = s->frac.p;
-  pa.ntot = s->ntot;
+  s->work.fill(pa, s->ntot);
   return pa;
 }
 
@@ -286,38 +329,55 @@ static PointParams point_params(const hm_problem* p, long long off) {
 struct GradArgs {
   int prec, N, C;
   long long n3, nspec;
+  double delta;
   const void* tw;
   const void* amp;
   void *w, *pw, *gw;
-  void *S1, *S2, *V;
+  void *S1, *S2;
   PointArrays pa;
   const PointParams* pp;
   int max_pts, pts_blocks;
   double *prior_part, *pts_part, *kinl_f, *kinl_p;
   ChainScal* cs;
+  const PtWork* work;
   Prof* prof;
 };
 
+// One gradient evaluation of C chains at their current (w, d):
+//   side stream : bucket count, bucket placement of the points   (x-planes)
+//   main stream : w -> w_k (planes, then x pencils with the velocity
+//                 weights) -> per-plane inverse with the CIC gather -> FP64
+//                 likelihood -> per-plane CIC scatter + forward -> x pencils
+//                 with the adjoint weights -> per-plane inverse with the
+//                 gradient / leapfrog epilogue -> distance kick/drift.
 static int grad_eval(const GradArgs& a, int mode, cudaStream_t st) {
-  const size_t rsz = a.prec == HM_FP32 ? 4 : 8;
   Prof* pf = a.prof;
-  // forward: w -> w_k -> v_k (x, y, z) -> v grids
+  const PtWork& wk = *a.work;
+  cudaStream_t ax = wk.aux;
+  PlanePoints pts{};
+  pts.off = a.pa.off;
+  pts.rec = a.pa.rec;
+  pts.part = a.pa.part;
+  pts.ntot = a.pa.ntot;
+  pts.inv_delta = 1.0 / a.delta;
+  // fork: bucketing of the points on the side stream
+  HM_CUDA(cudaEventRecord(wk.fork, st));
+  HM_CUDA(cudaStreamWaitEvent(ax, wk.fork, 0));
+  HM_PROF(pf, KK_MEMSET_CNT, ax, cudaMemsetAsync(a.pa.cnt, 0, sizeof(int) * (size_t)a.C * a.N, ax));
+  HM_PROF(pf, KK_PREP, ax, launch_points_prep(a.C, a.max_pts, a.pp, a.pa, ax));
+  HM_PROF(pf, KK_PLACE, ax, launch_points_place(a.prec, a.C, a.max_pts, a.pp, a.pa, ax));
+  HM_CUDA(cudaEventRecord(wk.join, ax));
+  // forward field operator
   HM_PROF(pf, KK_R2C_FIELD, st, launch_plane_r2c(a.prec, a.N, a.w, a.n3, a.S1, a.nspec, a.C, a.tw, st));
   HM_PROF(pf, KK_PENCIL_VEL, st,
           launch_pencil(a.prec, a.N, PM_VEL, a.S1, a.nspec, a.S2, a.nspec, a.C, a.tw, a.amp, st));
-  HM_PROF(pf, KK_C2R_VEL, st,
-          launch_plane_c2r(a.prec, a.N, a.S2, a.nspec, a.V, a.n3, 3 * a.C, a.tw, nullptr, st));
-  // likelihood at the points, residuals and distance gradient
-  HM_PROF(pf, KK_GATHER, st,
-          launch_points_gather(a.prec, a.C, a.max_pts, a.pp, a.pa, a.V, 3 * a.n3, a.pts_part, a.pts_blocks,
-                               a.cs, st));
-  // adjoint: residuals -> CIC scatter into the v grids (reused) -> spectra
-  HM_PROF(pf, KK_MEMSET, st, cudaMemsetAsync(a.V, 0, rsz * 3 * (size_t)a.n3 * a.C, st));
-  HM_PROF(pf, KK_SCATTER, st, launch_points_scatter(a.prec, a.C, a.max_pts, a.pp, a.pa, a.V, 3 * a.n3, st));
-  if (mode != GM_GRAD)
-    HM_PROF(pf, KK_KICK_PTS, st,
-            launch_points_kick(a.C, a.max_pts, a.pp, a.pa, mode, a.kinl_p, a.pts_blocks, a.cs, nullptr, st));
-  HM_PROF(pf, KK_R2C_ADJ, st, launch_plane_r2c(a.prec, a.N, a.V, a.n3, a.S1, a.nspec, 3 * a.C, a.tw, st));
+  // join, then velocity planes with the CIC gather at the points
+  HM_CUDA(cudaStreamWaitEvent(st, wk.join, 0));
+  HM_PROF(pf, KK_C2R_GATHER, st, launch_plane_c2r_gather(a.prec, a.N, a.S2, a.nspec, pts, 3 * a.C, a.tw, st));
+  HM_PROF(pf, KK_LIK, st,
+          launch_points_lik(a.prec, a.C, a.max_pts, a.pp, a.pa, a.pts_part, a.pts_blocks, a.cs, st));
+  // adjoint: residuals scattered plane by plane, forward transform, weights
+  HM_PROF(pf, KK_R2C_SCATTER, st, launch_plane_r2c_scatter(a.prec, a.N, pts, a.S1, a.nspec, 3 * a.C, a.tw, st));
   HM_PROF(pf, KK_PENCIL_ADJ, st,
           launch_pencil(a.prec, a.N, PM_ADJ, a.S1, a.nspec, a.S2, a.nspec, a.C, a.tw, a.amp, st));
   FieldEpi epi{};
@@ -330,6 +390,9 @@ static int grad_eval(const GradArgs& a, int mode, cudaStream_t st) {
   epi.grid_stride = a.n3;
   epi.mode = mode;
   HM_PROF(pf, KK_C2R_GRAD, st, launch_plane_c2r(a.prec, a.N, a.S2, a.nspec, nullptr, 0, a.C, a.tw, &epi, st));
+  if (mode != GM_GRAD && a.max_pts > 0)
+    HM_PROF(pf, KK_KICK_PTS, st,
+            launch_points_kick(a.C, a.max_pts, a.pp, a.pa, mode, a.kinl_p, a.pts_blocks, a.cs, st));
   return HM_OK;
 }
 
@@ -499,12 +562,9 @@ static int ensure_ws(hm_problem* p) {
   const int N = p->N;
   HM_TRY(p->S1.alloc(2 * p->rsz * 3 * p->nspec));
   HM_TRY(p->S2.alloc(2 * p->rsz * 3 * p->nspec));
-  HM_TRY(p->V.alloc(p->rsz * 3 * p->n3));
-  HM_TRY(p->r.alloc(p->rsz * std::max<long long>(p->n, 1)));
-  HM_TRY(p->cell.alloc(4 * std::max<long long>(p->n, 1)));
-  HM_TRY(p->frac.alloc(p->rsz * 3 * std::max<long long>(p->n, 1)));
+  HM_TRY(p->pw.alloc(p->prec, 1, N, p->n));
   HM_TRY(p->prior_part.alloc(8 * N));
-  const int pb = (int)std::max<long long>(1, (p->n + 255) / 256);
+  const int pb = points_blocks((int)p->n);
   HM_TRY(p->pts_part.alloc(8 * pb));
   HM_TRY(p->kin_part.alloc(8 * std::max(N, pb)));
   HM_TRY(p->pp.alloc(sizeof(PointParams)));
@@ -539,10 +599,7 @@ int hm_logpost_grad(hm_problem* p, const void* w_dev, const double* d_dev, doubl
   pa.d = const_cast<double*>(d_dev);
   pa.pd = nullptr;
   pa.gd = grad_d_dev;
-  pa.r = p->r.p;
-  pa.cell = p->cell.as<int>();
-  pa.frac = p->frac.p;
-  pa.ntot = p->n;
+  p->pw.fill(pa, p->n);
   ChainScal* cs = p->cs.as<ChainScal>();
   HM_CUDA(cudaMemsetAsync(&cs->status, 0, sizeof(int), st));
   GradArgs a{};
@@ -551,6 +608,7 @@ int hm_logpost_grad(hm_problem* p, const void* w_dev, const double* d_dev, doubl
   a.C = 1;
   a.n3 = p->n3;
   a.nspec = p->nspec;
+  a.delta = p->delta;
   a.tw = p->tw.p;
   a.amp = p->amp.p;
   a.w = const_cast<void*>(w_dev);
@@ -558,16 +616,16 @@ int hm_logpost_grad(hm_problem* p, const void* w_dev, const double* d_dev, doubl
   a.gw = grad_w_dev;
   a.S1 = p->S1.p;
   a.S2 = p->S2.p;
-  a.V = p->V.p;
   a.pa = pa;
   a.pp = p->pp.as<PointParams>();
   a.max_pts = (int)p->n;
-  a.pts_blocks = (int)std::max<long long>(1, (p->n + 255) / 256);
+  a.pts_blocks = points_blocks((int)p->n);
   a.prior_part = p->prior_part.as<double>();
   a.pts_part = p->pts_part.as<double>();
   a.kinl_f = p->kin_part.as<double>();
   a.kinl_p = p->kin_part.as<double>();
   a.cs = cs;
+  a.work = &p->pw;
   HM_TRY(grad_eval(a, GM_GRAD, st));
   HM_CUDA(launch_finalize(1, a.prior_part, p->N, a.pts_part, a.pts_blocks, nullptr, 0, nullptr, 0, FIN_PSI,
                           0ull, p->chain_id.as<int>(), cs, nullptr, st));
@@ -661,6 +719,7 @@ static GradArgs state_args(hm_state* s) {
   a.C = s->C;
   a.n3 = s->n3;
   a.nspec = s->nspec;
+  a.delta = s->p0->delta;
   a.tw = s->p0->tw.p;
   a.amp = s->p0->amp.p;
   a.w = s->w.p;
@@ -668,7 +727,6 @@ static GradArgs state_args(hm_state* s) {
   a.gw = s->gw.p;
   a.S1 = s->S1.p;
   a.S2 = s->S2.p;
-  a.V = s->V.p;
   a.pa = point_arrays(s);
   a.pp = s->pp.as<PointParams>();
   a.max_pts = s->max_pts;
@@ -678,6 +736,7 @@ static GradArgs state_args(hm_state* s) {
   a.kinl_f = s->kinl_f.as<double>();
   a.kinl_p = s->kinl_p.as<double>();
   a.cs = s->cs.as<ChainScal>();
+  a.work = &s->work;
   return a;
 }
 
@@ -728,7 +787,7 @@ int hm_state_create_batch(hm_problem* const* problems, int32_t n_problems, int32
   }
   s->ntot = tot;
   s->max_pts = maxp;
-  s->pts_blocks = std::max(1, (maxp + 255) / 256);
+  s->pts_blocks = points_blocks(maxp);
   s->nparts_f = (int)std::min<long long>(256, std::max<long long>(1, (s->n3 / 2 + 255) / 256));
   s->nparts_p = std::max(1, std::min(64, (maxp / 2 + 255) / 256));
   const size_t C = n_chains, rs = s->rsz;
@@ -737,7 +796,6 @@ int hm_state_create_batch(hm_problem* const* problems, int32_t n_problems, int32
   HM_TRY(s->gw.alloc(rs * C * s->n3));
   HM_TRY(s->w0.alloc(rs * C * s->n3));
   HM_TRY(s->gw0.alloc(rs * C * s->n3));
-  HM_TRY(s->V.alloc(rs * 3 * C * s->n3));
   HM_TRY(s->S1.alloc(2 * rs * 3 * C * s->nspec));
   HM_TRY(s->S2.alloc(2 * rs * 3 * C * s->nspec));
   HM_CUDA(cudaMemset(s->w.p, 0, rs * C * s->n3));
@@ -746,9 +804,7 @@ int hm_state_create_batch(hm_problem* const* problems, int32_t n_problems, int32
   DevBuf* dbl[] = {&s->rx, &s->ry, &s->rz, &s->mu, &s->smu, &s->zobs, &s->scz, &s->d, &s->pd, &s->gd, &s->d0, &s->gd0};
   for (DevBuf* b : dbl) HM_TRY(b->alloc(8 * nt));
   HM_CUDA(cudaMemset(s->pd.p, 0, 8 * nt));
-  HM_TRY(s->r.alloc(rs * nt));
-  HM_TRY(s->cell.alloc(4 * nt));
-  HM_TRY(s->frac.alloc(rs * 3 * nt));
+  HM_TRY(s->work.alloc(s->prec, n_chains, s->N, tot));
   for (int c = 0; c < n_chains; ++c) {
     hm_problem* p = s->chain_prob[c];
     const long long n = p->n;
@@ -965,7 +1021,7 @@ int hm_run_chain(hm_state* s, int32_t n_traj, int32_t n_leapfrog, const double* 
   Prof* pf = s->prof.get();
   if (pf) {
     HM_TRY(profile_collect(s));
-    HM_TRY(pf->reserve(12 * n_leapfrog + 8));
+    HM_TRY(pf->reserve(14 * n_leapfrog + 8));
     pf->idx = 0;
   }
   // With profiling, a single-trajectory call leaves its events pending (read

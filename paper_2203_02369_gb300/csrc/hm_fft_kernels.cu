@@ -28,108 +28,224 @@ template <> __device__ __forceinline__ double vget<double>(const double2& v, int
 
 template <int N> struct PlaneCfg {
   static constexpr int NH = N / 2 + 1;
-  static constexpr int ZP = N + 1;                 // pitch of packed z rows
+  static constexpr int ZP = 2 * NH;                // pitch of packed z rows (= 2 spectrum rows)
   static constexpr int NT = N >= 128 ? 512 : (N >= 64 ? 256 : 128);
-  static constexpr int ZSIZE = (N / 2) * ZP;       // complex elements
-  static constexpr int HSIZE = N * NH;
+  static constexpr int SIZE = N * NH;              // complex elements of the plane buffer
+  static constexpr int MINB = N >= 128 ? 2 : 1;    // CTAs per SM the register budget aims at
 };
 
 template <typename T, int N> constexpr size_t plane_smem_bytes() {
-  return sizeof(cplx<T>) * (PlaneCfg<N>::ZSIZE + PlaneCfg<N>::HSIZE);
+  return sizeof(cplx<T>) * PlaneCfg<N>::SIZE;
+}
+
+// The plane buffer B holds N*(N/2+1) complex values and is read through two
+// views that share memory:
+//   spectrum view  H[y][k] = B[y*NH + k]            (y < N, k <= N/2)
+//   packed view    Z[r][z] = B[r*ZP + z], ZP = 2 NH (r < N/2, z < N), whose
+//                  real/imaginary parts are the real rows y = 2r and 2r+1.
+// Z row r and H rows 2r, 2r+1 occupy the same addresses, so the real <->
+// half-spectrum (un)packing runs in place, row pair by row pair.
+template <typename T, int N>
+__device__ __forceinline__ T* zreal(cplx<T>* B, int y, int z) {
+  return reinterpret_cast<T*>(&B[(y >> 1) * PlaneCfg<N>::ZP + z]) + (y & 1);
+}
+
+// Z rows (after the forward z FFT) -> H rows (half spectra of the real rows).
+template <typename T, int N>
+__device__ __forceinline__ void unpack_rows(cplx<T>* B) {
+  using C = cplx<T>;
+  using P = PlaneCfg<N>;
+  constexpr int NH = P::NH, ZP = P::ZP, NT = P::NT;
+  constexpr int TOT = (N / 2) * NH;
+  constexpr int PER = (TOT + NT - 1) / NT;
+  C a[PER], b[PER];
+#pragma unroll
+  for (int i = 0; i < PER; ++i) {
+    const int e = threadIdx.x + i * NT;
+    if (e < TOT) {
+      const int r = e / NH, k = e % NH;
+      const C zk = B[r * ZP + k];
+      const C zm = cconj(B[r * ZP + ((N - k) & (N - 1))]);
+      const C sp = cadd(zk, zm), df = csub(zk, zm);
+      a[i] = C{(T)0.5 * sp.x, (T)0.5 * sp.y};
+      b[i] = C{(T)0.5 * df.y, (T)-0.5 * df.x};
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int i = 0; i < PER; ++i) {
+    const int e = threadIdx.x + i * NT;
+    if (e < TOT) {
+      const int r = e / NH, k = e % NH;
+      B[r * ZP + k] = a[i];
+      B[r * ZP + NH + k] = b[i];
+    }
+  }
+  __syncthreads();
+}
+
+// H rows (inverse-transformed along y) -> Z rows ready for the inverse z FFT.
+// The imaginary parts at kz = 0 and N/2 are dropped (c2r semantics).
+template <typename T, int N>
+__device__ __forceinline__ void pack_rows(cplx<T>* B) {
+  using C = cplx<T>;
+  using P = PlaneCfg<N>;
+  constexpr int NH = P::NH, ZP = P::ZP, NT = P::NT;
+  constexpr int TOT = (N / 2) * N;
+  constexpr int PER = (TOT + NT - 1) / NT;
+  C o[PER];
+#pragma unroll
+  for (int i = 0; i < PER; ++i) {
+    const int e = threadIdx.x + i * NT;
+    if (e < TOT) {
+      const int r = e / N, k = e % N;
+      C a, b;
+      if (k <= N / 2) {
+        a = B[r * ZP + k];
+        b = B[r * ZP + NH + k];
+        if (k == 0 || k == N / 2) {
+          a.y = 0;
+          b.y = 0;
+        }
+      } else {
+        a = cconj(B[r * ZP + (N - k)]);
+        b = cconj(B[r * ZP + NH + (N - k)]);
+      }
+      o[i] = C{a.x - b.y, a.y + b.x};
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int i = 0; i < PER; ++i) {
+    const int e = threadIdx.x + i * NT;
+    if (e < TOT) B[(e / N) * ZP + (e % N)] = o[i];
+  }
+  __syncthreads();
+}
+
+// Bucket ranges of the plane's two point sets: side 0 has its lower CIC
+// corner on this plane (bucket ix), side 1 its upper corner (bucket ix-1).
+struct PlaneBuckets {
+  int b0, n0, b1, n1;
+};
+template <int N>
+__device__ __forceinline__ PlaneBuckets plane_buckets(const int* __restrict__ off, int c, int ix) {
+  const int* o = off + (long long)c * (N + 1);
+  const int ixm = (ix + N - 1) & (N - 1);
+  PlaneBuckets pb;
+  pb.b0 = o[ix];
+  pb.n0 = o[ix + 1] - o[ix];
+  pb.b1 = o[ixm];
+  pb.n1 = o[ixm + 1] - o[ixm];
+  return pb;
+}
+
+template <typename T> __device__ __forceinline__ T rcomp(const PtRec<T>& p, int j) {
+  return j == 0 ? p.rx : (j == 1 ? p.ry : p.rz);
 }
 
 // ---------------------------------------------------------------------------
 // Plane pass, forward: real plane x -> (z r2c, y c2c) -> spectrum plane.
+// SCATTER builds the plane from the bucketed points instead of loading it:
+// s_j(corner) += r rhat_j W(corner), with shared-memory atomics (the adjoint
+// of the CIC gather, restricted to this plane).
 // ---------------------------------------------------------------------------
-template <typename T, int N>
-__global__ void __launch_bounds__(PlaneCfg<N>::NT)
+template <typename T, int N, bool SCATTER>
+__global__ void __launch_bounds__(PlaneCfg<N>::NT, (sizeof(T) == 4 ? PlaneCfg<N>::MINB : 1))
 k_plane_r2c(const T* __restrict__ in, long long in_stride, cplx<T>* __restrict__ out,
-            long long out_stride, const cplx<T>* __restrict__ tw) {
+            long long out_stride, const cplx<T>* __restrict__ tw, PlanePoints pts) {
   using C = cplx<T>;
   using P = PlaneCfg<N>;
-  constexpr int NT = P::NT, NH = P::NH, ZP = P::ZP;
+  constexpr int NT = P::NT, ZP = P::ZP;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  C* Z = reinterpret_cast<C*>(smem_raw);
-  C* H = Z + P::ZSIZE;
+  C* B = reinterpret_cast<C*>(smem_raw);
   const int ix = blockIdx.x;
   const int s = blockIdx.y;
-  const T* src = in + (long long)s * in_stride + (long long)ix * N * N;
-  using V = typename Vec16<T>::type;
-  constexpr int VW = Vec16<T>::W;
-  const V* srcv = reinterpret_cast<const V*>(src);
-  for (int e = threadIdx.x; e < N * N / VW; e += NT) {
-    V v = __ldg(&srcv[e]);
-    const int y = (e * VW) / N, z0 = (e * VW) % N;
-    T* zr = reinterpret_cast<T*>(&Z[(y >> 1) * ZP + z0]) + (y & 1);
+  if constexpr (!SCATTER) {
+    const T* src = in + (long long)s * in_stride + (long long)ix * N * N;
+    using V = typename Vec16<T>::type;
+    constexpr int VW = Vec16<T>::W;
+    const V* srcv = reinterpret_cast<const V*>(src);
+    for (int e = threadIdx.x; e < N * N / VW; e += NT) {
+      V v = __ldg(&srcv[e]);
+      const int y = (e * VW) / N, z0 = (e * VW) % N;
+      T* zr = reinterpret_cast<T*>(&B[(y >> 1) * ZP + z0]) + (y & 1);
 #pragma unroll
-    for (int q = 0; q < VW; ++q) zr[2 * q] = vget<T>(v, q);
+      for (int q = 0; q < VW; ++q) zr[2 * q] = vget<T>(v, q);
+    }
+  } else {
+    for (int e = threadIdx.x; e < P::SIZE; e += NT) B[e] = C{(T)0, (T)0};
+    __syncthreads();
+    const int c = s / 3, j = s % 3;
+    const PlaneBuckets pb = plane_buckets<N>(pts.off, c, ix);
+    const PtRec<T>* R = static_cast<const PtRec<T>*>(pts.rec);
+    for (int t = threadIdx.x; t < pb.n0 + pb.n1; t += NT) {
+      const bool lower = t < pb.n0;
+      const PtRec<T> p = R[lower ? pb.b0 + t : pb.b1 + (t - pb.n0)];
+      const T val = p.r * rcomp(p, j) * (lower ? (T)1 - p.fx : p.fx);
+      if (val == (T)0) continue;
+      const int iy = p.yz / N, iz = p.yz % N;
+      const int iy1 = (iy + 1) & (N - 1), iz1 = (iz + 1) & (N - 1);
+      const T wy1 = p.fy, wy0 = (T)1 - p.fy, wz1 = p.fz, wz0 = (T)1 - p.fz;
+      atomicAdd(zreal<T, N>(B, iy, iz), val * wy0 * wz0);
+      atomicAdd(zreal<T, N>(B, iy, iz1), val * wy0 * wz1);
+      atomicAdd(zreal<T, N>(B, iy1, iz), val * wy1 * wz0);
+      atomicAdd(zreal<T, N>(B, iy1, iz1), val * wy1 * wz1);
+    }
   }
   __syncthreads();
-  fft_smem<T, N, false, N / 2, NT, false>(Z, ZP, 1, tw);
-  // unpack two real rows from each packed row
-  for (int e = threadIdx.x; e < (N / 2) * NH; e += NT) {
-    const int r = e / NH, k = e % NH;
-    const C zk = Z[r * ZP + k];
-    const C zm = cconj(Z[r * ZP + ((N - k) & (N - 1))]);
-    const C sp = cadd(zk, zm), df = csub(zk, zm);
-    H[(2 * r) * NH + k] = C{(T)0.5 * sp.x, (T)0.5 * sp.y};
-    H[(2 * r + 1) * NH + k] = C{(T)0.5 * df.y, (T)-0.5 * df.x};
+  fft_smem<T, N, false, N / 2, NT, false>(B, ZP, 1, tw);
+  unpack_rows<T, N>(B);
+  fft_smem<T, N, false, P::NH, NT, true>(B, 1, P::NH, tw);
+  C* dst = out + (long long)s * out_stride + (long long)ix * P::SIZE;
+  if constexpr (sizeof(T) == 4) {
+    float4* d4 = reinterpret_cast<float4*>(dst);
+    const float4* s4 = reinterpret_cast<const float4*>(B);
+    for (int e = threadIdx.x; e < P::SIZE / 2; e += NT) d4[e] = s4[e];
+  } else {
+    for (int e = threadIdx.x; e < P::SIZE; e += NT) dst[e] = B[e];
   }
-  __syncthreads();
-  fft_smem<T, N, false, NH, NT, true>(H, 1, NH, tw);
-  C* dst = out + (long long)s * out_stride + (long long)ix * N * NH;
-  // the plane is contiguous in both smem and global memory
-  for (int e = threadIdx.x; e < N * NH; e += NT) dst[e] = H[e];
 }
 
 // ---------------------------------------------------------------------------
-// Plane pass, inverse: spectrum plane -> (y c2c, z c2r) -> real plane, with
-// either a plain store or the fused gradient / leapfrog epilogue.
+// Plane pass, inverse: spectrum plane -> (y c2c, z c2r) -> real plane, then
+// MODE 0: plain store; 1: gradient / leapfrog epilogue; 2: CIC gather of the
+// bucketed points (u and du partials of this plane and component).
 // ---------------------------------------------------------------------------
-template <typename T, int N>
-__global__ void __launch_bounds__(PlaneCfg<N>::NT)
+enum C2RMode : int { C2R_STORE = 0, C2R_EPI = 1, C2R_GATHER = 2 };
+
+template <typename T, int N, int MODE>
+__global__ void __launch_bounds__(PlaneCfg<N>::NT, (sizeof(T) == 4 ? PlaneCfg<N>::MINB : 1))
 k_plane_c2r(const cplx<T>* __restrict__ in, long long in_stride, T* __restrict__ out,
-            long long out_stride, const cplx<T>* __restrict__ tw, FieldEpi epi, int use_epi) {
+            long long out_stride, const cplx<T>* __restrict__ tw, FieldEpi epi, PlanePoints pts) {
   using C = cplx<T>;
   using P = PlaneCfg<N>;
-  constexpr int NT = P::NT, NH = P::NH, ZP = P::ZP;
+  constexpr int NT = P::NT, ZP = P::ZP;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  C* Z = reinterpret_cast<C*>(smem_raw);
-  C* H = Z + P::ZSIZE;
+  C* B = reinterpret_cast<C*>(smem_raw);
   __shared__ double red[2][NT / 32];
   const int ix = blockIdx.x;
   const int s = blockIdx.y;
-  const C* src = in + (long long)s * in_stride + (long long)ix * N * NH;
-  for (int e = threadIdx.x; e < N * NH; e += NT) H[e] = src[e];
-  __syncthreads();
-  fft_smem<T, N, true, NH, NT, true>(H, 1, NH, tw);
-  // pack rows 2r (real part) and 2r+1 (imaginary part) into one complex row
-  for (int e = threadIdx.x; e < (N / 2) * N; e += NT) {
-    const int r = e / N, k = e % N;
-    C a, b;
-    if (k <= N / 2) {
-      a = H[(2 * r) * NH + k];
-      b = H[(2 * r + 1) * NH + k];
-      if (k == 0 || k == N / 2) {
-        a.y = 0;
-        b.y = 0;
-      }
-    } else {
-      a = cconj(H[(2 * r) * NH + (N - k)]);
-      b = cconj(H[(2 * r + 1) * NH + (N - k)]);
-    }
-    Z[r * ZP + k] = C{a.x - b.y, a.y + b.x};
+  const C* src = in + (long long)s * in_stride + (long long)ix * P::SIZE;
+  if constexpr (sizeof(T) == 4) {
+    const float4* s4 = reinterpret_cast<const float4*>(src);
+    float4* b4 = reinterpret_cast<float4*>(B);
+    for (int e = threadIdx.x; e < P::SIZE / 2; e += NT) b4[e] = __ldg(&s4[e]);
+  } else {
+    for (int e = threadIdx.x; e < P::SIZE; e += NT) B[e] = src[e];
   }
   __syncthreads();
-  fft_smem<T, N, true, N / 2, NT, false>(Z, ZP, 1, tw);
+  fft_smem<T, N, true, P::NH, NT, true>(B, 1, P::NH, tw);
+  pack_rows<T, N>(B);
+  fft_smem<T, N, true, N / 2, NT, false>(B, ZP, 1, tw);
   using V = typename Vec16<T>::type;
   constexpr int VW = Vec16<T>::W;
-  if (!use_epi) {
+  if constexpr (MODE == C2R_STORE) {
     T* dst = out + (long long)s * out_stride + (long long)ix * N * N;
     V* dstv = reinterpret_cast<V*>(dst);
     for (int e = threadIdx.x; e < N * N / VW; e += NT) {
       const int y = (e * VW) / N, z0 = (e * VW) % N;
-      const T* zr = reinterpret_cast<const T*>(&Z[(y >> 1) * ZP + z0]) + (y & 1);
+      const T* zr = reinterpret_cast<const T*>(&B[(y >> 1) * ZP + z0]) + (y & 1);
       T t[VW];
 #pragma unroll
       for (int q = 0; q < VW; ++q) t[q] = zr[2 * q];
@@ -138,79 +254,106 @@ k_plane_c2r(const cplx<T>* __restrict__ in, long long in_stride, T* __restrict__
       else v = V{t[0], t[1]};
       dstv[e] = v;
     }
-    return;
-  }
-  // ---- gradient / leapfrog epilogue (one chain per blockIdx.y) ----
-  const long long base = (long long)s * epi.grid_stride + (long long)ix * N * N;
-  T* w = reinterpret_cast<T*>(epi.w) + base;
-  T* pw = reinterpret_cast<T*>(epi.pw) + base;
-  T* gw = reinterpret_cast<T*>(epi.gw) + base;
-  const int mode = epi.mode;
-  const T eps = (T)epi.cs[s].eps;
-  const T ck = (mode == GM_KICK_DRIFT) ? eps : (T)0.5 * eps;
-  double acc_w = 0.0, acc_p = 0.0;
-  V* wv = reinterpret_cast<V*>(w);
-  V* pv = reinterpret_cast<V*>(pw);
-  V* gv = reinterpret_cast<V*>(gw);
-  for (int e = threadIdx.x; e < N * N / VW; e += NT) {
-    const int y = (e * VW) / N, z0 = (e * VW) % N;
-    const T* zr = reinterpret_cast<const T*>(&Z[(y >> 1) * ZP + z0]) + (y & 1);
-    V wq = wv[e];
-    T wt[VW], pt[VW], gt[VW];
-    V pq;
-    if (mode != GM_GRAD) pq = pv[e];
+  } else if constexpr (MODE == C2R_GATHER) {
+    const int c = s / 3, j = s % 3;
+    const PlaneBuckets pb = plane_buckets<N>(pts.off, c, ix);
+    const PtRec<T>* R = static_cast<const PtRec<T>*>(pts.rec);
+    T* part = static_cast<T*>(pts.part);
+    const T idl = (T)pts.inv_delta;
+    for (int t = threadIdx.x; t < pb.n0 + pb.n1; t += NT) {
+      const bool lower = t < pb.n0;
+      const int q = lower ? pb.b0 + t : pb.b1 + (t - pb.n0);
+      const PtRec<T> p = R[q];
+      const int iy = p.yz / N, iz = p.yz % N;
+      const int iy1 = (iy + 1) & (N - 1), iz1 = (iz + 1) & (N - 1);
+      const T v00 = *zreal<T, N>(B, iy, iz), v01 = *zreal<T, N>(B, iy, iz1);
+      const T v10 = *zreal<T, N>(B, iy1, iz), v11 = *zreal<T, N>(B, iy1, iz1);
+      const T wy1 = p.fy, wy0 = (T)1 - p.fy, wz1 = p.fz, wz0 = (T)1 - p.fz;
+      const T a0 = wz0 * v00 + wz1 * v01, a1 = wz0 * v10 + wz1 * v11;
+      const T S = wy0 * a0 + wy1 * a1;      // y-z interpolation on this plane
+      const T Gy = a1 - a0;                 // d/dy (per cell) of it
+      const T Gz = wy0 * (v01 - v00) + wy1 * (v11 - v10);
+      const T wx = lower ? (T)1 - p.fx : p.fx;
+      const T sx = lower ? (T)-1 : (T)1;
+      const T rj = rcomp(p, j);
+      const int side = lower ? 0 : 1;
+      part[(long long)(side * 3 + j) * pts.ntot + q] = rj * wx * S;
+      part[(long long)(6 + side * 3 + j) * pts.ntot + q] =
+          rj * (p.rx * sx * S + p.ry * wx * Gy + p.rz * wx * Gz) * idl;
+    }
+  } else {
+    // ---- gradient / leapfrog epilogue (one chain per blockIdx.y) ----
+    const long long base = (long long)s * epi.grid_stride + (long long)ix * N * N;
+    T* w = reinterpret_cast<T*>(epi.w) + base;
+    T* pw = reinterpret_cast<T*>(epi.pw) + base;
+    T* gw = reinterpret_cast<T*>(epi.gw) + base;
+    const int mode = epi.mode;
+    const T eps = (T)epi.cs[s].eps;
+    const T ck = (mode == GM_KICK_DRIFT) ? eps : (T)0.5 * eps;
+    double acc_w = 0.0, acc_p = 0.0;
+    V* wv = reinterpret_cast<V*>(w);
+    V* pv = reinterpret_cast<V*>(pw);
+    V* gv = reinterpret_cast<V*>(gw);
+    for (int e = threadIdx.x; e < N * N / VW; e += NT) {
+      const int y = (e * VW) / N, z0 = (e * VW) % N;
+      const T* zr = reinterpret_cast<const T*>(&B[(y >> 1) * ZP + z0]) + (y & 1);
+      V wq = wv[e];
+      T wt[VW], pt[VW], gt[VW];
+      V pq;
+      if (mode != GM_GRAD) pq = pv[e];
 #pragma unroll
-    for (int q = 0; q < VW; ++q) {
-      const T wi = vget<T>(wq, q);
-      const T g = wi + zr[2 * q];
-      acc_w += 0.5 * (double)wi * (double)wi;
-      gt[q] = g;
+      for (int q = 0; q < VW; ++q) {
+        const T wi = vget<T>(wq, q);
+        const T g = wi + zr[2 * q];
+        acc_w += 0.5 * (double)wi * (double)wi;
+        gt[q] = g;
+        if (mode != GM_GRAD) {
+          T p = vget<T>(pq, q) - ck * g;
+          pt[q] = p;
+          wt[q] = (mode == GM_KICK_LAST) ? wi : wi + eps * p;
+          acc_p += 0.5 * (double)p * (double)p;
+        }
+      }
+      if (mode == GM_GRAD || mode == GM_KICK_LAST) {
+        V g;
+        if constexpr (VW == 4) g = V{gt[0], gt[1], gt[2], gt[3]};
+        else g = V{gt[0], gt[1]};
+        gv[e] = g;
+      }
       if (mode != GM_GRAD) {
-        T p = vget<T>(pq, q) - ck * g;
-        pt[q] = p;
-        wt[q] = (mode == GM_KICK_LAST) ? wi : wi + eps * p;
-        acc_p += 0.5 * (double)p * (double)p;
+        V p, ww;
+        if constexpr (VW == 4) {
+          p = V{pt[0], pt[1], pt[2], pt[3]};
+          ww = V{wt[0], wt[1], wt[2], wt[3]};
+        } else {
+          p = V{pt[0], pt[1]};
+          ww = V{wt[0], wt[1]};
+        }
+        pv[e] = p;
+        if (mode != GM_KICK_LAST) wv[e] = ww;
       }
     }
-    if (mode == GM_GRAD || mode == GM_KICK_LAST) {
-      V g;
-      if constexpr (VW == 4) g = V{gt[0], gt[1], gt[2], gt[3]};
-      else g = V{gt[0], gt[1]};
-      gv[e] = g;
-    }
-    if (mode != GM_GRAD) {
-      V p, ww;
-      if constexpr (VW == 4) {
-        p = V{pt[0], pt[1], pt[2], pt[3]};
-        ww = V{wt[0], wt[1], wt[2], wt[3]};
-      } else {
-        p = V{pt[0], pt[1]};
-        ww = V{wt[0], wt[1]};
-      }
-      pv[e] = p;
-      if (mode != GM_KICK_LAST) wv[e] = ww;
-    }
-  }
-  // deterministic block reduction: warp shuffles, then warp 0
+    // deterministic block reduction: warp shuffles, then thread 0 in order
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    acc_w += __shfl_down_sync(0xffffffffu, acc_w, o);
-    acc_p += __shfl_down_sync(0xffffffffu, acc_p, o);
-  }
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  if (lane == 0) {
-    red[0][wid] = acc_w;
-    red[1][wid] = acc_p;
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double a = 0.0, b = 0.0;
-    for (int i = 0; i < NT / 32; ++i) {
-      a += red[0][i];
-      b += red[1][i];
+    for (int o = 16; o > 0; o >>= 1) {
+      acc_w += __shfl_down_sync(0xffffffffu, acc_w, o);
+      acc_p += __shfl_down_sync(0xffffffffu, acc_p, o);
     }
-    epi.prior_part[(long long)s * N + ix] = a;
-    if (mode == GM_KICK_LAST) epi.kin_part[(long long)s * N + ix] = b;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) {
+      red[0][wid] = acc_w;
+      red[1][wid] = acc_p;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double a = 0.0, b = 0.0;
+      for (int i = 0; i < NT / 32; ++i) {
+        a += red[0][i];
+        b += red[1][i];
+      }
+      epi.prior_part[(long long)s * N + ix] = a;
+      if (mode == GM_KICK_LAST) epi.kin_part[(long long)s * N + ix] = b;
+    }
   }
 }
 
@@ -295,27 +438,28 @@ k_pencil(const cplx<T>* __restrict__ in, long long in_stride, cplx<T>* __restric
 // ---------------------------------------------------------------------------
 // Launchers.
 // ---------------------------------------------------------------------------
-template <typename T, int N>
+template <typename T, int N, bool SC>
 static cudaError_t plane_r2c_t(const void* in, long long in_stride, void* out, long long out_stride,
-                               int count, const void* tw, cudaStream_t st) {
+                               int count, const void* tw, const PlanePoints& pts, cudaStream_t st) {
   constexpr size_t sm = plane_smem_bytes<T, N>();
   dim3 grid(N, count);
-  k_plane_r2c<T, N><<<grid, PlaneCfg<N>::NT, sm, st>>>(
+  k_plane_r2c<T, N, SC><<<grid, PlaneCfg<N>::NT, sm, st>>>(
       static_cast<const T*>(in), in_stride, static_cast<cplx<T>*>(out), out_stride,
-      static_cast<const cplx<T>*>(tw));
+      static_cast<const cplx<T>*>(tw), pts);
   return cudaGetLastError();
 }
 
-template <typename T, int N>
+template <typename T, int N, int MODE>
 static cudaError_t plane_c2r_t(const void* in, long long in_stride, void* out, long long out_stride,
-                               int count, const void* tw, const FieldEpi* epi, cudaStream_t st) {
+                               int count, const void* tw, const FieldEpi* epi, const PlanePoints& pts,
+                               cudaStream_t st) {
   constexpr size_t sm = plane_smem_bytes<T, N>();
   dim3 grid(N, count);
   FieldEpi e{};
   if (epi) e = *epi;
-  k_plane_c2r<T, N><<<grid, PlaneCfg<N>::NT, sm, st>>>(
+  k_plane_c2r<T, N, MODE><<<grid, PlaneCfg<N>::NT, sm, st>>>(
       static_cast<const cplx<T>*>(in), in_stride, static_cast<T*>(out), out_stride,
-      static_cast<const cplx<T>*>(tw), e, epi ? 1 : 0);
+      static_cast<const cplx<T>*>(tw), e, pts);
   return cudaGetLastError();
 }
 
@@ -332,10 +476,11 @@ static cudaError_t pencil_t(const void* in, long long in_stride, void* out, long
   return cudaGetLastError();
 }
 
-// Supported grids: FP32 N in {8..128}; FP64 N in {8..64} (shared memory).
+// Supported grids: N in {8, 16, 32, 64, 128} at both precisions (one x-plane
+// of the half spectrum must fit in one CTA's shared memory).
 bool fft_supported(int prec, int N) {
-  if (prec == 0) return N == 8 || N == 16 || N == 32 || N == 64 || N == 128;
-  return N == 8 || N == 16 || N == 32 || N == 64;
+  (void)prec;
+  return N == 8 || N == 16 || N == 32 || N == 64 || N == 128;
 }
 
 #define HM_DISPATCH_N(PREC, N, CALL_F, CALL_D)                          \
@@ -354,6 +499,7 @@ bool fft_supported(int prec, int N) {
         case 16: { using T = double; constexpr int NN = 16; return CALL_D; }  \
         case 32: { using T = double; constexpr int NN = 32; return CALL_D; }  \
         case 64: { using T = double; constexpr int NN = 64; return CALL_D; }  \
+        case 128: { using T = double; constexpr int NN = 128; return CALL_D; } \
       }                                                                 \
     }                                                                   \
     return cudaErrorInvalidValue;                                       \
@@ -362,14 +508,18 @@ bool fft_supported(int prec, int N) {
 template <typename T, int N>
 static cudaError_t prepare_t() {
   cudaError_t e;
-  constexpr size_t sp = plane_smem_bytes<T, N>();
-  if ((e = cudaFuncSetAttribute(k_plane_r2c<T, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sp)) != cudaSuccess) return e;
-  if ((e = cudaFuncSetAttribute(k_plane_c2r<T, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sp)) != cudaSuccess) return e;
-  constexpr size_t s1 = sizeof(cplx<T>) * N * kTC, s3 = sizeof(cplx<T>) * N * 3 * kTC;
-  if ((e = cudaFuncSetAttribute(k_pencil<T, N, PM_FWD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s1)) != cudaSuccess) return e;
-  if ((e = cudaFuncSetAttribute(k_pencil<T, N, PM_INV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s1)) != cudaSuccess) return e;
-  if ((e = cudaFuncSetAttribute(k_pencil<T, N, PM_VEL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s3)) != cudaSuccess) return e;
-  return cudaFuncSetAttribute(k_pencil<T, N, PM_ADJ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s3);
+  constexpr int sp = (int)plane_smem_bytes<T, N>();
+  const cudaFuncAttribute A = cudaFuncAttributeMaxDynamicSharedMemorySize;
+  if ((e = cudaFuncSetAttribute(k_plane_r2c<T, N, false>, A, sp)) != cudaSuccess) return e;
+  if ((e = cudaFuncSetAttribute(k_plane_r2c<T, N, true>, A, sp)) != cudaSuccess) return e;
+  if ((e = cudaFuncSetAttribute(k_plane_c2r<T, N, C2R_STORE>, A, sp)) != cudaSuccess) return e;
+  if ((e = cudaFuncSetAttribute(k_plane_c2r<T, N, C2R_EPI>, A, sp)) != cudaSuccess) return e;
+  if ((e = cudaFuncSetAttribute(k_plane_c2r<T, N, C2R_GATHER>, A, sp)) != cudaSuccess) return e;
+  constexpr int s1 = (int)(sizeof(cplx<T>) * N * kTC), s3 = (int)(sizeof(cplx<T>) * N * 3 * kTC);
+  if ((e = cudaFuncSetAttribute(k_pencil<T, N, PM_FWD>, A, s1)) != cudaSuccess) return e;
+  if ((e = cudaFuncSetAttribute(k_pencil<T, N, PM_INV>, A, s1)) != cudaSuccess) return e;
+  if ((e = cudaFuncSetAttribute(k_pencil<T, N, PM_VEL>, A, s3)) != cudaSuccess) return e;
+  return cudaFuncSetAttribute(k_pencil<T, N, PM_ADJ>, A, s3);
 }
 
 cudaError_t fft_prepare(int prec, int N) {
@@ -378,15 +528,33 @@ cudaError_t fft_prepare(int prec, int N) {
 
 cudaError_t launch_plane_r2c(int prec, int N, const void* in, long long in_stride, void* out,
                              long long out_stride, int count, const void* tw, cudaStream_t st) {
-  HM_DISPATCH_N(prec, N, (plane_r2c_t<T, NN>(in, in_stride, out, out_stride, count, tw, st)),
-                (plane_r2c_t<T, NN>(in, in_stride, out, out_stride, count, tw, st)));
+  PlanePoints none{};
+  HM_DISPATCH_N(prec, N, (plane_r2c_t<T, NN, false>(in, in_stride, out, out_stride, count, tw, none, st)),
+                (plane_r2c_t<T, NN, false>(in, in_stride, out, out_stride, count, tw, none, st)));
+}
+
+cudaError_t launch_plane_r2c_scatter(int prec, int N, const PlanePoints& pts, void* out, long long out_stride,
+                                     int count, const void* tw, cudaStream_t st) {
+  HM_DISPATCH_N(prec, N, (plane_r2c_t<T, NN, true>(nullptr, 0, out, out_stride, count, tw, pts, st)),
+                (plane_r2c_t<T, NN, true>(nullptr, 0, out, out_stride, count, tw, pts, st)));
 }
 
 cudaError_t launch_plane_c2r(int prec, int N, const void* in, long long in_stride, void* out,
                              long long out_stride, int count, const void* tw, const FieldEpi* epi,
                              cudaStream_t st) {
-  HM_DISPATCH_N(prec, N, (plane_c2r_t<T, NN>(in, in_stride, out, out_stride, count, tw, epi, st)),
-                (plane_c2r_t<T, NN>(in, in_stride, out, out_stride, count, tw, epi, st)));
+  PlanePoints none{};
+  if (epi) {
+    HM_DISPATCH_N(prec, N, (plane_c2r_t<T, NN, C2R_EPI>(in, in_stride, out, out_stride, count, tw, epi, none, st)),
+                  (plane_c2r_t<T, NN, C2R_EPI>(in, in_stride, out, out_stride, count, tw, epi, none, st)));
+  }
+  HM_DISPATCH_N(prec, N, (plane_c2r_t<T, NN, C2R_STORE>(in, in_stride, out, out_stride, count, tw, nullptr, none, st)),
+                (plane_c2r_t<T, NN, C2R_STORE>(in, in_stride, out, out_stride, count, tw, nullptr, none, st)));
+}
+
+cudaError_t launch_plane_c2r_gather(int prec, int N, const void* in, long long in_stride,
+                                    const PlanePoints& pts, int count, const void* tw, cudaStream_t st) {
+  HM_DISPATCH_N(prec, N, (plane_c2r_t<T, NN, C2R_GATHER>(in, in_stride, nullptr, 0, count, tw, nullptr, pts, st)),
+                (plane_c2r_t<T, NN, C2R_GATHER>(in, in_stride, nullptr, 0, count, tw, nullptr, pts, st)));
 }
 
 template <typename T, int N>

@@ -50,6 +50,29 @@ __device__ __forceinline__ void normal_pair(unsigned long long seed, unsigned pa
   n1 = r * s;
 }
 
+// Normals in the field precision: FP64 Box-Muller for double fields; for
+// float fields the same 53-bit uniforms go through FP32 log/sqrt/sincospi
+// (the momenta are stored in FP32 anyway), which keeps the FP64 units free.
+template <typename T>
+__device__ __forceinline__ void normal_pair_t(unsigned long long seed, unsigned pair, unsigned traj,
+                                              unsigned chain, unsigned tag, T& n0, T& n1) {
+  if constexpr (sizeof(T) == 8) {
+    double a, b;
+    normal_pair(seed, pair, traj, chain, tag, a, b);
+    n0 = a;
+    n1 = b;
+  } else {
+    const uint4 x = philox4x32_10(make_uint4(pair, traj, chain, tag), key_of(seed));
+    const float om = (float)(1.0 - u53(x.x, x.y));
+    const float u2 = (float)u53(x.z, x.w);
+    const float r = sqrtf(-2.0f * logf(om));
+    float s, c;
+    sincospif(2.0f * u2, &s, &c);
+    n0 = r * c;
+    n1 = r * s;
+  }
+}
+
 template <typename T>
 __device__ __forceinline__ double block_sum2(double v, double* red) {
 #pragma unroll
@@ -88,10 +111,7 @@ k_traj_begin_field(long long n3, T* __restrict__ w, T* __restrict__ pw, const T*
     const long long e = off + 2 * q;
     T p[2];
     if (draw) {
-      double n0, n1;
-      normal_pair(seed, (unsigned)q, traj, cid, 0u, n0, n1);
-      p[0] = (T)n0;
-      p[1] = (T)n1;
+      normal_pair_t<T>(seed, (unsigned)q, traj, cid, 0u, p[0], p[1]);
     } else {
       p[0] = pw[e];
       p[1] = pw[e + 1];

@@ -41,7 +41,7 @@ struct ChainScal {
   long long traj_run0;   // counter at the start of the current run (trace row 0)
   int accept;            // last decision
   int status;            // bit flags, see STATUS_*
-  int n_bad;             // points outside the support at the last evaluation
+  int n_bad;             // unused (kept for layout)
   int sample_d;          // 1: distances move, 0: held fixed
 };
 
@@ -52,7 +52,6 @@ enum GradMode : int {
   GM_GRAD = 0,        // grad_w = w + g, prior partials (no momentum update)
   GM_KICK_DRIFT = 1,  // p -= eps*grad; w += eps*p
   GM_KICK_LAST = 2,   // p -= eps/2*grad; store grad; kinetic partials
-  GM_KICK_HALF_DRIFT = 3  // p -= eps/2*grad; w += eps*p (reverse use / tests)
 };
 
 struct FieldEpi {
@@ -66,27 +65,17 @@ struct FieldEpi {
   int mode;
 };
 
-// ---- FFT passes (hm_fft_kernels.cu) ----
-// Spectrum layout: [x][y][z], z in 0..N/2 (NH = N/2+1 entries), complex.
-enum PencilMode : int { PM_FWD = 0, PM_INV = 1, PM_VEL = 2, PM_ADJ = 3 };
+// One point as the plane passes see it, stored in x-plane bucket order:
+// fractional offsets in its cell, direction, (iy*N + iz) of the lower
+// corner, and the residual r = dPsi/du once the likelihood has run.
+template <typename T> struct PtRec {
+  T fx, fy, fz;
+  T rx, ry, rz;
+  int yz;
+  T r;
+};
 
-// count grids, real [count][N^3] -> partially transformed planes.
-cudaError_t launch_plane_r2c(int prec, int N, const void* in, long long in_stride, void* out,
-                             long long out_stride, int count, const void* tw, cudaStream_t st);
-// count spectra -> real grids (plain store), or the gradient epilogue.
-cudaError_t launch_plane_c2r(int prec, int N, const void* in, long long in_stride, void* out,
-                             long long out_stride, int count, const void* tw, const FieldEpi* epi,
-                             cudaStream_t st);
-// x-axis pass over count chains.  PM_VEL: 1 spectrum -> 3; PM_ADJ: 3 -> 1.
-cudaError_t launch_pencil(int prec, int N, int mode, const void* in, long long in_stride, void* out,
-                          long long out_stride, int count, const void* tw, const void* amp,
-                          cudaStream_t st);
-bool fft_supported(int prec, int N);
-// Raise the dynamic shared-memory limit of every FFT kernel for (prec, N) on
-// the current device; call once per device before any launch or capture.
-cudaError_t fft_prepare(int prec, int N);
-
-// ---- points (hm_points.cu) ----
+// Point-side arrays of C chains (points of chain c at [pt_off, pt_off+pt_n)).
 struct PointArrays {
   const double* rx;
   const double* ry;
@@ -98,22 +87,66 @@ struct PointArrays {
   double* d;
   double* pd;
   double* gd;
-  void* r;        // T residual dPsi/du per point
-  int* cell;      // linear lower-corner cell index
-  void* frac;     // T [3][ntot] fractional offsets
+  int* cx;        // x index of the lower corner (bucket), per point
+  int* slot;      // rank inside the bucket (atomic order), per point
+  int* pos;       // position in bucket order, per point
+  int* cnt;       // [C][N] bucket sizes (zeroed before every evaluation)
+  int* off;       // [C][N+1] bucket starts in the global bucket order
+  void* rec;      // PtRec<T> [ntot] in bucket order
+  void* part;     // T [12][ntot]: per (side, component) u and du partials, bucket order
   long long ntot;
 };
 
-cudaError_t launch_points_gather(int prec, int n_chains, int max_pts, const PointParams* pp,
-                                 PointArrays pa, const void* vgrid, long long grid_stride,
-                                 double* pts_part, int part_stride, ChainScal* cs, cudaStream_t st);
-cudaError_t launch_points_scatter(int prec, int n_chains, int max_pts, const PointParams* pp,
-                                  PointArrays pa, void* sgrid, long long grid_stride,
-                                  cudaStream_t st);
-// p_d/d update after the scatter (mode as GradMode) and kinetic partials.
+// ---- FFT passes (hm_fft_kernels.cu) ----
+// Spectrum layout: [x][y][z], z in 0..N/2 (NH = N/2+1 entries), complex.
+enum PencilMode : int { PM_FWD = 0, PM_INV = 1, PM_VEL = 2, PM_ADJ = 3 };
+
+// Plane-pass inputs/outputs beyond plain arrays.
+struct PlanePoints {
+  const int* off;       // [C][N+1]
+  const void* rec;      // PtRec<T>, bucket order
+  void* part;           // T [12][ntot]
+  long long ntot;
+  double inv_delta;     // 1/Delta for the spatial derivative
+};
+
+// count grids, real [count][N^3] -> plane-transformed spectra.
+cudaError_t launch_plane_r2c(int prec, int N, const void* in, long long in_stride, void* out,
+                             long long out_stride, int count, const void* tw, cudaStream_t st);
+// 3C scatter planes built from the bucketed residuals, then transformed.
+cudaError_t launch_plane_r2c_scatter(int prec, int N, const PlanePoints& pts, void* out, long long out_stride,
+                                     int count, const void* tw, cudaStream_t st);
+// count spectra -> real grids (plain store), or the gradient epilogue.
+cudaError_t launch_plane_c2r(int prec, int N, const void* in, long long in_stride, void* out,
+                             long long out_stride, int count, const void* tw, const FieldEpi* epi,
+                             cudaStream_t st);
+// 3C velocity spectra -> CIC partials of u and du at the bucketed points.
+cudaError_t launch_plane_c2r_gather(int prec, int N, const void* in, long long in_stride,
+                                    const PlanePoints& pts, int count, const void* tw, cudaStream_t st);
+// x-axis pass over count chains.  PM_VEL: 1 spectrum -> 3; PM_ADJ: 3 -> 1.
+cudaError_t launch_pencil(int prec, int N, int mode, const void* in, long long in_stride, void* out,
+                          long long out_stride, int count, const void* tw, const void* amp,
+                          cudaStream_t st);
+bool fft_supported(int prec, int N);
+// Raise the dynamic shared-memory limit of every FFT kernel for (prec, N) on
+// the current device; call once per device before any launch or capture.
+cudaError_t fft_prepare(int prec, int N);
+
+// ---- points (hm_points.cu) ----
+// bucket counts (x index of the lower corner) at the current distances
+cudaError_t launch_points_prep(int n_chains, int max_pts, const PointParams* pp, PointArrays pa,
+                               cudaStream_t st);
+// bucket offsets, full cells and the bucket-ordered point records
+cudaError_t launch_points_place(int prec, int n_chains, int max_pts, const PointParams* pp,
+                                PointArrays pa, cudaStream_t st);
+// u, du from the partials; FP64 likelihood, residuals, distance gradient
+cudaError_t launch_points_lik(int prec, int n_chains, int max_pts, const PointParams* pp, PointArrays pa,
+                              double* pts_part, int part_stride, ChainScal* cs, cudaStream_t st);
+// p_d/d update after the gradient (mode as GradMode) and kinetic partials.
 cudaError_t launch_points_kick(int n_chains, int max_pts, const PointParams* pp, PointArrays pa,
                                int mode, double* kin_part, int part_stride, ChainScal* cs,
-                               double* gd_store, cudaStream_t st);
+                               cudaStream_t st);
+int points_blocks(int max_pts);
 cudaError_t launch_cells(int n_chains, int max_pts, const PointParams* pp, const double* d,
                          PointArrays pa, int* cell_out, cudaStream_t st);
 cudaError_t launch_cell_sort(int N3, long long n, const int* cell, int* perm, int* hist_ws,

@@ -8,7 +8,7 @@
 
 namespace hm {
 
-constexpr int kPtsNT = 256;
+constexpr int kPtsNT = 128;
 
 // Lower-corner cell and fractional offsets of x = o + d rhat, formed as
 // t = (o + d*r)/Delta with one IEEE rounding per operation (no contraction),
@@ -68,7 +68,6 @@ __device__ __forceinline__ bool log_prior(const PointParams& P, double d, double
   return true;
 }
 
-template <typename T>
 __device__ __forceinline__ double block_sum(double v, double* red) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
@@ -83,15 +82,77 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
   return s;
 }
 
+// A distance that cannot be placed on the grid (non-finite or absurdly
+// large) is bucketed as if it sat at the observer; its likelihood term is
+// +inf and its residual 0, so the plane passes ignore it.
+__device__ __forceinline__ double placeable(double d) {
+  return (isfinite(d) && fabs(d) < 1e7) ? d : 0.0;
+}
+
 // ---------------------------------------------------------------------------
-// Gather + likelihood.  vgrid holds v_x, v_y, v_z for every chain:
-// vgrid[c*grid_stride + j*N^3 + (ix*N + iy)*N + iz].
+// Bucketing by the x index of the lower CIC corner: counts (and the rank of
+// each point inside its bucket, in atomic order) ...
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kPtsNT)
+k_points_prep(const PointParams* __restrict__ pp, PointArrays pa) {
+  const int c = blockIdx.y;
+  const PointParams& P = pp[c];
+  const long long il = (long long)blockIdx.x * kPtsNT + threadIdx.x;
+  if (il >= P.pt_n) return;
+  const long long i = P.pt_off + il;
+  int cx;
+  double f;
+  cell_axis(P.obs[0], placeable(pa.d[i]), pa.rx[i], P.delta, P.N, cx, f);
+  pa.cx[i] = cx;
+  pa.slot[i] = atomicAdd(&pa.cnt[c * P.N + cx], 1);
+}
+
+// ... then the bucket offsets and the bucket-ordered point records.
+template <typename T>
+__global__ void __launch_bounds__(kPtsNT)
+k_points_place(const PointParams* __restrict__ pp, PointArrays pa) {
+  __shared__ int excl[257];
+  const int c = blockIdx.y;
+  const PointParams& P = pp[c];
+  const int N = P.N;
+  if (threadIdx.x == 0) {
+    int acc = 0;
+    for (int b = 0; b < N; ++b) {
+      excl[b] = acc;
+      acc += pa.cnt[c * N + b];
+    }
+    excl[N] = acc;
+  }
+  __syncthreads();
+  if (blockIdx.x == 0)
+    for (int b = threadIdx.x; b <= N; b += kPtsNT) pa.off[c * (N + 1) + b] = (int)P.pt_off + excl[b];
+  const long long il = (long long)blockIdx.x * kPtsNT + threadIdx.x;
+  if (il >= P.pt_n) return;
+  const long long i = P.pt_off + il;
+  const double rx = pa.rx[i], ry = pa.ry[i], rz = pa.rz[i];
+  const CellPos cp = cell_of(P, placeable(pa.d[i]), rx, ry, rz);
+  // the bucket and rank come from the counting pass (same arithmetic, same d)
+  const int pos = (int)P.pt_off + excl[pa.cx[i]] + pa.slot[i];
+  pa.pos[i] = pos;
+  PtRec<T> r;
+  r.fx = (T)cp.fx;
+  r.fy = (T)cp.fy;
+  r.fz = (T)cp.fz;
+  r.rx = (T)rx;
+  r.ry = (T)ry;
+  r.rz = (T)rz;
+  r.yz = cp.iy * N + cp.iz;
+  r.r = (T)0;
+  static_cast<PtRec<T>*>(pa.rec)[pos] = r;
+}
+
+// ---------------------------------------------------------------------------
+// Likelihood: u and du from the plane partials, then the FP64 point terms.
 // ---------------------------------------------------------------------------
 template <typename T>
 __global__ void __launch_bounds__(kPtsNT)
-k_points_gather(const PointParams* __restrict__ pp, PointArrays pa, const T* __restrict__ vgrid,
-                long long grid_stride, double* __restrict__ pts_part, int part_stride,
-                ChainScal* __restrict__ cs) {
+k_points_lik(const PointParams* __restrict__ pp, PointArrays pa, double* __restrict__ pts_part,
+             int part_stride, ChainScal* __restrict__ cs) {
   __shared__ double red[kPtsNT / 32];
   const int c = blockIdx.y;
   const PointParams& P = pp[c];
@@ -100,128 +161,54 @@ k_points_gather(const PointParams* __restrict__ pp, PointArrays pa, const T* __r
   int bad = 0;
   if (il < P.pt_n) {
     const long long i = P.pt_off + il;
+    const int pos = pa.pos[i];
+    const T* part = static_cast<const T*>(pa.part);
+    double u = 0.0, du = 0.0;
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+      u += (double)part[(long long)k * pa.ntot + pos];
+      du += (double)part[(long long)(6 + k) * pa.ntot + pos];
+    }
     const double d = pa.d[i];
-    const double rx = pa.rx[i], ry = pa.ry[i], rz = pa.rz[i];
-    const CellPos cp = cell_of(P, d, rx, ry, rz);
-    const int N = P.N;
-    const long long N3 = (long long)N * N * N;
-    T* frac = static_cast<T*>(pa.frac);
-    pa.cell[i] = (cp.ix * N + cp.iy) * N + cp.iz;
-    frac[i] = (T)cp.fx;
-    frac[pa.ntot + i] = (T)cp.fy;
-    frac[2 * pa.ntot + i] = (T)cp.fz;
-    // domain of the second-order zbar(d) and of the distance prior
     const double om = P.omega_m;
     const double x = 1.0 - 3.0 * om * kH0 * d / kC;
     double lp = 0.0, dlp = 0.0;
     const bool ok = d > 0.0 && x > 0.0 && log_prior(P, d, lp, dlp);
-    T* rres = static_cast<T*>(pa.r);
+    PtRec<T>* rec = static_cast<PtRec<T>*>(pa.rec);
     if (!ok) {
       psi_i = __longlong_as_double(0x7ff0000000000000LL);  // +inf
-      rres[i] = (T)0;
+      rec[pos].r = (T)0;
       pa.gd[i] = 0.0;
       bad = 1;
     } else {
-      // CIC gather of the three components and their spatial gradients
-      const T fx = (T)cp.fx, fy = (T)cp.fy, fz = (T)cp.fz;
-      const T wx[2] = {(T)1 - fx, fx}, wy[2] = {(T)1 - fy, fy}, wz[2] = {(T)1 - fz, fz};
-      const int xs[2] = {cp.ix, cp.ix + 1 == N ? 0 : cp.ix + 1};
-      const int ys[2] = {cp.iy, cp.iy + 1 == N ? 0 : cp.iy + 1};
-      const int zs[2] = {cp.iz, cp.iz + 1 == N ? 0 : cp.iz + 1};
-      const T* vb = vgrid + (long long)c * grid_stride;
-      T val[3] = {0, 0, 0}, gx[3] = {0, 0, 0}, gy[3] = {0, 0, 0}, gz[3] = {0, 0, 0};
-#pragma unroll
-      for (int a = 0; a < 2; ++a)
-#pragma unroll
-        for (int b = 0; b < 2; ++b)
-#pragma unroll
-          for (int e = 0; e < 2; ++e) {
-            const long long idx = ((long long)xs[a] * N + ys[b]) * N + zs[e];
-            const T wxyz = wx[a] * wy[b] * wz[e];
-            const T dx = (a ? (T)1 : (T)-1) * wy[b] * wz[e];
-            const T dy = (b ? (T)1 : (T)-1) * wx[a] * wz[e];
-            const T dz = (e ? (T)1 : (T)-1) * wx[a] * wy[b];
-#pragma unroll
-            for (int j = 0; j < 3; ++j) {
-              const T g = __ldg(&vb[j * N3 + idx]);
-              val[j] += wxyz * g;
-              gx[j] += dx * g;
-              gy[j] += dy * g;
-              gz[j] += dz * g;
-            }
-          }
-      const double r3[3] = {rx, ry, rz};
-      double u = 0.0, du = 0.0;
-#pragma unroll
-      for (int j = 0; j < 3; ++j) {
-        u += r3[j] * (double)val[j];
-        du += r3[j] * ((double)gx[j] * rx + (double)gy[j] * ry + (double)gz[j] * rz);
-      }
-      du /= P.delta;
-      // point likelihood terms, FP64
       const double sq = sqrt(x);
       const double zb = 2.0 / (3.0 * om) * (1.0 - sq);
       const double zbp = (kH0 / kC) / sq;
       const double opz = 1.0 + zb;
+      const double iopz = 1.0 / opz;
       const double mu_d = 5.0 * log10(d * opz / P.h) + 25.0;
-      const double mup = 5.0 / log(10.0) * (1.0 / d + zbp / opz);
+      const double mup = (5.0 / 2.302585092994045684) * (1.0 / d + zbp * iopz);
       const double z = pa.zobs[i];
-      const double vo = kC * (z - zb) / opz;
-      const double vop = -kC * zbp * (1.0 + z) / (opz * opz);
+      const double vo = kC * (z - zb) * iopz;
+      const double vop = -kC * zbp * (1.0 + z) * iopz * iopz;
       const double scz = pa.scz[i];
-      const double k2 = P.sigma_nl2 + scz * scz / (opz * opz);
-      const double k2p = -2.0 * scz * scz * zbp / (opz * opz * opz);
+      const double scz2 = scz * scz;
+      const double k2 = P.sigma_nl2 + scz2 * iopz * iopz;
+      const double ik2 = 1.0 / k2;
+      const double k2p = -2.0 * scz2 * zbp * iopz * iopz * iopz;
       const double smu = pa.smu[i];
+      const double ismu2 = 1.0 / (smu * smu);
       const double res_mu = pa.mu[i] - mu_d;
       const double res_v = vo - u;
-      psi_i = res_mu * res_mu / (2.0 * smu * smu) + res_v * res_v / (2.0 * k2) + 0.5 * log(k2) - lp;
-      rres[i] = (T)(-res_v / k2);
-      pa.gd[i] = -res_mu * mup / (smu * smu) + res_v * (vop - du) / k2 -
-                 res_v * res_v * k2p / (2.0 * k2 * k2) + k2p / (2.0 * k2) - dlp;
+      psi_i = 0.5 * res_mu * res_mu * ismu2 + 0.5 * res_v * res_v * ik2 + 0.5 * log(k2) - lp;
+      rec[pos].r = (T)(-res_v * ik2);
+      pa.gd[i] = -res_mu * mup * ismu2 + res_v * (vop - du) * ik2 -
+                 0.5 * res_v * res_v * k2p * ik2 * ik2 + 0.5 * k2p * ik2 - dlp;
     }
   }
-  const double s = block_sum<T>(psi_i, red);
+  const double s = block_sum(psi_i, red);
   if (threadIdx.x == 0) pts_part[(long long)c * part_stride + blockIdx.x] = s;
   if (bad) atomicOr(&cs[c].status, STATUS_DOMAIN);
-}
-
-// ---------------------------------------------------------------------------
-// Adjoint CIC scatter: s_j(corner) += r_i rhat_ij W(corner).
-// ---------------------------------------------------------------------------
-template <typename T>
-__global__ void __launch_bounds__(kPtsNT)
-k_points_scatter(const PointParams* __restrict__ pp, PointArrays pa, T* __restrict__ sgrid,
-                 long long grid_stride) {
-  const int c = blockIdx.y;
-  const PointParams& P = pp[c];
-  const long long il = (long long)blockIdx.x * kPtsNT + threadIdx.x;
-  if (il >= P.pt_n) return;
-  const long long i = P.pt_off + il;
-  const T r = static_cast<const T*>(pa.r)[i];
-  if (r == (T)0) return;
-  const int N = P.N;
-  const long long N3 = (long long)N * N * N;
-  const int lin = pa.cell[i];
-  const int iz = lin % N, iy = (lin / N) % N, ix = lin / (N * N);
-  const T* frac = static_cast<const T*>(pa.frac);
-  const T fx = frac[i], fy = frac[pa.ntot + i], fz = frac[2 * pa.ntot + i];
-  const T wx[2] = {(T)1 - fx, fx}, wy[2] = {(T)1 - fy, fy}, wz[2] = {(T)1 - fz, fz};
-  const int xs[2] = {ix, ix + 1 == N ? 0 : ix + 1};
-  const int ys[2] = {iy, iy + 1 == N ? 0 : iy + 1};
-  const int zs[2] = {iz, iz + 1 == N ? 0 : iz + 1};
-  const T rj[3] = {r * (T)pa.rx[i], r * (T)pa.ry[i], r * (T)pa.rz[i]};
-  T* sb = sgrid + (long long)c * grid_stride;
-#pragma unroll
-  for (int a = 0; a < 2; ++a)
-#pragma unroll
-    for (int b = 0; b < 2; ++b)
-#pragma unroll
-      for (int e = 0; e < 2; ++e) {
-        const long long idx = ((long long)xs[a] * N + ys[b]) * N + zs[e];
-        const T wxyz = wx[a] * wy[b] * wz[e];
-#pragma unroll
-        for (int j = 0; j < 3; ++j) atomicAdd(&sb[j * N3 + idx], rj[j] * wxyz);
-      }
 }
 
 // ---------------------------------------------------------------------------
@@ -241,11 +228,11 @@ k_points_kick(const PointParams* __restrict__ pp, PointArrays pa, int mode, doub
     const double ck = (mode == GM_KICK_DRIFT) ? eps : 0.5 * eps;
     double p = pa.pd[i] - ck * pa.gd[i];
     pa.pd[i] = p;
-    if (mode == GM_KICK_DRIFT || mode == GM_KICK_HALF_DRIFT) pa.d[i] = pa.d[i] + eps * P.minv_d * p;
+    if (mode == GM_KICK_DRIFT) pa.d[i] = pa.d[i] + eps * P.minv_d * p;
     k = 0.5 * P.minv_d * p * p;
   }
   if (mode == GM_KICK_LAST) {
-    const double s = block_sum<double>(k, red);
+    const double s = block_sum(k, red);
     if (threadIdx.x == 0) kin_part[(long long)c * part_stride + blockIdx.x] = s;
   }
 }
@@ -336,39 +323,39 @@ __global__ void __launch_bounds__(kSortNT) k_cell_sort(int N3, long long n, cons
 // Launchers.
 // ---------------------------------------------------------------------------
 static inline dim3 pts_grid(int n_chains, int max_pts) {
-  return dim3((unsigned)((max_pts + kPtsNT - 1) / kPtsNT > 0 ? (max_pts + kPtsNT - 1) / kPtsNT : 1), n_chains);
+  return dim3((unsigned)points_blocks(max_pts), n_chains);
 }
 
-cudaError_t launch_points_gather(int prec, int n_chains, int max_pts, const PointParams* pp,
-                                 PointArrays pa, const void* vgrid, long long grid_stride,
-                                 double* pts_part, int part_stride, ChainScal* cs, cudaStream_t st) {
-  dim3 g = pts_grid(n_chains, max_pts);
-  if (prec == 0)
-    k_points_gather<float><<<g, kPtsNT, 0, st>>>(pp, pa, static_cast<const float*>(vgrid), grid_stride,
-                                                 pts_part, part_stride, cs);
-  else
-    k_points_gather<double><<<g, kPtsNT, 0, st>>>(pp, pa, static_cast<const double*>(vgrid), grid_stride,
-                                                  pts_part, part_stride, cs);
+int points_blocks(int max_pts) { return max_pts > 0 ? (max_pts + kPtsNT - 1) / kPtsNT : 1; }
+
+cudaError_t launch_points_prep(int n_chains, int max_pts, const PointParams* pp, PointArrays pa,
+                               cudaStream_t st) {
+  if (max_pts <= 0) return cudaSuccess;
+  k_points_prep<<<pts_grid(n_chains, max_pts), kPtsNT, 0, st>>>(pp, pa);
   return cudaGetLastError();
 }
 
-cudaError_t launch_points_scatter(int prec, int n_chains, int max_pts, const PointParams* pp,
-                                  PointArrays pa, void* sgrid, long long grid_stride,
-                                  cudaStream_t st) {
-  if (max_pts <= 0) return cudaSuccess;
-  dim3 g = pts_grid(n_chains, max_pts);
+cudaError_t launch_points_place(int prec, int n_chains, int max_pts, const PointParams* pp,
+                                PointArrays pa, cudaStream_t st) {
+  // runs even without points: block 0 writes the (empty) bucket offsets
+  if (prec == 0) k_points_place<float><<<pts_grid(n_chains, max_pts), kPtsNT, 0, st>>>(pp, pa);
+  else k_points_place<double><<<pts_grid(n_chains, max_pts), kPtsNT, 0, st>>>(pp, pa);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_points_lik(int prec, int n_chains, int max_pts, const PointParams* pp, PointArrays pa,
+                              double* pts_part, int part_stride, ChainScal* cs, cudaStream_t st) {
   if (prec == 0)
-    k_points_scatter<float><<<g, kPtsNT, 0, st>>>(pp, pa, static_cast<float*>(sgrid), grid_stride);
+    k_points_lik<float><<<pts_grid(n_chains, max_pts), kPtsNT, 0, st>>>(pp, pa, pts_part, part_stride, cs);
   else
-    k_points_scatter<double><<<g, kPtsNT, 0, st>>>(pp, pa, static_cast<double*>(sgrid), grid_stride);
+    k_points_lik<double><<<pts_grid(n_chains, max_pts), kPtsNT, 0, st>>>(pp, pa, pts_part, part_stride, cs);
   return cudaGetLastError();
 }
 
 cudaError_t launch_points_kick(int n_chains, int max_pts, const PointParams* pp, PointArrays pa,
                                int mode, double* kin_part, int part_stride, ChainScal* cs,
-                               double* /*gd_store*/, cudaStream_t st) {
-  dim3 g = pts_grid(n_chains, max_pts);
-  k_points_kick<<<g, kPtsNT, 0, st>>>(pp, pa, mode, kin_part, part_stride, cs);
+                               cudaStream_t st) {
+  k_points_kick<<<pts_grid(n_chains, max_pts), kPtsNT, 0, st>>>(pp, pa, mode, kin_part, part_stride, cs);
   return cudaGetLastError();
 }
 

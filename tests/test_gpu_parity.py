@@ -19,8 +19,13 @@ TOL = {"fp64": 1e-12, "fp32": 1e-5}
 
 
 def rel(a, b):
-    a = np.asarray(a, dtype=np.float64).ravel()
-    b = np.asarray(b, dtype=np.float64).ravel()
+    a = np.asarray(a).ravel()
+    b = np.asarray(b).ravel()
+    if np.iscomplexobj(a) or np.iscomplexobj(b):
+        a = np.concatenate([np.real(a), np.imag(a)])
+        b = np.concatenate([np.real(b), np.imag(b)])
+    a = a.astype(np.float64)
+    b = b.astype(np.float64)
     den = np.linalg.norm(b)
     return np.linalg.norm(a - b) / (den if den > 0 else 1.0)
 
@@ -50,7 +55,7 @@ def make_case(H, N, L, n, precision, seed, mask=0.0, r_max=None, sigma_mu=(0.2, 
 
 # ------------------------------------------------------------------ FFT ----
 @pytest.mark.parametrize("N,prec", [(8, "fp32"), (16, "fp32"), (32, "fp32"), (64, "fp32"), (128, "fp32"),
-                                    (8, "fp64"), (16, "fp64"), (32, "fp64"), (64, "fp64")])
+                                    (8, "fp64"), (16, "fp64"), (32, "fp64"), (64, "fp64"), (128, "fp64")])
 def test_fft_roundtrip_vs_numpy(H, N, prec):
     p = H.Problem(N, 100.0, precision=prec)
     rng = np.random.default_rng(N)
