@@ -196,7 +196,8 @@ double tophat(double x) { return 3.0 * (std::sin(x) - x * std::cos(x)) / (x * x 
 // Per-evaluation point workspace (bucketing, records, partials) and the
 // side stream on which the bucketing overlaps the first FFT passes.
 struct PtWork {
-  DevBuf cx, slot, pos, cnt, off, rec, part;
+  DevBuf cx, slot, pos, cnt, off, rec, part, lk;
+  int CN = 0;  // C*N: the count buffer holds two halves of CN ints (ping-pong)
   cudaStream_t aux = nullptr;
   cudaEvent_t fork = nullptr, join = nullptr;
   ~PtWork() {
@@ -211,11 +212,13 @@ struct PtWork {
     HM_TRY(cx.alloc(4 * nt));
     HM_TRY(slot.alloc(4 * nt));
     HM_TRY(pos.alloc(4 * nt));
-    HM_TRY(cnt.alloc(4 * (size_t)C * N));
+    HM_TRY(cnt.alloc(4 * 2 * (size_t)C * N));
     HM_TRY(off.alloc(4 * (size_t)C * (N + 1)));
     HM_TRY(rec.alloc(recsz * nt));
     HM_TRY(part.alloc(rsz * 12 * nt));
-    if (cudaMemset(cnt.p, 0, 4 * (size_t)C * N) != cudaSuccess) return fail(HM_ECUDA, "cudaMemset failed");
+    HM_TRY(lk.alloc(8 * 6 * nt));
+    CN = C * N;
+    if (cudaMemset(cnt.p, 0, 4 * 2 * (size_t)C * N) != cudaSuccess) return fail(HM_ECUDA, "cudaMemset failed");
     if (!aux) {
       if (cudaStreamCreateWithFlags(&aux, cudaStreamNonBlocking) != cudaSuccess ||
           cudaEventCreateWithFlags(&fork, cudaEventDisableTiming) != cudaSuccess ||
@@ -224,14 +227,18 @@ struct PtWork {
     }
     return HM_OK;
   }
-  void fill(PointArrays& pa, long long ntot) const {
+  int* half(int parity) const { return cnt.as<int>() + (size_t)(parity & 1) * CN; }
+  // parity selects which count half holds the current distances' buckets
+  void fill(PointArrays& pa, long long ntot, int parity = 0) const {
     pa.cx = cx.as<int>();
     pa.slot = slot.as<int>();
     pa.pos = pos.as<int>();
-    pa.cnt = cnt.as<int>();
+    pa.cnt = half(parity);
+    pa.cnt_next = half(parity + 1);
     pa.off = off.as<int>();
     pa.rec = rec.p;
     pa.part = part.p;
+    pa.lk = lk.as<double>();
     pa.ntot = ntot;
   }
 };
@@ -350,9 +357,11 @@ struct GradArgs {
 //                 likelihood -> per-plane CIC scatter + forward -> x pencils
 //                 with the adjoint weights -> per-plane inverse with the
 //                 gradient / leapfrog epilogue -> distance kick/drift.
-static int grad_eval(const GradArgs& a, int mode, cudaStream_t st) {
+static int grad_eval(const GradArgs& a0, int mode, cudaStream_t st, int parity, bool count_first) {
+  GradArgs a = a0;
   Prof* pf = a.prof;
   const PtWork& wk = *a.work;
+  wk.fill(a.pa, a.pa.ntot, parity);
   cudaStream_t ax = wk.aux;
   PlanePoints pts{};
   pts.off = a.pa.off;
@@ -360,12 +369,14 @@ static int grad_eval(const GradArgs& a, int mode, cudaStream_t st) {
   pts.part = a.pa.part;
   pts.ntot = a.pa.ntot;
   pts.inv_delta = 1.0 / a.delta;
-  // fork: bucketing of the points on the side stream
+  // fork: bucket placement and the d-only likelihood terms on the side stream
   HM_CUDA(cudaEventRecord(wk.fork, st));
   HM_CUDA(cudaStreamWaitEvent(ax, wk.fork, 0));
-  HM_PROF(pf, KK_MEMSET_CNT, ax, cudaMemsetAsync(a.pa.cnt, 0, sizeof(int) * (size_t)a.C * a.N, ax));
-  HM_PROF(pf, KK_PREP, ax, launch_points_prep(a.C, a.max_pts, a.pp, a.pa, ax));
-  HM_PROF(pf, KK_PLACE, ax, launch_points_place(a.prec, a.C, a.max_pts, a.pp, a.pa, ax));
+  if (count_first) {
+    HM_PROF(pf, KK_MEMSET_CNT, ax, cudaMemsetAsync(a.pa.cnt, 0, sizeof(int) * (size_t)a.C * a.N, ax));
+    HM_PROF(pf, KK_PREP, ax, launch_points_prep(a.C, a.max_pts, a.pp, a.pa, ax));
+  }
+  HM_PROF(pf, KK_PLACE, ax, launch_points_place(a.prec, a.C, a.max_pts, a.pp, a.pa, a.cs, ax));
   HM_CUDA(cudaEventRecord(wk.join, ax));
   // forward field operator
   HM_PROF(pf, KK_R2C_FIELD, st, launch_plane_r2c(a.prec, a.N, a.w, a.n3, a.S1, a.nspec, a.C, a.tw, st));
@@ -374,8 +385,7 @@ static int grad_eval(const GradArgs& a, int mode, cudaStream_t st) {
   // join, then velocity planes with the CIC gather at the points
   HM_CUDA(cudaStreamWaitEvent(st, wk.join, 0));
   HM_PROF(pf, KK_C2R_GATHER, st, launch_plane_c2r_gather(a.prec, a.N, a.S2, a.nspec, pts, 3 * a.C, a.tw, st));
-  HM_PROF(pf, KK_LIK, st,
-          launch_points_lik(a.prec, a.C, a.max_pts, a.pp, a.pa, a.pts_part, a.pts_blocks, a.cs, st));
+  HM_PROF(pf, KK_LIK, st, launch_points_lik(a.prec, a.C, a.max_pts, a.pp, a.pa, a.pts_part, a.pts_blocks, st));
   // adjoint: residuals scattered plane by plane, forward transform, weights
   HM_PROF(pf, KK_R2C_SCATTER, st, launch_plane_r2c_scatter(a.prec, a.N, pts, a.S1, a.nspec, 3 * a.C, a.tw, st));
   HM_PROF(pf, KK_PENCIL_ADJ, st,
@@ -626,7 +636,7 @@ int hm_logpost_grad(hm_problem* p, const void* w_dev, const double* d_dev, doubl
   a.kinl_p = p->kin_part.as<double>();
   a.cs = cs;
   a.work = &p->pw;
-  HM_TRY(grad_eval(a, GM_GRAD, st));
+  HM_TRY(grad_eval(a, GM_GRAD, st, 0, true));
   HM_CUDA(launch_finalize(1, a.prior_part, p->N, a.pts_part, a.pts_blocks, nullptr, 0, nullptr, 0, FIN_PSI,
                           0ull, p->chain_id.as<int>(), cs, nullptr, st));
   HM_CUDA(cudaMemcpyAsync(psi_dev, &cs->psi, sizeof(double), cudaMemcpyDeviceToDevice, st));
@@ -742,7 +752,7 @@ static GradArgs state_args(hm_state* s) {
 
 static int state_refresh(hm_state* s, cudaStream_t st) {
   GradArgs a = state_args(s);
-  HM_TRY(grad_eval(a, GM_GRAD, st));
+  HM_TRY(grad_eval(a, GM_GRAD, st, 0, true));
   HM_CUDA(launch_finalize(s->C, a.prior_part, s->N, a.pts_part, s->pts_blocks, nullptr, 0, nullptr, 0, FIN_PSI,
                           s->seed, s->chain_id.as<int>(), a.cs, nullptr, st));
   return HM_OK;
@@ -952,17 +962,22 @@ static int leapfrog_body(hm_state* s, int n_steps, int draw, cudaStream_t st, Pr
   GradArgs a = state_args(s);
   a.prof = pf;
   PointArrays pa = a.pa;
+  s->work.fill(pa, s->ntot, 1);   // begin counts the drifted d into half 0 (pa.cnt_next)
   if (pf) HM_CUDA(pf->begin(KK_BEGIN, st));
   HM_CUDA(launch_traj_begin_field(s->prec, s->C, s->n3, s->w.p, s->pw.p, s->gw.p, s->w0.p, s->gw0.p, s->seed,
                                   s->chain_id.as<int>(), s->kinb_f.as<double>(), s->nparts_f, draw, a.cs, st));
-  if (s->max_pts > 0)
+  if (s->max_pts > 0) {
+    HM_CUDA(cudaMemsetAsync(pa.cnt_next, 0, sizeof(int) * (size_t)s->C * s->N, st));
     HM_CUDA(launch_traj_begin_points(s->C, s->max_pts, a.pp, pa, s->d0.as<double>(), s->gd0.as<double>(), s->seed,
                                      s->chain_id.as<int>(), s->kinb_p.as<double>(), s->nparts_p, draw, a.cs, st));
+  }
   HM_CUDA(launch_finalize(s->C, nullptr, 0, nullptr, 0, s->kinb_f.as<double>(), s->nparts_f,
                           s->kinb_p.as<double>(), s->max_pts > 0 ? s->nparts_p : 0, FIN_HOLD, s->seed,
                           s->chain_id.as<int>(), a.cs, nullptr, st));
   if (pf) HM_CUDA(pf->end(st));
-  for (int l = 1; l <= n_steps; ++l) HM_TRY(grad_eval(a, l < n_steps ? GM_KICK_DRIFT : GM_KICK_LAST, st));
+  // evaluation l reads the counts of half (l-1)%2 and its kick counts into the other
+  for (int l = 1; l <= n_steps; ++l)
+    HM_TRY(grad_eval(a, l < n_steps ? GM_KICK_DRIFT : GM_KICK_LAST, st, (l - 1) & 1, false));
   return HM_OK;
 }
 

@@ -190,4 +190,35 @@ __device__ __forceinline__ void fft_smem(cplx<T>* buf, int rs, int es, const cpl
   }
 }
 
+// Per-thread accumulator of 0.5 * sum x^2 for energy reductions.  For FP32
+// data it keeps an unevaluated pair (hi, lo) of floats: x*x is split exactly
+// into p + e with an FMA, p/2 is added with Knuth's TwoSum and every rounding
+// error goes to lo, so the per-thread sum carries about 48 significant bits
+// without using the (slow on this part) FP64 pipe; the pair is converted to
+// double once per thread for the FP64 block and grid reductions.  For FP64
+// data it is a plain double sum.
+template <typename T> struct HalfSqAcc;
+template <> struct HalfSqAcc<double> {
+  double s = 0.0;
+  __device__ __forceinline__ void add_half_sq(double x) { s += 0.5 * x * x; }
+  __device__ __forceinline__ double value() const { return s; }
+};
+template <> struct HalfSqAcc<float> {
+  float hi = 0.f, lo = 0.f;
+  __device__ __forceinline__ void add(float x) {
+    const float s = __fadd_rn(hi, x);
+    const float bp = __fadd_rn(s, -hi);
+    const float err = __fadd_rn(__fadd_rn(hi, -__fadd_rn(s, -bp)), __fadd_rn(x, -bp));
+    hi = s;
+    lo = __fadd_rn(lo, err);
+  }
+  __device__ __forceinline__ void add_half_sq(float x) {
+    const float p = __fmul_rn(x, x);
+    const float e = __fmaf_rn(x, x, -p);
+    add(__fmul_rn(0.5f, p));
+    lo = __fmaf_rn(0.5f, e, lo);
+  }
+  __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
+};
+
 }  // namespace hm

@@ -123,6 +123,52 @@ __device__ __forceinline__ void pack_rows(cplx<T>* B) {
   __syncthreads();
 }
 
+// Real plane (rows y, contiguous z) <-> packed view.  Item (r, zp) covers
+// rows 2r, 2r+1 and columns z = 2zp, 2zp+1: two 2-wide global accesses per
+// row and one 16-byte (FP32) shared access, so consecutive threads touch
+// consecutive shared words (no bank conflicts).
+template <typename T, int N>
+__device__ __forceinline__ void load_plane_packed(cplx<T>* B, const T* __restrict__ src) {
+  using P = PlaneCfg<N>;
+  constexpr int ITEMS = (N / 2) * (N / 2);
+  for (int e = threadIdx.x; e < ITEMS; e += P::NT) {
+    const int r = e / (N / 2), z = 2 * (e % (N / 2));
+    if constexpr (sizeof(T) == 4) {
+      const float2 a = __ldg(reinterpret_cast<const float2*>(src + (2 * r) * N + z));
+      const float2 b = __ldg(reinterpret_cast<const float2*>(src + (2 * r + 1) * N + z));
+      *reinterpret_cast<float4*>(&B[r * P::ZP + z]) = make_float4(a.x, b.x, a.y, b.y);
+    } else {
+      const double2 a = __ldg(reinterpret_cast<const double2*>(src + (2 * r) * N + z));
+      const double2 b = __ldg(reinterpret_cast<const double2*>(src + (2 * r + 1) * N + z));
+      B[r * P::ZP + z] = cplx<T>{a.x, b.x};
+      B[r * P::ZP + z + 1] = cplx<T>{a.y, b.y};
+    }
+  }
+}
+
+// values of item (r, zp): v[0] = (2r, z), v[1] = (2r+1, z), v[2] = (2r, z+1), v[3] = (2r+1, z+1)
+template <typename T, int N>
+__device__ __forceinline__ void read_item(const cplx<T>* B, int r, int z, T* v) {
+  using P = PlaneCfg<N>;
+  if constexpr (sizeof(T) == 4) {
+    const float4 q = *reinterpret_cast<const float4*>(&B[r * P::ZP + z]);
+    v[0] = q.x;
+    v[1] = q.y;
+    v[2] = q.z;
+    v[3] = q.w;
+  } else {
+    const cplx<T> a = B[r * P::ZP + z], b = B[r * P::ZP + z + 1];
+    v[0] = a.x;
+    v[1] = a.y;
+    v[2] = b.x;
+    v[3] = b.y;
+  }
+}
+
+template <typename T> struct Pair2;
+template <> struct Pair2<float> { using type = float2; };
+template <> struct Pair2<double> { using type = double2; };
+
 // Bucket ranges of the plane's two point sets: side 0 has its lower CIC
 // corner on this plane (bucket ix), side 1 its upper corner (bucket ix-1).
 struct PlaneBuckets {
@@ -162,17 +208,7 @@ k_plane_r2c(const T* __restrict__ in, long long in_stride, cplx<T>* __restrict__
   const int ix = blockIdx.x;
   const int s = blockIdx.y;
   if constexpr (!SCATTER) {
-    const T* src = in + (long long)s * in_stride + (long long)ix * N * N;
-    using V = typename Vec16<T>::type;
-    constexpr int VW = Vec16<T>::W;
-    const V* srcv = reinterpret_cast<const V*>(src);
-    for (int e = threadIdx.x; e < N * N / VW; e += NT) {
-      V v = __ldg(&srcv[e]);
-      const int y = (e * VW) / N, z0 = (e * VW) % N;
-      T* zr = reinterpret_cast<T*>(&B[(y >> 1) * ZP + z0]) + (y & 1);
-#pragma unroll
-      for (int q = 0; q < VW; ++q) zr[2 * q] = vget<T>(v, q);
-    }
+    load_plane_packed<T, N>(B, in + (long long)s * in_stride + (long long)ix * N * N);
   } else {
     for (int e = threadIdx.x; e < P::SIZE; e += NT) B[e] = C{(T)0, (T)0};
     __syncthreads();
@@ -238,21 +274,16 @@ k_plane_c2r(const cplx<T>* __restrict__ in, long long in_stride, T* __restrict__
   fft_smem<T, N, true, P::NH, NT, true>(B, 1, P::NH, tw);
   pack_rows<T, N>(B);
   fft_smem<T, N, true, N / 2, NT, false>(B, ZP, 1, tw);
-  using V = typename Vec16<T>::type;
-  constexpr int VW = Vec16<T>::W;
+  using V2 = typename Pair2<T>::type;
+  constexpr int ITEMS = (N / 2) * (N / 2);
   if constexpr (MODE == C2R_STORE) {
     T* dst = out + (long long)s * out_stride + (long long)ix * N * N;
-    V* dstv = reinterpret_cast<V*>(dst);
-    for (int e = threadIdx.x; e < N * N / VW; e += NT) {
-      const int y = (e * VW) / N, z0 = (e * VW) % N;
-      const T* zr = reinterpret_cast<const T*>(&B[(y >> 1) * ZP + z0]) + (y & 1);
-      T t[VW];
-#pragma unroll
-      for (int q = 0; q < VW; ++q) t[q] = zr[2 * q];
-      V v;
-      if constexpr (VW == 4) v = V{t[0], t[1], t[2], t[3]};
-      else v = V{t[0], t[1]};
-      dstv[e] = v;
+    for (int e = threadIdx.x; e < ITEMS; e += NT) {
+      const int r = e / (N / 2), z = 2 * (e % (N / 2));
+      T v[4];
+      read_item<T, N>(B, r, z, v);
+      *reinterpret_cast<V2*>(dst + (2 * r) * N + z) = V2{v[0], v[2]};
+      *reinterpret_cast<V2*>(dst + (2 * r + 1) * N + z) = V2{v[1], v[3]};
     }
   } else if constexpr (MODE == C2R_GATHER) {
     const int c = s / 3, j = s % 3;
@@ -290,49 +321,31 @@ k_plane_c2r(const cplx<T>* __restrict__ in, long long in_stride, T* __restrict__
     const int mode = epi.mode;
     const T eps = (T)epi.cs[s].eps;
     const T ck = (mode == GM_KICK_DRIFT) ? eps : (T)0.5 * eps;
-    double acc_w = 0.0, acc_p = 0.0;
-    V* wv = reinterpret_cast<V*>(w);
-    V* pv = reinterpret_cast<V*>(pw);
-    V* gv = reinterpret_cast<V*>(gw);
-    for (int e = threadIdx.x; e < N * N / VW; e += NT) {
-      const int y = (e * VW) / N, z0 = (e * VW) % N;
-      const T* zr = reinterpret_cast<const T*>(&B[(y >> 1) * ZP + z0]) + (y & 1);
-      V wq = wv[e];
-      T wt[VW], pt[VW], gt[VW];
-      V pq;
-      if (mode != GM_GRAD) pq = pv[e];
+    HalfSqAcc<T> aw, ap;
+    for (int e = threadIdx.x; e < ITEMS; e += NT) {
+      const int r = e / (N / 2), z = 2 * (e % (N / 2));
+      T g[4];
+      read_item<T, N>(B, r, z, g);
 #pragma unroll
-      for (int q = 0; q < VW; ++q) {
-        const T wi = vget<T>(wq, q);
-        const T g = wi + zr[2 * q];
-        acc_w += 0.5 * (double)wi * (double)wi;
-        gt[q] = g;
+      for (int h = 0; h < 2; ++h) {   // row 2r + h, columns z, z + 1
+        const long long o = (long long)(2 * r + h) * N + z;
+        const V2 wq = *reinterpret_cast<const V2*>(w + o);
+        const T w0 = wq.x, w1 = wq.y;
+        const T g0 = w0 + g[h], g1 = w1 + g[2 + h];
+        aw.add_half_sq(w0);
+        aw.add_half_sq(w1);
+        if (mode == GM_GRAD || mode == GM_KICK_LAST) *reinterpret_cast<V2*>(gw + o) = V2{g0, g1};
         if (mode != GM_GRAD) {
-          T p = vget<T>(pq, q) - ck * g;
-          pt[q] = p;
-          wt[q] = (mode == GM_KICK_LAST) ? wi : wi + eps * p;
-          acc_p += 0.5 * (double)p * (double)p;
+          const V2 pq = *reinterpret_cast<const V2*>(pw + o);
+          const T p0 = pq.x - ck * g0, p1 = pq.y - ck * g1;
+          *reinterpret_cast<V2*>(pw + o) = V2{p0, p1};
+          ap.add_half_sq(p0);
+          ap.add_half_sq(p1);
+          if (mode == GM_KICK_DRIFT) *reinterpret_cast<V2*>(w + o) = V2{w0 + eps * p0, w1 + eps * p1};
         }
-      }
-      if (mode == GM_GRAD || mode == GM_KICK_LAST) {
-        V g;
-        if constexpr (VW == 4) g = V{gt[0], gt[1], gt[2], gt[3]};
-        else g = V{gt[0], gt[1]};
-        gv[e] = g;
-      }
-      if (mode != GM_GRAD) {
-        V p, ww;
-        if constexpr (VW == 4) {
-          p = V{pt[0], pt[1], pt[2], pt[3]};
-          ww = V{wt[0], wt[1], wt[2], wt[3]};
-        } else {
-          p = V{pt[0], pt[1]};
-          ww = V{wt[0], wt[1]};
-        }
-        pv[e] = p;
-        if (mode != GM_KICK_LAST) wv[e] = ww;
       }
     }
+    double acc_w = aw.value(), acc_p = ap.value();
     // deterministic block reduction: warp shuffles, then thread 0 in order
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {

@@ -6,6 +6,7 @@
 // hamilton, M_ab).
 #include "hm_fft.cuh"
 #include "hm_internal.h"
+#include "hm_device.cuh"
 #include "hamlet.h"
 
 namespace hm {
@@ -104,7 +105,7 @@ k_traj_begin_field(long long n3, T* __restrict__ w, T* __restrict__ pw, const T*
   const T eps = (T)cs[c].eps;
   const unsigned traj = (unsigned)cs[c].traj;
   const unsigned cid = (unsigned)chain_id[c];
-  double kin = 0.0;
+  HalfSqAcc<T> kin;
   const long long npair = n3 / 2;
   for (long long q = (long long)blockIdx.x * kEwNT + threadIdx.x; q < npair;
        q += (long long)gridDim.x * kEwNT) {
@@ -118,7 +119,7 @@ k_traj_begin_field(long long n3, T* __restrict__ w, T* __restrict__ pw, const T*
     }
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
-      kin += 0.5 * (double)p[h] * (double)p[h];
+      kin.add_half_sq(p[h]);
       const T wi = w[e + h], gi = gw[e + h];
       w0[e + h] = wi;
       gw0[e + h] = gi;
@@ -127,7 +128,7 @@ k_traj_begin_field(long long n3, T* __restrict__ w, T* __restrict__ pw, const T*
       w[e + h] = wi + eps * ph;
     }
   }
-  const double s = block_sum2<T>(kin, red);
+  const double s = block_sum2<T>(kin.value(), red);
   if (threadIdx.x == 0) kin_part[(long long)c * gridDim.x + blockIdx.x] = s;
 }
 
@@ -157,15 +158,23 @@ k_traj_begin_points(const PointParams* __restrict__ pp, PointArrays pa, double* 
       const double di = pa.d[i], gi = pa.gd[i];
       d0[i] = di;
       gd0[i] = gi;
+      double dn = di;
       if (sd) {
         const double p = draw ? nn[h] / sqrt(P.minv_d) : pa.pd[i];
         kin += 0.5 * P.minv_d * p * p;
         const double ph = p - 0.5 * eps * gi;
         pa.pd[i] = ph;
-        pa.d[i] = di + eps * P.minv_d * ph;
+        dn = di + eps * P.minv_d * ph;
+        pa.d[i] = dn;
       } else {
         pa.pd[i] = 0.0;
       }
+      // buckets of the drifted distances for the first evaluation
+      int cx;
+      double f;
+      cell_axis(P.obs[0], placeable(dn), pa.rx[i], P.delta, P.N, cx, f);
+      pa.cx[i] = cx;
+      pa.slot[i] = atomicAdd(&pa.cnt_next[c * P.N + cx], 1);
     }
   }
   const double s = block_sum2<double>(kin, red);
@@ -175,30 +184,40 @@ k_traj_begin_points(const PointParams* __restrict__ pp, PointArrays pa, double* 
 // ---------------------------------------------------------------------------
 // Per-chain scalar finalisation (one CTA per chain, fixed summation order).
 // ---------------------------------------------------------------------------
+// Fixed-order sum of n values by one warp: lane l adds l, l+32, ... in order,
+// then a fixed shuffle tree; lane 0 gets the result.
+__device__ __forceinline__ double warp_sum_fixed(const double* __restrict__ x, int n) {
+  double s = 0.0;
+  for (int i = threadIdx.x; i < n; i += 32) s += x[i];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  return s;
+}
+
 __global__ void k_finalize(const double* __restrict__ prior_part, int n_prior,
                            const double* __restrict__ pts_part, int n_pts,
                            const double* __restrict__ kin_part, int n_kin,
                            const double* __restrict__ kin_pts_part, int n_kin_pts, int what,
                            unsigned long long seed, const int* __restrict__ chain_id,
                            ChainScal* __restrict__ cs, hm_trace* __restrict__ trace) {
-  if (threadIdx.x != 0) return;
   const int c = blockIdx.x;
+  double a = 0.0, b = 0.0, k = 0.0, kp = 0.0;
+  if (what & FIN_PSI) {
+    a = warp_sum_fixed(prior_part + (long long)c * n_prior, n_prior);
+    b = warp_sum_fixed(pts_part + (long long)c * n_pts, n_pts);
+  }
+  if (what & (FIN_HOLD | FIN_ACCEPT | FIN_KIN)) {
+    k = warp_sum_fixed(kin_part + (long long)c * n_kin, n_kin);
+    kp = warp_sum_fixed(kin_pts_part + (long long)c * n_kin_pts, n_kin_pts);
+  }
+  if (threadIdx.x != 0) return;
   ChainScal& S = cs[c];
   if (what & FIN_PSI) {
-    double a = 0.0, b = 0.0;
-    for (int i = 0; i < n_prior; ++i) a += prior_part[(long long)c * n_prior + i];
-    for (int i = 0; i < n_pts; ++i) b += pts_part[(long long)c * n_pts + i];
     S.psi_prior = a;
     S.psi_pts = b;
     S.psi = a + b;
   }
-  if (what & (FIN_HOLD | FIN_ACCEPT | FIN_KIN)) {
-    double k = 0.0;
-    for (int i = 0; i < n_kin; ++i) k += kin_part[(long long)c * n_kin + i];
-    if (S.sample_d)
-      for (int i = 0; i < n_kin_pts; ++i) k += kin_pts_part[(long long)c * n_kin_pts + i];
-    S.kin = k;
-  }
+  if (what & (FIN_HOLD | FIN_ACCEPT | FIN_KIN)) S.kin = S.sample_d ? k + kp : k;
   if (what & FIN_HOLD) {
     S.psi0 = S.psi;
     S.H_old = S.psi + S.kin;

@@ -90,10 +90,12 @@ struct PointArrays {
   int* cx;        // x index of the lower corner (bucket), per point
   int* slot;      // rank inside the bucket (atomic order), per point
   int* pos;       // position in bucket order, per point
-  int* cnt;       // [C][N] bucket sizes (zeroed before every evaluation)
+  int* cnt;       // [C][N] bucket sizes of the current distances
+  int* cnt_next;  // [C][N] bucket sizes being counted for the next evaluation
   int* off;       // [C][N+1] bucket starts in the global bucket order
   void* rec;      // PtRec<T> [ntot] in bucket order
   void* part;     // T [12][ntot]: per (side, component) u and du partials, bucket order
+  double* lk;     // [6][ntot] terms of the point likelihood that depend on d only
   long long ntot;
 };
 
@@ -133,16 +135,20 @@ bool fft_supported(int prec, int N);
 cudaError_t fft_prepare(int prec, int N);
 
 // ---- points (hm_points.cu) ----
-// bucket counts (x index of the lower corner) at the current distances
+// bucket counts (x index of the lower corner) of the current distances into pa.cnt
 cudaError_t launch_points_prep(int n_chains, int max_pts, const PointParams* pp, PointArrays pa,
                                cudaStream_t st);
-// bucket offsets, full cells and the bucket-ordered point records
+// bucket offsets, full cells, bucket-ordered records, and the FP64 terms of
+// the likelihood that depend on d alone (distance modulus, observed velocity,
+// kappa, prior) with their derivatives
 cudaError_t launch_points_place(int prec, int n_chains, int max_pts, const PointParams* pp,
-                                PointArrays pa, cudaStream_t st);
-// u, du from the partials; FP64 likelihood, residuals, distance gradient
+                                PointArrays pa, ChainScal* cs, cudaStream_t st);
+// u, du from the plane partials, the velocity term, residuals, distance
+// gradient and Psi partials; zeroes pa.cnt_next for the kick's counting
 cudaError_t launch_points_lik(int prec, int n_chains, int max_pts, const PointParams* pp, PointArrays pa,
-                              double* pts_part, int part_stride, ChainScal* cs, cudaStream_t st);
-// p_d/d update after the gradient (mode as GradMode) and kinetic partials.
+                              double* pts_part, int part_stride, cudaStream_t st);
+// p_d/d update after the gradient (mode as GradMode), kinetic partials, and
+// (GM_KICK_DRIFT) the bucket counts of the new distances into pa.cnt_next.
 cudaError_t launch_points_kick(int n_chains, int max_pts, const PointParams* pp, PointArrays pa,
                                int mode, double* kin_part, int part_stride, ChainScal* cs,
                                cudaStream_t st);
@@ -158,6 +164,7 @@ cudaError_t launch_traj_begin_field(int prec, int n_chains, long long n3, void* 
                                     const void* gw, void* w0, void* gw0, unsigned long long seed,
                                     const int* chain_id, double* kin_part, int nparts, int draw,
                                     ChainScal* cs, cudaStream_t st);
+// also counts the drifted distances into pa.cnt_next (zeroed beforehand)
 cudaError_t launch_traj_begin_points(int n_chains, int max_pts, const PointParams* pp,
                                      PointArrays pa, double* d0, double* gd0,
                                      unsigned long long seed, const int* chain_id,

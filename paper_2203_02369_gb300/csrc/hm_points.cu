@@ -5,29 +5,11 @@
 // update of the distances (mass matrix eq. M_ab: (sigma_v/H0)^2 for d).
 #include "hm_fft.cuh"
 #include "hm_internal.h"
+#include "hm_device.cuh"
 
 namespace hm {
 
 constexpr int kPtsNT = 128;
-
-// Lower-corner cell and fractional offsets of x = o + d rhat, formed as
-// t = (o + d*r)/Delta with one IEEE rounding per operation (no contraction),
-// so that the cell indices are reproducible bit for bit on any IEEE host.
-struct CellPos {
-  int ix, iy, iz;
-  double fx, fy, fz;
-};
-
-__device__ __forceinline__ void cell_axis(double o, double d, double r, double delta, int N, int& i,
-                                          double& f) {
-  const double t = __ddiv_rn(__dadd_rn(o, __dmul_rn(d, r)), delta);
-  const double fl = floor(t);
-  f = __dadd_rn(t, -fl);
-  long long ii = (long long)fl;
-  ii %= N;
-  if (ii < 0) ii += N;
-  i = (int)ii;
-}
 
 __device__ __forceinline__ CellPos cell_of(const PointParams& P, double d, double rx, double ry, double rz) {
   CellPos c;
@@ -82,13 +64,6 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
   return s;
 }
 
-// A distance that cannot be placed on the grid (non-finite or absurdly
-// large) is bucketed as if it sat at the observer; its likelihood term is
-// +inf and its residual 0, so the plane passes ignore it.
-__device__ __forceinline__ double placeable(double d) {
-  return (isfinite(d) && fabs(d) < 1e7) ? d : 0.0;
-}
-
 // ---------------------------------------------------------------------------
 // Bucketing by the x index of the lower CIC corner: counts (and the rank of
 // each point inside its bucket, in atomic order) ...
@@ -107,10 +82,14 @@ k_points_prep(const PointParams* __restrict__ pp, PointArrays pa) {
   pa.slot[i] = atomicAdd(&pa.cnt[c * P.N + cx], 1);
 }
 
-// ... then the bucket offsets and the bucket-ordered point records.
+// ... then the bucket offsets, the bucket-ordered point records, and the
+// d-only FP64 likelihood terms:
+//   lk[0] = A   = (mu_i - mu(d))^2/(2 s_mu^2) + ln kappa - ln pi_D(d)  (+inf outside)
+//   lk[1] = A'  = dA/dd
+//   lk[2] = v_obs(d), lk[3] = v_obs'(d), lk[4] = 1/kappa^2, lk[5] = (kappa^2)'
 template <typename T>
 __global__ void __launch_bounds__(kPtsNT)
-k_points_place(const PointParams* __restrict__ pp, PointArrays pa) {
+k_points_place(const PointParams* __restrict__ pp, PointArrays pa, ChainScal* __restrict__ cs) {
   __shared__ int excl[257];
   const int c = blockIdx.y;
   const PointParams& P = pp[c];
@@ -130,7 +109,8 @@ k_points_place(const PointParams* __restrict__ pp, PointArrays pa) {
   if (il >= P.pt_n) return;
   const long long i = P.pt_off + il;
   const double rx = pa.rx[i], ry = pa.ry[i], rz = pa.rz[i];
-  const CellPos cp = cell_of(P, placeable(pa.d[i]), rx, ry, rz);
+  const double d = pa.d[i];
+  const CellPos cp = cell_of(P, placeable(d), rx, ry, rz);
   // the bucket and rank come from the counting pass (same arithmetic, same d)
   const int pos = (int)P.pt_off + excl[pa.cx[i]] + pa.slot[i];
   pa.pos[i] = pos;
@@ -144,71 +124,90 @@ k_points_place(const PointParams* __restrict__ pp, PointArrays pa) {
   r.yz = cp.iy * N + cp.iz;
   r.r = (T)0;
   static_cast<PtRec<T>*>(pa.rec)[pos] = r;
+  // likelihood terms that depend on d only (eqs. lmu, vrobs, kappa, D)
+  const double om = P.omega_m;
+  const double x = 1.0 - 3.0 * om * kH0 * d / kC;
+  double lp = 0.0, dlp = 0.0;
+  const bool ok = d > 0.0 && x > 0.0 && log_prior(P, d, lp, dlp);
+  const long long nt = pa.ntot;
+  if (!ok) {
+    pa.lk[i] = __longlong_as_double(0x7ff0000000000000LL);  // +inf
+    pa.lk[nt + i] = 0.0;
+    pa.lk[2 * nt + i] = 0.0;
+    pa.lk[3 * nt + i] = 0.0;
+    pa.lk[4 * nt + i] = 0.0;
+    pa.lk[5 * nt + i] = 0.0;
+    atomicOr(&cs[c].status, STATUS_DOMAIN);
+    return;
+  }
+  const double sq = sqrt(x);
+  const double zb = 2.0 / (3.0 * om) * (1.0 - sq);
+  const double zbp = (kH0 / kC) / sq;
+  const double opz = 1.0 + zb;
+  const double iopz = 1.0 / opz;
+  const double mu_d = 5.0 * log10(d * opz / P.h) + 25.0;
+  const double mup = (5.0 / 2.302585092994045684) * (1.0 / d + zbp * iopz);
+  const double z = pa.zobs[i];
+  const double scz = pa.scz[i];
+  const double scz2 = scz * scz;
+  const double k2 = P.sigma_nl2 + scz2 * iopz * iopz;
+  const double ik2 = 1.0 / k2;
+  const double k2p = -2.0 * scz2 * zbp * iopz * iopz * iopz;
+  const double smu = pa.smu[i];
+  const double ismu2 = 1.0 / (smu * smu);
+  const double res_mu = pa.mu[i] - mu_d;
+  pa.lk[i] = 0.5 * res_mu * res_mu * ismu2 + 0.5 * log(k2) - lp;
+  pa.lk[nt + i] = -res_mu * mup * ismu2 + 0.5 * k2p * ik2 - dlp;
+  pa.lk[2 * nt + i] = kC * (z - zb) * iopz;
+  pa.lk[3 * nt + i] = -kC * zbp * (1.0 + z) * iopz * iopz;
+  pa.lk[4 * nt + i] = ik2;
+  pa.lk[5 * nt + i] = k2p;
 }
 
 // ---------------------------------------------------------------------------
-// Likelihood: u and du from the plane partials, then the FP64 point terms.
+// Velocity term: u and du from the plane partials, then
+//   Psi_i = A + (v_obs - u)^2/(2 kappa^2),  r_i = -(v_obs - u)/kappa^2,
+//   dPsi_i/dd = A' + (v_obs - u)(v_obs' - u')/kappa^2 - (v_obs - u)^2 (kappa^2)'/(2 kappa^4).
 // ---------------------------------------------------------------------------
 template <typename T>
 __global__ void __launch_bounds__(kPtsNT)
 k_points_lik(const PointParams* __restrict__ pp, PointArrays pa, double* __restrict__ pts_part,
-             int part_stride, ChainScal* __restrict__ cs) {
+             int part_stride) {
   __shared__ double red[kPtsNT / 32];
   const int c = blockIdx.y;
   const PointParams& P = pp[c];
+  if (blockIdx.x == 0)
+    for (int b = threadIdx.x; b < P.N; b += kPtsNT) pa.cnt_next[c * P.N + b] = 0;
   const long long il = (long long)blockIdx.x * kPtsNT + threadIdx.x;
   double psi_i = 0.0;
-  int bad = 0;
   if (il < P.pt_n) {
     const long long i = P.pt_off + il;
+    const long long nt = pa.ntot;
     const int pos = pa.pos[i];
-    const T* part = static_cast<const T*>(pa.part);
-    double u = 0.0, du = 0.0;
-#pragma unroll
-    for (int k = 0; k < 6; ++k) {
-      u += (double)part[(long long)k * pa.ntot + pos];
-      du += (double)part[(long long)(6 + k) * pa.ntot + pos];
-    }
-    const double d = pa.d[i];
-    const double om = P.omega_m;
-    const double x = 1.0 - 3.0 * om * kH0 * d / kC;
-    double lp = 0.0, dlp = 0.0;
-    const bool ok = d > 0.0 && x > 0.0 && log_prior(P, d, lp, dlp);
+    const double A = pa.lk[i];
     PtRec<T>* rec = static_cast<PtRec<T>*>(pa.rec);
-    if (!ok) {
-      psi_i = __longlong_as_double(0x7ff0000000000000LL);  // +inf
+    if (!isfinite(A)) {
+      psi_i = A;
       rec[pos].r = (T)0;
       pa.gd[i] = 0.0;
-      bad = 1;
     } else {
-      const double sq = sqrt(x);
-      const double zb = 2.0 / (3.0 * om) * (1.0 - sq);
-      const double zbp = (kH0 / kC) / sq;
-      const double opz = 1.0 + zb;
-      const double iopz = 1.0 / opz;
-      const double mu_d = 5.0 * log10(d * opz / P.h) + 25.0;
-      const double mup = (5.0 / 2.302585092994045684) * (1.0 / d + zbp * iopz);
-      const double z = pa.zobs[i];
-      const double vo = kC * (z - zb) * iopz;
-      const double vop = -kC * zbp * (1.0 + z) * iopz * iopz;
-      const double scz = pa.scz[i];
-      const double scz2 = scz * scz;
-      const double k2 = P.sigma_nl2 + scz2 * iopz * iopz;
-      const double ik2 = 1.0 / k2;
-      const double k2p = -2.0 * scz2 * zbp * iopz * iopz * iopz;
-      const double smu = pa.smu[i];
-      const double ismu2 = 1.0 / (smu * smu);
-      const double res_mu = pa.mu[i] - mu_d;
+      const T* part = static_cast<const T*>(pa.part);
+      double u = 0.0, du = 0.0;
+#pragma unroll
+      for (int k = 0; k < 6; ++k) {
+        u += (double)part[(long long)k * nt + pos];
+        du += (double)part[(long long)(6 + k) * nt + pos];
+      }
+      const double vo = pa.lk[2 * nt + i], vop = pa.lk[3 * nt + i];
+      const double ik2 = pa.lk[4 * nt + i], k2p = pa.lk[5 * nt + i];
       const double res_v = vo - u;
-      psi_i = 0.5 * res_mu * res_mu * ismu2 + 0.5 * res_v * res_v * ik2 + 0.5 * log(k2) - lp;
+      psi_i = A + 0.5 * res_v * res_v * ik2;
       rec[pos].r = (T)(-res_v * ik2);
-      pa.gd[i] = -res_mu * mup * ismu2 + res_v * (vop - du) * ik2 -
-                 0.5 * res_v * res_v * k2p * ik2 * ik2 + 0.5 * k2p * ik2 - dlp;
+      pa.gd[i] = pa.lk[nt + i] + res_v * (vop - du) * ik2 - 0.5 * res_v * res_v * k2p * ik2 * ik2;
     }
   }
   const double s = block_sum(psi_i, red);
   if (threadIdx.x == 0) pts_part[(long long)c * part_stride + blockIdx.x] = s;
-  if (bad) atomicOr(&cs[c].status, STATUS_DOMAIN);
 }
 
 // ---------------------------------------------------------------------------
@@ -223,13 +222,27 @@ k_points_kick(const PointParams* __restrict__ pp, PointArrays pa, int mode, doub
   const long long il = (long long)blockIdx.x * kPtsNT + threadIdx.x;
   double k = 0.0;
   const double eps = cs[c].eps;
-  if (il < P.pt_n && cs[c].sample_d) {
+  if (il < P.pt_n) {
     const long long i = P.pt_off + il;
-    const double ck = (mode == GM_KICK_DRIFT) ? eps : 0.5 * eps;
-    double p = pa.pd[i] - ck * pa.gd[i];
-    pa.pd[i] = p;
-    if (mode == GM_KICK_DRIFT) pa.d[i] = pa.d[i] + eps * P.minv_d * p;
-    k = 0.5 * P.minv_d * p * p;
+    double d = pa.d[i];
+    if (cs[c].sample_d) {
+      const double ck = (mode == GM_KICK_DRIFT) ? eps : 0.5 * eps;
+      const double p = pa.pd[i] - ck * pa.gd[i];
+      pa.pd[i] = p;
+      if (mode == GM_KICK_DRIFT) {
+        d = d + eps * P.minv_d * p;
+        pa.d[i] = d;
+      }
+      k = 0.5 * P.minv_d * p * p;
+    }
+    if (mode == GM_KICK_DRIFT) {
+      // buckets of the drifted distances, for the next evaluation
+      int cx;
+      double f;
+      cell_axis(P.obs[0], placeable(d), pa.rx[i], P.delta, P.N, cx, f);
+      pa.cx[i] = cx;
+      pa.slot[i] = atomicAdd(&pa.cnt_next[c * P.N + cx], 1);
+    }
   }
   if (mode == GM_KICK_LAST) {
     const double s = block_sum(k, red);
@@ -336,19 +349,19 @@ cudaError_t launch_points_prep(int n_chains, int max_pts, const PointParams* pp,
 }
 
 cudaError_t launch_points_place(int prec, int n_chains, int max_pts, const PointParams* pp,
-                                PointArrays pa, cudaStream_t st) {
+                                PointArrays pa, ChainScal* cs, cudaStream_t st) {
   // runs even without points: block 0 writes the (empty) bucket offsets
-  if (prec == 0) k_points_place<float><<<pts_grid(n_chains, max_pts), kPtsNT, 0, st>>>(pp, pa);
-  else k_points_place<double><<<pts_grid(n_chains, max_pts), kPtsNT, 0, st>>>(pp, pa);
+  if (prec == 0) k_points_place<float><<<pts_grid(n_chains, max_pts), kPtsNT, 0, st>>>(pp, pa, cs);
+  else k_points_place<double><<<pts_grid(n_chains, max_pts), kPtsNT, 0, st>>>(pp, pa, cs);
   return cudaGetLastError();
 }
 
 cudaError_t launch_points_lik(int prec, int n_chains, int max_pts, const PointParams* pp, PointArrays pa,
-                              double* pts_part, int part_stride, ChainScal* cs, cudaStream_t st) {
+                              double* pts_part, int part_stride, cudaStream_t st) {
   if (prec == 0)
-    k_points_lik<float><<<pts_grid(n_chains, max_pts), kPtsNT, 0, st>>>(pp, pa, pts_part, part_stride, cs);
+    k_points_lik<float><<<pts_grid(n_chains, max_pts), kPtsNT, 0, st>>>(pp, pa, pts_part, part_stride);
   else
-    k_points_lik<double><<<pts_grid(n_chains, max_pts), kPtsNT, 0, st>>>(pp, pa, pts_part, part_stride, cs);
+    k_points_lik<double><<<pts_grid(n_chains, max_pts), kPtsNT, 0, st>>>(pp, pa, pts_part, part_stride);
   return cudaGetLastError();
 }
 
