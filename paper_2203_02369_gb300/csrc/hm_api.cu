@@ -206,6 +206,7 @@ struct PtWork {
     if (aux) cudaStreamDestroy(aux);
   }
   int alloc(int prec, int C, int N, long long ntot) {
+    N *= plane_split(N);   // sub-buckets per chain
     const size_t nt = (size_t)std::max<long long>(ntot, 1);
     const size_t rsz = prec == HM_FP32 ? 4 : 8;
     const size_t recsz = prec == HM_FP32 ? sizeof(PtRec<float>) : sizeof(PtRec<double>);
@@ -263,6 +264,7 @@ struct hm_problem {
 
 struct hm_state {
   int C = 0, N = 0, prec = 0, device = 0;
+  int NP = 0;    // plane-pass partial sums per chain: N planes * CTAs per plane
   long long n3 = 0, nspec = 0, ntot = 0;
   int max_pts = 0, pts_blocks = 1;
   int nparts_f = 1, nparts_p = 1;
@@ -317,6 +319,8 @@ static PointParams point_params(const hm_problem* p, long long off) {
   P.sigma_nl2 = p->desc.sigma_nl * p->desc.sigma_nl;
   P.minv_d = p->minv_d;
   P.N = p->N;
+  P.ksplit = plane_split(p->N);
+  P.rq = p->N / P.ksplit;
   P.prior_kind = p->desc.prior_kind;
   P.prior_nbins = p->desc.prior_nbins;
   P.prior_d0 = p->desc.prior_d0;
@@ -373,7 +377,7 @@ static int grad_eval(const GradArgs& a0, int mode, cudaStream_t st, int parity, 
   HM_CUDA(cudaEventRecord(wk.fork, st));
   HM_CUDA(cudaStreamWaitEvent(ax, wk.fork, 0));
   if (count_first) {
-    HM_PROF(pf, KK_MEMSET_CNT, ax, cudaMemsetAsync(a.pa.cnt, 0, sizeof(int) * (size_t)a.C * a.N, ax));
+    HM_PROF(pf, KK_MEMSET_CNT, ax, cudaMemsetAsync(a.pa.cnt, 0, sizeof(int) * (size_t)wk.CN, ax));
     HM_PROF(pf, KK_PREP, ax, launch_points_prep(a.C, a.max_pts, a.pp, a.pa, ax));
   }
   HM_PROF(pf, KK_PLACE, ax, launch_points_place(a.prec, a.C, a.max_pts, a.pp, a.pa, a.cs, ax));
@@ -427,6 +431,7 @@ int hm_init_problem(const hm_problem_desc* desc, hm_problem** out) {
   const hm_problem_desc& d = *desc;
   if (d.precision != HM_FP32 && d.precision != HM_FP64) return fail(HM_EINVAL, "precision must be HM_FP32 or HM_FP64");
   if (!fft_supported(d.precision, d.N)) return fail(HM_EINVAL, "unsupported grid size N for this precision");
+  if (d.N * plane_split(d.N) >= 1024) return fail(HM_EINVAL, "too many point buckets per chain for this N");
   if (!(d.L > 0) || !(d.omega_m > 0) || !(d.omega_b > 0) || !(d.h > 0) || !(d.sigma8 > 0) ||
       !(d.T_cmb > 0) || !std::isfinite(d.n_s) || !(d.sigma_nl >= 0))
     return fail(HM_EINVAL, "bad cosmology or box parameters");
@@ -573,10 +578,10 @@ static int ensure_ws(hm_problem* p) {
   HM_TRY(p->S1.alloc(2 * p->rsz * 3 * p->nspec));
   HM_TRY(p->S2.alloc(2 * p->rsz * 3 * p->nspec));
   HM_TRY(p->pw.alloc(p->prec, 1, N, p->n));
-  HM_TRY(p->prior_part.alloc(8 * N));
+  HM_TRY(p->prior_part.alloc(8 * N * plane_split(N)));
   const int pb = points_blocks((int)p->n);
   HM_TRY(p->pts_part.alloc(8 * pb));
-  HM_TRY(p->kin_part.alloc(8 * std::max(N, pb)));
+  HM_TRY(p->kin_part.alloc(8 * std::max(N * plane_split(N), pb)));
   HM_TRY(p->pp.alloc(sizeof(PointParams)));
   HM_TRY(p->cs.alloc(sizeof(ChainScal)));
   HM_TRY(p->chain_id.alloc(sizeof(int)));
@@ -637,7 +642,7 @@ int hm_logpost_grad(hm_problem* p, const void* w_dev, const double* d_dev, doubl
   a.cs = cs;
   a.work = &p->pw;
   HM_TRY(grad_eval(a, GM_GRAD, st, 0, true));
-  HM_CUDA(launch_finalize(1, a.prior_part, p->N, a.pts_part, a.pts_blocks, nullptr, 0, nullptr, 0, FIN_PSI,
+  HM_CUDA(launch_finalize(1, a.prior_part, p->N * plane_split(p->N), a.pts_part, a.pts_blocks, nullptr, 0, nullptr, 0, FIN_PSI,
                           0ull, p->chain_id.as<int>(), cs, nullptr, st));
   HM_CUDA(cudaMemcpyAsync(psi_dev, &cs->psi, sizeof(double), cudaMemcpyDeviceToDevice, st));
   return HM_OK;
@@ -753,7 +758,7 @@ static GradArgs state_args(hm_state* s) {
 static int state_refresh(hm_state* s, cudaStream_t st) {
   GradArgs a = state_args(s);
   HM_TRY(grad_eval(a, GM_GRAD, st, 0, true));
-  HM_CUDA(launch_finalize(s->C, a.prior_part, s->N, a.pts_part, s->pts_blocks, nullptr, 0, nullptr, 0, FIN_PSI,
+  HM_CUDA(launch_finalize(s->C, a.prior_part, s->NP, a.pts_part, s->pts_blocks, nullptr, 0, nullptr, 0, FIN_PSI,
                           s->seed, s->chain_id.as<int>(), a.cs, nullptr, st));
   return HM_OK;
 }
@@ -774,6 +779,7 @@ int hm_state_create_batch(hm_problem* const* problems, int32_t n_problems, int32
   auto s = std::make_unique<hm_state>();
   s->C = n_chains;
   s->N = p0->N;
+  s->NP = p0->N * plane_split(p0->N);
   s->prec = p0->prec;
   s->device = p0->device;
   s->n3 = p0->n3;
@@ -847,11 +853,11 @@ int hm_state_create_batch(hm_problem* const* problems, int32_t n_problems, int32
   for (int c = 0; c < n_chains; ++c) ids[c] = chain_ids ? chain_ids[c] : c;
   HM_TRY(s->chain_id.alloc(sizeof(int) * C));
   HM_CUDA(cudaMemcpy(s->chain_id.p, ids.data(), sizeof(int) * C, cudaMemcpyHostToDevice));
-  HM_TRY(s->prior_part.alloc(8 * C * s->N));
+  HM_TRY(s->prior_part.alloc(8 * C * s->NP));
   HM_TRY(s->pts_part.alloc(8 * C * s->pts_blocks));
   HM_TRY(s->kinb_f.alloc(8 * C * s->nparts_f));
   HM_TRY(s->kinb_p.alloc(8 * C * s->nparts_p));
-  HM_TRY(s->kinl_f.alloc(8 * C * s->N));
+  HM_TRY(s->kinl_f.alloc(8 * C * s->NP));
   HM_TRY(s->kinl_p.alloc(8 * C * s->pts_blocks));
   HM_CUDA(cudaMemset(s->kinl_p.p, 0, 8 * C * s->pts_blocks));
   HM_CUDA(cudaMemset(s->kinb_p.p, 0, 8 * C * s->nparts_p));
@@ -967,7 +973,7 @@ static int leapfrog_body(hm_state* s, int n_steps, int draw, cudaStream_t st, Pr
   HM_CUDA(launch_traj_begin_field(s->prec, s->C, s->n3, s->w.p, s->pw.p, s->gw.p, s->w0.p, s->gw0.p, s->seed,
                                   s->chain_id.as<int>(), s->kinb_f.as<double>(), s->nparts_f, draw, a.cs, st));
   if (s->max_pts > 0) {
-    HM_CUDA(cudaMemsetAsync(pa.cnt_next, 0, sizeof(int) * (size_t)s->C * s->N, st));
+    HM_CUDA(cudaMemsetAsync(pa.cnt_next, 0, sizeof(int) * (size_t)s->work.CN, st));
     HM_CUDA(launch_traj_begin_points(s->C, s->max_pts, a.pp, pa, s->d0.as<double>(), s->gd0.as<double>(), s->seed,
                                      s->chain_id.as<int>(), s->kinb_p.as<double>(), s->nparts_p, draw, a.cs, st));
   }
@@ -990,7 +996,7 @@ int hm_leapfrog(hm_state* s, int32_t n_steps, double eps, int32_t sample_distanc
   HM_TRY(set_run(s, e.data(), sample_distances, st));
   HM_TRY(leapfrog_body(s, n_steps, 0, st, nullptr));
   GradArgs a = state_args(s);
-  HM_CUDA(launch_finalize(s->C, a.prior_part, s->N, a.pts_part, s->pts_blocks, a.kinl_f, s->N, a.kinl_p,
+  HM_CUDA(launch_finalize(s->C, a.prior_part, s->NP, a.pts_part, s->pts_blocks, a.kinl_f, s->NP, a.kinl_p,
                           s->max_pts > 0 ? s->pts_blocks : 0, FIN_PSI | FIN_KIN, s->seed, s->chain_id.as<int>(),
                           a.cs, nullptr, st));
   return HM_OK;
@@ -1008,7 +1014,7 @@ static int trajectory(hm_state* s, int n_leapfrog, cudaStream_t st, Prof* pf) {
   HM_TRY(leapfrog_body(s, n_leapfrog, 1, st, pf));
   GradArgs a = state_args(s);
   HM_PROF(pf, KK_FINALIZE, st,
-          launch_finalize(s->C, a.prior_part, s->N, a.pts_part, s->pts_blocks, a.kinl_f, s->N, a.kinl_p,
+          launch_finalize(s->C, a.prior_part, s->NP, a.pts_part, s->pts_blocks, a.kinl_f, s->NP, a.kinl_p,
                           s->max_pts > 0 ? s->pts_blocks : 0, FIN_PSI | FIN_ACCEPT, s->seed,
                           s->chain_id.as<int>(), a.cs, s->trace_dev.p, st));
   HM_PROF(pf, KK_RESTORE, st,

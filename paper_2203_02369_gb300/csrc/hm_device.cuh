@@ -30,4 +30,15 @@ __device__ __forceinline__ double placeable(double d) {
   return (isfinite(d) && fabs(d) < 1e7) ? d : 0.0;
 }
 
+// Bucket key of a point: x-plane of its lower CIC corner, then the CTA of
+// that plane's cluster that owns its row cy.
+__device__ __forceinline__ int bucket_key(const PointParams& P, double d, double rx, double ry) {
+  int cx, cy;
+  double f;
+  const double dd = placeable(d);
+  cell_axis(P.obs[0], dd, rx, P.delta, P.N, cx, f);
+  cell_axis(P.obs[1], dd, ry, P.delta, P.N, cy, f);
+  return cx * P.ksplit + cy / P.rq;
+}
+
 }  // namespace hm

@@ -170,11 +170,9 @@ k_traj_begin_points(const PointParams* __restrict__ pp, PointArrays pa, double* 
         pa.pd[i] = 0.0;
       }
       // buckets of the drifted distances for the first evaluation
-      int cx;
-      double f;
-      cell_axis(P.obs[0], placeable(dn), pa.rx[i], P.delta, P.N, cx, f);
-      pa.cx[i] = cx;
-      pa.slot[i] = atomicAdd(&pa.cnt_next[c * P.N + cx], 1);
+      const int key = bucket_key(P, dn, pa.rx[i], pa.ry[i]);
+      pa.cx[i] = key;
+      pa.slot[i] = atomicAdd(&pa.cnt_next[c * P.N * P.ksplit + key], 1);
     }
   }
   const double s = block_sum2<double>(kin, red);

@@ -11,6 +11,13 @@ constexpr double kH0 = 100.0;      // km/s/(Mpc/h)
 
 enum PriorKind : int { PRIOR_TABLE = 0, PRIOR_POWER = 1 };
 
+// CTAs (one thread-block cluster) per x-plane in the plane passes; the
+// points of a plane are sub-bucketed by the CTA owning their row cy.
+template <int N> struct PlaneSplit {
+  static constexpr int K = N >= 128 ? 4 : (N >= 64 ? 2 : 1);
+};
+int plane_split(int N);
+
 // Per-chain constants of the point likelihood (device resident).
 struct PointParams {
   double obs[3];
@@ -21,7 +28,8 @@ struct PointParams {
   int N;
   int prior_kind;
   int prior_nbins;
-  int pad0;
+  int ksplit;            // CTAs per plane (sub-buckets per x-plane)
+  int rq;                // rows per CTA, N / ksplit
   double prior_d0, prior_bin;
   const double* prior_logdens;
   double prior_alpha, prior_dmin, prior_dmax;
@@ -87,12 +95,12 @@ struct PointArrays {
   double* d;
   double* pd;
   double* gd;
-  int* cx;        // x index of the lower corner (bucket), per point
+  int* cx;        // bucket key cx*ksplit + cy/rq of the lower corner, per point
   int* slot;      // rank inside the bucket (atomic order), per point
   int* pos;       // position in bucket order, per point
-  int* cnt;       // [C][N] bucket sizes of the current distances
-  int* cnt_next;  // [C][N] bucket sizes being counted for the next evaluation
-  int* off;       // [C][N+1] bucket starts in the global bucket order
+  int* cnt;       // [C][NB] bucket sizes of the current distances (NB = N*ksplit)
+  int* cnt_next;  // [C][NB] bucket sizes being counted for the next evaluation
+  int* off;       // [C][NB+1] bucket starts in the global bucket order
   void* rec;      // PtRec<T> [ntot] in bucket order
   void* part;     // T [12][ntot]: per (side, component) u and du partials, bucket order
   double* lk;     // [6][ntot] terms of the point likelihood that depend on d only
@@ -105,7 +113,7 @@ enum PencilMode : int { PM_FWD = 0, PM_INV = 1, PM_VEL = 2, PM_ADJ = 3 };
 
 // Plane-pass inputs/outputs beyond plain arrays.
 struct PlanePoints {
-  const int* off;       // [C][N+1]
+  const int* off;       // [C][N*K+1]
   const void* rec;      // PtRec<T>, bucket order
   void* part;           // T [12][ntot]
   long long ntot;

@@ -75,11 +75,9 @@ k_points_prep(const PointParams* __restrict__ pp, PointArrays pa) {
   const long long il = (long long)blockIdx.x * kPtsNT + threadIdx.x;
   if (il >= P.pt_n) return;
   const long long i = P.pt_off + il;
-  int cx;
-  double f;
-  cell_axis(P.obs[0], placeable(pa.d[i]), pa.rx[i], P.delta, P.N, cx, f);
-  pa.cx[i] = cx;
-  pa.slot[i] = atomicAdd(&pa.cnt[c * P.N + cx], 1);
+  const int key = bucket_key(P, pa.d[i], pa.rx[i], pa.ry[i]);
+  pa.cx[i] = key;
+  pa.slot[i] = atomicAdd(&pa.cnt[c * P.N * P.ksplit + key], 1);
 }
 
 // ... then the bucket offsets, the bucket-ordered point records, and the
@@ -90,21 +88,47 @@ k_points_prep(const PointParams* __restrict__ pp, PointArrays pa) {
 template <typename T>
 __global__ void __launch_bounds__(kPtsNT)
 k_points_place(const PointParams* __restrict__ pp, PointArrays pa, ChainScal* __restrict__ cs) {
-  __shared__ int excl[257];
+  constexpr int kMaxNB = 1024;          // sub-buckets per chain (N * ksplit)
+  constexpr int PERT = kMaxNB / kPtsNT;
+  __shared__ int excl[kMaxNB + 1];
+  __shared__ int wsum[kPtsNT / 32];
   const int c = blockIdx.y;
   const PointParams& P = pp[c];
   const int N = P.N;
-  if (threadIdx.x == 0) {
-    int acc = 0;
-    for (int b = 0; b < N; ++b) {
-      excl[b] = acc;
-      acc += pa.cnt[c * N + b];
+  const int NB = N * P.ksplit;
+  {
+    // exclusive scan of the NB counts: PERT per thread, then warp and block
+    const int* cnt = pa.cnt + (long long)c * NB;
+    int v[PERT];
+    int loc = 0;
+#pragma unroll
+    for (int k = 0; k < PERT; ++k) {
+      const int b = threadIdx.x * PERT + k;
+      v[k] = b < NB ? cnt[b] : 0;
+      loc += v[k];
     }
-    excl[N] = acc;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int x = loc;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) wsum[wid] = x;
+    __syncthreads();
+    int base = 0;
+    for (int w2 = 0; w2 < wid; ++w2) base += wsum[w2];
+    int run = base + x - loc;
+#pragma unroll
+    for (int k = 0; k < PERT; ++k) {
+      const int b = threadIdx.x * PERT + k;
+      if (b <= NB) excl[b] = run;
+      run += v[k];
+    }
+    __syncthreads();
   }
-  __syncthreads();
   if (blockIdx.x == 0)
-    for (int b = threadIdx.x; b <= N; b += kPtsNT) pa.off[c * (N + 1) + b] = (int)P.pt_off + excl[b];
+    for (int b = threadIdx.x; b <= NB; b += kPtsNT) pa.off[(long long)c * (NB + 1) + b] = (int)P.pt_off + excl[b];
   const long long il = (long long)blockIdx.x * kPtsNT + threadIdx.x;
   if (il >= P.pt_n) return;
   const long long i = P.pt_off + il;
@@ -177,7 +201,7 @@ k_points_lik(const PointParams* __restrict__ pp, PointArrays pa, double* __restr
   const int c = blockIdx.y;
   const PointParams& P = pp[c];
   if (blockIdx.x == 0)
-    for (int b = threadIdx.x; b < P.N; b += kPtsNT) pa.cnt_next[c * P.N + b] = 0;
+    for (int b = threadIdx.x; b < P.N * P.ksplit; b += kPtsNT) pa.cnt_next[c * P.N * P.ksplit + b] = 0;
   const long long il = (long long)blockIdx.x * kPtsNT + threadIdx.x;
   double psi_i = 0.0;
   if (il < P.pt_n) {
@@ -237,11 +261,9 @@ k_points_kick(const PointParams* __restrict__ pp, PointArrays pa, int mode, doub
     }
     if (mode == GM_KICK_DRIFT) {
       // buckets of the drifted distances, for the next evaluation
-      int cx;
-      double f;
-      cell_axis(P.obs[0], placeable(d), pa.rx[i], P.delta, P.N, cx, f);
-      pa.cx[i] = cx;
-      pa.slot[i] = atomicAdd(&pa.cnt_next[c * P.N + cx], 1);
+      const int key = bucket_key(P, d, pa.rx[i], pa.ry[i]);
+      pa.cx[i] = key;
+      pa.slot[i] = atomicAdd(&pa.cnt_next[c * P.N * P.ksplit + key], 1);
     }
   }
   if (mode == GM_KICK_LAST) {
