@@ -129,13 +129,12 @@ def algorithmic_bytes(N, n, C=1, rsz=4):
         "pencil_velocity": C * (S + 3 * S),
         "plane_c2r_velocity_gather": C * (3 * S + 3 * 2 * n * (32 + 8)),
         "memset_bucket_counts": 0,
-        "points_bucket_count": C * n * 24,
-        "points_bucket_place": C * n * 72,
-        "points_likelihood": C * n * 104,
+        "points_bucket_count_standalone": C * n * 24,
+        "points_bucket_place": C * n * (72 + 48 + 40),
+        "points_likelihood_kick": C * n * (104 + 40 + 24),
         "plane_r2c_scatter_adjoint": C * (3 * S + 3 * 2 * n * 32),
         "pencil_adjoint": C * (3 * S + S),
-        "plane_c2r_gradient_kick": C * (S + 4 * R),
-        "points_kick_drift": C * n * 40,
+        "plane_c2r_gradient_kick": C * (S + 4 * R + S),
         "trajectory_begin": C * (6 * R + 56 * n),
         "finalize_energy": 0,
         "restore_rejected": 0,

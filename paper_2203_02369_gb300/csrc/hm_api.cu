@@ -75,13 +75,13 @@ struct DevBuf {
 // ---------------------------------------------------------------------------
 enum KernelKind : int {
   KK_R2C_FIELD = 0, KK_PENCIL_VEL, KK_C2R_GATHER, KK_MEMSET_CNT, KK_PREP, KK_PLACE, KK_LIK,
-  KK_R2C_SCATTER, KK_PENCIL_ADJ, KK_C2R_GRAD, KK_KICK_PTS, KK_BEGIN, KK_FINALIZE, KK_RESTORE, KK_COUNT
+  KK_R2C_SCATTER, KK_PENCIL_ADJ, KK_C2R_GRAD, KK_BEGIN, KK_FINALIZE, KK_RESTORE, KK_COUNT
 };
 static const char* kKindNames[KK_COUNT] = {
     "plane_r2c_field", "pencil_velocity", "plane_c2r_velocity_gather", "memset_bucket_counts",
-    "points_bucket_count",
-    "points_bucket_place", "points_likelihood", "plane_r2c_scatter_adjoint", "pencil_adjoint",
-    "plane_c2r_gradient_kick", "points_kick_drift", "trajectory_begin", "finalize_energy",
+    "points_bucket_count_standalone",
+    "points_bucket_place", "points_likelihood_kick", "plane_r2c_scatter_adjoint", "pencil_adjoint",
+    "plane_c2r_gradient_kick", "trajectory_begin", "finalize_energy",
     "restore_rejected"};
 
 struct Prof {
@@ -197,7 +197,10 @@ double tophat(double x) { return 3.0 * (std::sin(x) - x * std::cos(x)) / (x * x 
 // side stream on which the bucketing overlaps the first FFT passes.
 struct PtWork {
   DevBuf cx, slot, pos, cnt, off, rec, part, lk;
-  int CN = 0;  // C*N: the count buffer holds two halves of CN ints (ping-pong)
+  int CN = 0;          // C*NB: each count half holds CN ints (ping-pong)
+  int OH = 0;          // C*(NB+1): ints in each offset half
+  size_t recsz = 0;    // bytes of one point record
+  long long nt = 1;    // records per half
   cudaStream_t aux = nullptr;
   cudaEvent_t fork = nullptr, join = nullptr;
   ~PtWork() {
@@ -207,18 +210,19 @@ struct PtWork {
   }
   int alloc(int prec, int C, int N, long long ntot) {
     N *= plane_split(N);   // sub-buckets per chain
-    const size_t nt = (size_t)std::max<long long>(ntot, 1);
+    nt = std::max<long long>(ntot, 1);
     const size_t rsz = prec == HM_FP32 ? 4 : 8;
-    const size_t recsz = prec == HM_FP32 ? sizeof(PtRec<float>) : sizeof(PtRec<double>);
+    recsz = prec == HM_FP32 ? sizeof(PtRec<float>) : sizeof(PtRec<double>);
     HM_TRY(cx.alloc(4 * nt));
     HM_TRY(slot.alloc(4 * nt));
     HM_TRY(pos.alloc(4 * nt));
     HM_TRY(cnt.alloc(4 * 2 * (size_t)C * N));
-    HM_TRY(off.alloc(4 * (size_t)C * (N + 1)));
-    HM_TRY(rec.alloc(recsz * nt));
+    HM_TRY(off.alloc(4 * 2 * (size_t)C * (N + 1)));
+    HM_TRY(rec.alloc(2 * recsz * nt));
     HM_TRY(part.alloc(rsz * 12 * nt));
     HM_TRY(lk.alloc(8 * 6 * nt));
     CN = C * N;
+    OH = C * (N + 1);
     if (cudaMemset(cnt.p, 0, 4 * 2 * (size_t)C * N) != cudaSuccess) return fail(HM_ECUDA, "cudaMemset failed");
     if (!aux) {
       if (cudaStreamCreateWithFlags(&aux, cudaStreamNonBlocking) != cudaSuccess ||
@@ -229,15 +233,16 @@ struct PtWork {
     return HM_OK;
   }
   int* half(int parity) const { return cnt.as<int>() + (size_t)(parity & 1) * CN; }
-  // parity selects which count half holds the current distances' buckets
+  // Buffers of evaluation parity `parity`: counts of its distances (cnt),
+  // the other count half (cnt_next), and its records and offsets.
   void fill(PointArrays& pa, long long ntot, int parity = 0) const {
     pa.cx = cx.as<int>();
     pa.slot = slot.as<int>();
     pa.pos = pos.as<int>();
     pa.cnt = half(parity);
     pa.cnt_next = half(parity + 1);
-    pa.off = off.as<int>();
-    pa.rec = rec.p;
+    pa.off = off.as<int>() + (size_t)(parity & 1) * OH;
+    pa.rec = static_cast<char*>(rec.p) + (size_t)(parity & 1) * recsz * nt;
     pa.part = part.p;
     pa.lk = lk.as<double>();
     pa.ntot = ntot;
@@ -354,60 +359,83 @@ struct GradArgs {
   Prof* prof;
 };
 
-// One gradient evaluation of C chains at their current (w, d):
-//   side stream : bucket count, bucket placement of the points   (x-planes)
-//   main stream : w -> w_k (planes, then x pencils with the velocity
-//                 weights) -> per-plane inverse with the CIC gather -> FP64
-//                 likelihood -> per-plane CIC scatter + forward -> x pencils
-//                 with the adjoint weights -> per-plane inverse with the
-//                 gradient / leapfrog epilogue -> distance kick/drift.
-static int grad_eval(const GradArgs& a0, int mode, cudaStream_t st, int parity, bool count_first) {
-  GradArgs a = a0;
+// The gradient evaluations of a leapfrog run (or one standalone evaluation)
+// for C chains.  Streams: the side stream `aux` places the points of
+// evaluation l+1 into x-plane buckets (and evaluates the FP64 likelihood
+// terms that depend on d alone) while the main stream runs evaluation l's
+// adjoint; the main stream of evaluation l is
+//   [plane r2c of w] -> x pencils with the velocity weights -> plane c2r with
+//   the CIC gather -> likelihood (+ distance kick/drift, next buckets) ->
+//   plane CIC scatter + r2c -> x pencils with the adjoint weights -> plane
+//   c2r with the field kick/drift (+ plane r2c of the drifted field).
+// Precondition: the bucket counts of the current distances are in count
+// half 0.  Evaluation l uses parity (l-1)&1 for counts, records, offsets.
+static int place_points(const GradArgs& a, int parity, cudaStream_t st) {
+  const PtWork& wk = *a.work;
+  PointArrays pa = a.pa;
+  wk.fill(pa, a.pa.ntot, parity);
+  HM_CUDA(cudaEventRecord(wk.fork, st));
+  HM_CUDA(cudaStreamWaitEvent(wk.aux, wk.fork, 0));
+  HM_PROF(a.prof, KK_PLACE, wk.aux, launch_points_place(a.prec, a.C, a.max_pts, a.pp, pa, a.cs, wk.aux));
+  HM_CUDA(cudaEventRecord(wk.join, wk.aux));
+  return HM_OK;
+}
+
+static int eval_run(const GradArgs& a, int n, int last_mode, cudaStream_t st) {
   Prof* pf = a.prof;
   const PtWork& wk = *a.work;
-  wk.fill(a.pa, a.pa.ntot, parity);
-  cudaStream_t ax = wk.aux;
-  PlanePoints pts{};
-  pts.off = a.pa.off;
-  pts.rec = a.pa.rec;
-  pts.part = a.pa.part;
-  pts.ntot = a.pa.ntot;
-  pts.inv_delta = 1.0 / a.delta;
-  // fork: bucket placement and the d-only likelihood terms on the side stream
-  HM_CUDA(cudaEventRecord(wk.fork, st));
-  HM_CUDA(cudaStreamWaitEvent(ax, wk.fork, 0));
-  if (count_first) {
-    HM_PROF(pf, KK_MEMSET_CNT, ax, cudaMemsetAsync(a.pa.cnt, 0, sizeof(int) * (size_t)wk.CN, ax));
-    HM_PROF(pf, KK_PREP, ax, launch_points_prep(a.C, a.max_pts, a.pp, a.pa, ax));
+  HM_TRY(place_points(a, 0, st));
+  bool have_spec = false;
+  for (int l = 1; l <= n; ++l) {
+    const int par = (l - 1) & 1;
+    const int mode = l < n ? GM_KICK_DRIFT : last_mode;
+    PointArrays pa = a.pa;
+    wk.fill(pa, a.pa.ntot, par);
+    PlanePoints pts{};
+    pts.off = pa.off;
+    pts.rec = pa.rec;
+    pts.part = pa.part;
+    pts.ntot = pa.ntot;
+    pts.inv_delta = 1.0 / a.delta;
+    // forward field operator
+    if (!have_spec)
+      HM_PROF(pf, KK_R2C_FIELD, st, launch_plane_r2c(a.prec, a.N, a.w, a.n3, a.S1, a.nspec, a.C, a.tw, st));
+    HM_PROF(pf, KK_PENCIL_VEL, st,
+            launch_pencil(a.prec, a.N, PM_VEL, a.S1, a.nspec, a.S2, a.nspec, a.C, a.tw, a.amp, st));
+    HM_CUDA(cudaStreamWaitEvent(st, wk.join, 0));   // buckets of this evaluation placed
+    HM_PROF(pf, KK_C2R_GATHER, st, launch_plane_c2r_gather(a.prec, a.N, a.S2, a.nspec, pts, 3 * a.C, a.tw, st));
+    HM_PROF(pf, KK_LIK, st,
+            launch_points_lik(a.prec, a.C, a.max_pts, a.pp, pa, a.pts_part, a.pts_blocks, mode, a.kinl_p, a.cs,
+                              st));
+    if (l < n) HM_TRY(place_points(a, par ^ 1, st));   // next evaluation's buckets, off the critical path
+    // adjoint: residuals scattered plane by plane, forward transform, weights
+    HM_PROF(pf, KK_R2C_SCATTER, st, launch_plane_r2c_scatter(a.prec, a.N, pts, a.S1, a.nspec, 3 * a.C, a.tw, st));
+    HM_PROF(pf, KK_PENCIL_ADJ, st,
+            launch_pencil(a.prec, a.N, PM_ADJ, a.S1, a.nspec, a.S2, a.nspec, a.C, a.tw, a.amp, st));
+    FieldEpi epi{};
+    epi.w = a.w;
+    epi.pw = a.pw;
+    epi.gw = a.gw;
+    epi.prior_part = a.prior_part;
+    epi.kin_part = a.kinl_f;
+    epi.cs = a.cs;
+    epi.grid_stride = a.n3;
+    epi.mode = mode;
+    void* next = (mode == GM_KICK_DRIFT) ? a.S1 : nullptr;   // S1 is free after the adjoint pencils
+    HM_PROF(pf, KK_C2R_GRAD, st,
+            launch_plane_c2r(a.prec, a.N, a.S2, a.nspec, nullptr, 0, a.C, a.tw, &epi, st, next));
+    have_spec = next != nullptr;
   }
-  HM_PROF(pf, KK_PLACE, ax, launch_points_place(a.prec, a.C, a.max_pts, a.pp, a.pa, a.cs, ax));
-  HM_CUDA(cudaEventRecord(wk.join, ax));
-  // forward field operator
-  HM_PROF(pf, KK_R2C_FIELD, st, launch_plane_r2c(a.prec, a.N, a.w, a.n3, a.S1, a.nspec, a.C, a.tw, st));
-  HM_PROF(pf, KK_PENCIL_VEL, st,
-          launch_pencil(a.prec, a.N, PM_VEL, a.S1, a.nspec, a.S2, a.nspec, a.C, a.tw, a.amp, st));
-  // join, then velocity planes with the CIC gather at the points
-  HM_CUDA(cudaStreamWaitEvent(st, wk.join, 0));
-  HM_PROF(pf, KK_C2R_GATHER, st, launch_plane_c2r_gather(a.prec, a.N, a.S2, a.nspec, pts, 3 * a.C, a.tw, st));
-  HM_PROF(pf, KK_LIK, st, launch_points_lik(a.prec, a.C, a.max_pts, a.pp, a.pa, a.pts_part, a.pts_blocks, st));
-  // adjoint: residuals scattered plane by plane, forward transform, weights
-  HM_PROF(pf, KK_R2C_SCATTER, st, launch_plane_r2c_scatter(a.prec, a.N, pts, a.S1, a.nspec, 3 * a.C, a.tw, st));
-  HM_PROF(pf, KK_PENCIL_ADJ, st,
-          launch_pencil(a.prec, a.N, PM_ADJ, a.S1, a.nspec, a.S2, a.nspec, a.C, a.tw, a.amp, st));
-  FieldEpi epi{};
-  epi.w = a.w;
-  epi.pw = a.pw;
-  epi.gw = a.gw;
-  epi.prior_part = a.prior_part;
-  epi.kin_part = a.kinl_f;
-  epi.cs = a.cs;
-  epi.grid_stride = a.n3;
-  epi.mode = mode;
-  HM_PROF(pf, KK_C2R_GRAD, st, launch_plane_c2r(a.prec, a.N, a.S2, a.nspec, nullptr, 0, a.C, a.tw, &epi, st));
-  if (mode != GM_GRAD && a.max_pts > 0)
-    HM_PROF(pf, KK_KICK_PTS, st,
-            launch_points_kick(a.C, a.max_pts, a.pp, a.pa, mode, a.kinl_p, a.pts_blocks, a.cs, st));
   return HM_OK;
+}
+
+// One standalone evaluation (no leapfrog update): bucket counts first.
+static int eval_single(const GradArgs& a, cudaStream_t st) {
+  PointArrays pa = a.pa;
+  a.work->fill(pa, a.pa.ntot, 0);
+  HM_PROF(a.prof, KK_MEMSET_CNT, st, cudaMemsetAsync(pa.cnt, 0, sizeof(int) * (size_t)a.work->CN, st));
+  HM_PROF(a.prof, KK_PREP, st, launch_points_prep(a.C, a.max_pts, a.pp, pa, st));
+  return eval_run(a, 1, GM_GRAD, st);
 }
 
 // ---------------------------------------------------------------------------
@@ -641,7 +669,7 @@ int hm_logpost_grad(hm_problem* p, const void* w_dev, const double* d_dev, doubl
   a.kinl_p = p->kin_part.as<double>();
   a.cs = cs;
   a.work = &p->pw;
-  HM_TRY(grad_eval(a, GM_GRAD, st, 0, true));
+  HM_TRY(eval_single(a, st));
   HM_CUDA(launch_finalize(1, a.prior_part, p->N * plane_split(p->N), a.pts_part, a.pts_blocks, nullptr, 0, nullptr, 0, FIN_PSI,
                           0ull, p->chain_id.as<int>(), cs, nullptr, st));
   HM_CUDA(cudaMemcpyAsync(psi_dev, &cs->psi, sizeof(double), cudaMemcpyDeviceToDevice, st));
@@ -757,7 +785,7 @@ static GradArgs state_args(hm_state* s) {
 
 static int state_refresh(hm_state* s, cudaStream_t st) {
   GradArgs a = state_args(s);
-  HM_TRY(grad_eval(a, GM_GRAD, st, 0, true));
+  HM_TRY(eval_single(a, st));
   HM_CUDA(launch_finalize(s->C, a.prior_part, s->NP, a.pts_part, s->pts_blocks, nullptr, 0, nullptr, 0, FIN_PSI,
                           s->seed, s->chain_id.as<int>(), a.cs, nullptr, st));
   return HM_OK;
@@ -981,10 +1009,7 @@ static int leapfrog_body(hm_state* s, int n_steps, int draw, cudaStream_t st, Pr
                           s->kinb_p.as<double>(), s->max_pts > 0 ? s->nparts_p : 0, FIN_HOLD, s->seed,
                           s->chain_id.as<int>(), a.cs, nullptr, st));
   if (pf) HM_CUDA(pf->end(st));
-  // evaluation l reads the counts of half (l-1)%2 and its kick counts into the other
-  for (int l = 1; l <= n_steps; ++l)
-    HM_TRY(grad_eval(a, l < n_steps ? GM_KICK_DRIFT : GM_KICK_LAST, st, (l - 1) & 1, false));
-  return HM_OK;
+  return eval_run(a, n_steps, GM_KICK_LAST, st);
 }
 
 int hm_leapfrog(hm_state* s, int32_t n_steps, double eps, int32_t sample_distances, void* stream) {

@@ -1,64 +1,62 @@
 // 3D real-to-complex / complex-to-real FFT passes and the fused k-space
 // weights of the linear velocity operator (eq. vel-field) and its adjoint.
 //
-// A 3D transform is two passes over memory:
-//   plane pass : one thread-block cluster of K CTAs per x-plane.  CTA q owns
-//                N/K real rows (two packed per complex row) for the z
-//                transform, then the K CTAs exchange row slabs for column
-//                slabs through distributed shared memory and each one runs
-//                the y transform of about (N/2+1)/K columns;
+// A 3D transform is two passes over HBM:
+//   plane pass : one CTA per x-plane; z (real <-> half complex, two real rows
+//                packed in one complex row) and y (complex) in shared memory;
 //   pencil pass: one CTA per tile of TC contiguous (y, kz) columns; the x
 //                transform runs in shared memory, with the k-space operator
 //                applied between a forward and an inverse x transform so the
-//                weighted spectra never take an extra trip through memory.
-// The plane passes also host the point work that lives on a plane: the CIC
-// gather of the velocity (after the inverse), the CIC scatter of the
-// residuals (before the forward) and the leapfrog update of the field.
+//                weighted spectra never take an extra trip through HBM.
 // Spectrum layout: [kx][ky][kz], kz = 0..N/2, natural order on every axis.
-#include <cooperative_groups.h>
-
 #include "hm_fft.cuh"
 #include "hm_internal.h"
 
-namespace cg = cooperative_groups;
-
 namespace hm {
+
+template <typename T> struct Vec16;
+template <> struct Vec16<float> { using type = float4; static constexpr int W = 4; };
+template <> struct Vec16<double> { using type = double2; static constexpr int W = 2; };
+
+template <typename T> __device__ __forceinline__ T vget(const typename Vec16<T>::type& v, int q);
+template <> __device__ __forceinline__ float vget<float>(const float4& v, int q) {
+  return q == 0 ? v.x : (q == 1 ? v.y : (q == 2 ? v.z : v.w));
+}
+template <> __device__ __forceinline__ double vget<double>(const double2& v, int q) {
+  return q == 0 ? v.x : v.y;
+}
 
 template <int N> struct PlaneCfg {
   static constexpr int NH = N / 2 + 1;
-  static constexpr int ZP = 2 * NH;           // pitch of a packed row (= two half-spectrum rows)
-  static constexpr int K = PlaneSplit<N>::K;  // CTAs per plane (cluster size)
-  static constexpr int RQ = N / K;            // real rows per CTA
-  static constexpr int PR = RQ / 2;           // packed rows per CTA
-  static constexpr int CW = (NH + K - 1) / K; // most half-spectrum columns of one CTA
-  static constexpr int CWP = CW | 1;          // odd pitch of the column slab
-  static constexpr int ROWSLAB = PR * ZP;     // complex elements
-  static constexpr int COLSLAB = N * CWP;
-  static constexpr int NT = N >= 128 ? 256 : 128;
+  static constexpr int ZP = 2 * NH;                // pitch of packed z rows (= 2 spectrum rows)
+  static constexpr int NT = N >= 128 ? 512 : (N >= 64 ? 256 : 128);
+  static constexpr int SIZE = N * NH;              // complex elements of the plane buffer
+  static constexpr int MINB = N >= 128 ? 2 : 1;    // CTAs per SM the register budget aims at
 };
 
 template <typename T, int N> constexpr size_t plane_smem_bytes() {
-  return sizeof(cplx<T>) * (PlaneCfg<N>::ROWSLAB + PlaneCfg<N>::COLSLAB);
+  return sizeof(cplx<T>) * PlaneCfg<N>::SIZE;
 }
 
-// Row slab R of CTA q holds real rows y in [q*RQ, (q+1)*RQ) through two views
-// sharing memory:
-//   spectrum view  H[yl][k] = R[yl*NH + k]       (half spectrum of row q*RQ + yl)
-//   packed view    Z[r][z]  = R[r*ZP + z]        (real rows 2r, 2r+1 in re, im)
+// The plane buffer B holds N*(N/2+1) complex values and is read through two
+// views that share memory:
+//   spectrum view  H[y][k] = B[y*NH + k]            (y < N, k <= N/2)
+//   packed view    Z[r][z] = B[r*ZP + z], ZP = 2 NH (r < N/2, z < N), whose
+//                  real/imaginary parts are the real rows y = 2r and 2r+1.
 // Z row r and H rows 2r, 2r+1 occupy the same addresses, so the real <->
-// half-spectrum (un)packing runs in place.
+// half-spectrum (un)packing runs in place, row pair by row pair.
 template <typename T, int N>
-__device__ __forceinline__ T* zreal_local(cplx<T>* R, int yl, int z) {
-  return reinterpret_cast<T*>(&R[(yl >> 1) * PlaneCfg<N>::ZP + z]) + (yl & 1);
+__device__ __forceinline__ T* zreal(cplx<T>* B, int y, int z) {
+  return reinterpret_cast<T*>(&B[(y >> 1) * PlaneCfg<N>::ZP + z]) + (y & 1);
 }
 
 // Z rows (after the forward z FFT) -> H rows (half spectra of the real rows).
 template <typename T, int N>
-__device__ __forceinline__ void unpack_rows(cplx<T>* R) {
+__device__ __forceinline__ void unpack_rows(cplx<T>* B) {
   using C = cplx<T>;
   using P = PlaneCfg<N>;
   constexpr int NH = P::NH, ZP = P::ZP, NT = P::NT;
-  constexpr int TOT = P::PR * NH;
+  constexpr int TOT = (N / 2) * NH;
   constexpr int PER = (TOT + NT - 1) / NT;
   C a[PER], b[PER];
 #pragma unroll
@@ -66,8 +64,8 @@ __device__ __forceinline__ void unpack_rows(cplx<T>* R) {
     const int e = threadIdx.x + i * NT;
     if (e < TOT) {
       const int r = e / NH, k = e % NH;
-      const C zk = R[r * ZP + k];
-      const C zm = cconj(R[r * ZP + ((N - k) & (N - 1))]);
+      const C zk = B[r * ZP + k];
+      const C zm = cconj(B[r * ZP + ((N - k) & (N - 1))]);
       const C sp = cadd(zk, zm), df = csub(zk, zm);
       a[i] = C{(T)0.5 * sp.x, (T)0.5 * sp.y};
       b[i] = C{(T)0.5 * df.y, (T)-0.5 * df.x};
@@ -79,8 +77,8 @@ __device__ __forceinline__ void unpack_rows(cplx<T>* R) {
     const int e = threadIdx.x + i * NT;
     if (e < TOT) {
       const int r = e / NH, k = e % NH;
-      R[r * ZP + k] = a[i];
-      R[r * ZP + NH + k] = b[i];
+      B[r * ZP + k] = a[i];
+      B[r * ZP + NH + k] = b[i];
     }
   }
   __syncthreads();
@@ -89,11 +87,11 @@ __device__ __forceinline__ void unpack_rows(cplx<T>* R) {
 // H rows (inverse-transformed along y) -> Z rows ready for the inverse z FFT.
 // The imaginary parts at kz = 0 and N/2 are dropped (c2r semantics).
 template <typename T, int N>
-__device__ __forceinline__ void pack_rows(cplx<T>* R) {
+__device__ __forceinline__ void pack_rows(cplx<T>* B) {
   using C = cplx<T>;
   using P = PlaneCfg<N>;
   constexpr int NH = P::NH, ZP = P::ZP, NT = P::NT;
-  constexpr int TOT = P::PR * N;
+  constexpr int TOT = (N / 2) * N;
   constexpr int PER = (TOT + NT - 1) / NT;
   C o[PER];
 #pragma unroll
@@ -103,15 +101,15 @@ __device__ __forceinline__ void pack_rows(cplx<T>* R) {
       const int r = e / N, k = e % N;
       C a, b;
       if (k <= N / 2) {
-        a = R[r * ZP + k];
-        b = R[r * ZP + NH + k];
+        a = B[r * ZP + k];
+        b = B[r * ZP + NH + k];
         if (k == 0 || k == N / 2) {
           a.y = 0;
           b.y = 0;
         }
       } else {
-        a = cconj(R[r * ZP + (N - k)]);
-        b = cconj(R[r * ZP + NH + (N - k)]);
+        a = cconj(B[r * ZP + (N - k)]);
+        b = cconj(B[r * ZP + NH + (N - k)]);
       }
       o[i] = C{a.x - b.y, a.y + b.x};
     }
@@ -120,50 +118,46 @@ __device__ __forceinline__ void pack_rows(cplx<T>* R) {
 #pragma unroll
   for (int i = 0; i < PER; ++i) {
     const int e = threadIdx.x + i * NT;
-    if (e < TOT) R[(e / N) * ZP + (e % N)] = o[i];
+    if (e < TOT) B[(e / N) * ZP + (e % N)] = o[i];
   }
   __syncthreads();
 }
 
-template <typename T> struct Pair2;
-template <> struct Pair2<float> { using type = float2; };
-template <> struct Pair2<double> { using type = double2; };
-
-// Own real rows (contiguous z) <-> packed view.  Item (r, zp) covers local
-// rows 2r, 2r+1 and columns z = 2zp, 2zp+1: two 2-wide global accesses and
-// one 16-byte (FP32) shared access, consecutive threads on consecutive
-// shared words.
+// Real plane (rows y, contiguous z) <-> packed view.  Item (r, zp) covers
+// rows 2r, 2r+1 and columns z = 2zp, 2zp+1: two 2-wide global accesses per
+// row and one 16-byte (FP32) shared access, so consecutive threads touch
+// consecutive shared words (no bank conflicts).
 template <typename T, int N>
-__device__ __forceinline__ void load_rows_packed(cplx<T>* R, const T* __restrict__ src) {
+__device__ __forceinline__ void load_plane_packed(cplx<T>* B, const T* __restrict__ src) {
   using P = PlaneCfg<N>;
-  constexpr int ITEMS = P::PR * (N / 2);
+  constexpr int ITEMS = (N / 2) * (N / 2);
   for (int e = threadIdx.x; e < ITEMS; e += P::NT) {
     const int r = e / (N / 2), z = 2 * (e % (N / 2));
     if constexpr (sizeof(T) == 4) {
       const float2 a = __ldg(reinterpret_cast<const float2*>(src + (2 * r) * N + z));
       const float2 b = __ldg(reinterpret_cast<const float2*>(src + (2 * r + 1) * N + z));
-      *reinterpret_cast<float4*>(&R[r * P::ZP + z]) = make_float4(a.x, b.x, a.y, b.y);
+      *reinterpret_cast<float4*>(&B[r * P::ZP + z]) = make_float4(a.x, b.x, a.y, b.y);
     } else {
       const double2 a = __ldg(reinterpret_cast<const double2*>(src + (2 * r) * N + z));
       const double2 b = __ldg(reinterpret_cast<const double2*>(src + (2 * r + 1) * N + z));
-      R[r * P::ZP + z] = cplx<T>{a.x, b.x};
-      R[r * P::ZP + z + 1] = cplx<T>{a.y, b.y};
+      B[r * P::ZP + z] = cplx<T>{a.x, b.x};
+      B[r * P::ZP + z + 1] = cplx<T>{a.y, b.y};
     }
   }
 }
 
 // values of item (r, zp): v[0] = (2r, z), v[1] = (2r+1, z), v[2] = (2r, z+1), v[3] = (2r+1, z+1)
 template <typename T, int N>
-__device__ __forceinline__ void read_item(const cplx<T>* R, int r, int z, T* v) {
+__device__ __forceinline__ void read_item(const cplx<T>* B, int r, int z, T* v) {
   using P = PlaneCfg<N>;
   if constexpr (sizeof(T) == 4) {
-    const float4 q = *reinterpret_cast<const float4*>(&R[r * P::ZP + z]);
+    const float4 q = *reinterpret_cast<const float4*>(&B[r * P::ZP + z]);
     v[0] = q.x;
     v[1] = q.y;
     v[2] = q.z;
     v[3] = q.w;
   } else {
-    const cplx<T> a = R[r * P::ZP + z], b = R[r * P::ZP + z + 1];
+    const cplx<T> a = B[r * P::ZP + z], b = B[r * P::ZP + z + 1];
     v[0] = a.x;
     v[1] = a.y;
     v[2] = b.x;
@@ -171,22 +165,24 @@ __device__ __forceinline__ void read_item(const cplx<T>* R, int r, int z, T* v) 
   }
 }
 
-// Sub-bucket ranges of this CTA's two point sets on plane ix: side 0 has its
-// lower CIC corner on the plane (bucket ix), side 1 its upper corner (bucket
-// ix-1); within a plane, points are split by the CTA owning their row cy.
+template <typename T> struct Pair2;
+template <> struct Pair2<float> { using type = float2; };
+template <> struct Pair2<double> { using type = double2; };
+
+// Bucket ranges of the plane's two point sets: side 0 has its lower CIC
+// corner on this plane (bucket ix), side 1 its upper corner (bucket ix-1).
 struct PlaneBuckets {
   int b0, n0, b1, n1;
 };
 template <int N>
-__device__ __forceinline__ PlaneBuckets plane_buckets(const int* __restrict__ off, int c, int ix, int q) {
-  constexpr int K = PlaneCfg<N>::K;
-  const int* o = off + (long long)c * (N * K + 1);
+__device__ __forceinline__ PlaneBuckets plane_buckets(const int* __restrict__ off, int c, int ix) {
+  const int* o = off + (long long)c * (N + 1);
   const int ixm = (ix + N - 1) & (N - 1);
   PlaneBuckets pb;
-  pb.b0 = o[ix * K + q];
-  pb.n0 = o[ix * K + q + 1] - pb.b0;
-  pb.b1 = o[ixm * K + q];
-  pb.n1 = o[ixm * K + q + 1] - pb.b1;
+  pb.b0 = o[ix];
+  pb.n0 = o[ix + 1] - o[ix];
+  pb.b1 = o[ixm];
+  pb.n1 = o[ixm + 1] - o[ixm];
   return pb;
 }
 
@@ -194,159 +190,116 @@ template <typename T> __device__ __forceinline__ T rcomp(const PtRec<T>& p, int 
   return j == 0 ? p.rx : (j == 1 ? p.ry : p.rz);
 }
 
-// Columns of CTA q: [c0, c1) of the NH half-spectrum columns.
-template <int N> __device__ __forceinline__ void own_columns(int q, int& c0, int& c1) {
-  constexpr int NH = PlaneCfg<N>::NH, K = PlaneCfg<N>::K;
-  c0 = (q * NH) / K;
-  c1 = ((q + 1) * NH) / K;
-}
-
 // ---------------------------------------------------------------------------
-// Plane pass, forward: real plane -> (z r2c, y c2c) -> spectrum plane.
+// Plane pass, forward: real plane x -> (z r2c, y c2c) -> spectrum plane.
 // SCATTER builds the plane from the bucketed points instead of loading it:
 // s_j(corner) += r rhat_j W(corner), with shared-memory atomics (the adjoint
-// of the CIC gather, restricted to this plane); the corner row cy + 1 may
-// belong to the next CTA of the cluster and is reached through DSMEM.
+// of the CIC gather, restricted to this plane).
 // ---------------------------------------------------------------------------
 template <typename T, int N, bool SCATTER>
-__global__ void __cluster_dims__(PlaneCfg<N>::K, 1, 1) __launch_bounds__(PlaneCfg<N>::NT)
+__global__ void __launch_bounds__(PlaneCfg<N>::NT, (sizeof(T) == 4 ? PlaneCfg<N>::MINB : 1))
 k_plane_r2c(const T* __restrict__ in, long long in_stride, cplx<T>* __restrict__ out,
             long long out_stride, const cplx<T>* __restrict__ tw, PlanePoints pts) {
   using C = cplx<T>;
   using P = PlaneCfg<N>;
-  constexpr int NT = P::NT, K = P::K, RQ = P::RQ, NH = P::NH, CWP = P::CWP;
+  constexpr int NT = P::NT, ZP = P::ZP;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  C* R = reinterpret_cast<C*>(smem_raw);
-  C* Cs = R + P::ROWSLAB;
-  cg::cluster_group cl = cg::this_cluster();
-  const int q = (int)cl.block_rank();
-  const int ix = blockIdx.x / K;
+  C* B = reinterpret_cast<C*>(smem_raw);
+  const int ix = blockIdx.x;
   const int s = blockIdx.y;
-  const int row0 = q * RQ;
-  auto rem = [&](int k) -> C* { return cl.map_shared_rank(R, k); };   // CTA k's row slab
   if constexpr (!SCATTER) {
-    load_rows_packed<T, N>(R, in + (long long)s * in_stride + ((long long)ix * N + row0) * N);
-    __syncthreads();
+    load_plane_packed<T, N>(B, in + (long long)s * in_stride + (long long)ix * N * N);
   } else {
-    for (int e = threadIdx.x; e < P::ROWSLAB; e += NT) R[e] = C{(T)0, (T)0};
-    cl.sync();   // every slab of the cluster is zero before any remote add
+    for (int e = threadIdx.x; e < P::SIZE; e += NT) B[e] = C{(T)0, (T)0};
+    __syncthreads();
     const int c = s / 3, j = s % 3;
-    const PlaneBuckets pb = plane_buckets<N>(pts.off, c, ix, q);
-    const PtRec<T>* Rp = static_cast<const PtRec<T>*>(pts.rec);
+    const PlaneBuckets pb = plane_buckets<N>(pts.off, c, ix);
+    const PtRec<T>* R = static_cast<const PtRec<T>*>(pts.rec);
     for (int t = threadIdx.x; t < pb.n0 + pb.n1; t += NT) {
       const bool lower = t < pb.n0;
-      const PtRec<T> p = Rp[lower ? pb.b0 + t : pb.b1 + (t - pb.n0)];
+      const PtRec<T> p = R[lower ? pb.b0 + t : pb.b1 + (t - pb.n0)];
       const T val = p.r * rcomp(p, j) * (lower ? (T)1 - p.fx : p.fx);
       if (val == (T)0) continue;
       const int iy = p.yz / N, iz = p.yz % N;
-      if (iy < row0 || iy >= row0 + RQ) continue;   // not this CTA's row (never for a consistent bucket)
       const int iy1 = (iy + 1) & (N - 1), iz1 = (iz + 1) & (N - 1);
       const T wy1 = p.fy, wy0 = (T)1 - p.fy, wz1 = p.fz, wz0 = (T)1 - p.fz;
-      // row iy is ours; row iy + 1 belongs to CTA (iy + 1) / RQ
-      const int o1 = iy1 / RQ;
-      atomicAdd(zreal_local<T, N>(R, iy - row0, iz), val * wy0 * wz0);
-      atomicAdd(zreal_local<T, N>(R, iy - row0, iz1), val * wy0 * wz1);
-      atomicAdd(zreal_local<T, N>(rem(o1), iy1 - o1 * RQ, iz), val * wy1 * wz0);
-      atomicAdd(zreal_local<T, N>(rem(o1), iy1 - o1 * RQ, iz1), val * wy1 * wz1);
+      atomicAdd(zreal<T, N>(B, iy, iz), val * wy0 * wz0);
+      atomicAdd(zreal<T, N>(B, iy, iz1), val * wy0 * wz1);
+      atomicAdd(zreal<T, N>(B, iy1, iz), val * wy1 * wz0);
+      atomicAdd(zreal<T, N>(B, iy1, iz1), val * wy1 * wz1);
     }
-    cl.sync();
   }
-  fft_smem<T, N, false, P::PR, NT, false>(R, P::ZP, 1, tw);
-  unpack_rows<T, N>(R);
-  cl.sync();   // all row slabs hold half spectra
-  int c0, c1;
-  own_columns<N>(q, c0, c1);
-  const int nc = c1 - c0;
-  for (int e = threadIdx.x; e < N * P::CW; e += NT) {
-    const int y = e / P::CW, cc = e % P::CW;
-    C v = C{(T)0, (T)0};
-    if (cc < nc) {
-      const int o = y / RQ;
-      v = rem(o)[(y - o * RQ) * NH + c0 + cc];
-    }
-    Cs[y * CWP + cc] = v;
-  }
-  cl.sync();   // remote reads done before any CTA moves on or exits
-  fft_smem<T, N, false, P::CW, NT, true>(Cs, 1, CWP, tw);
-  C* dst = out + (long long)s * out_stride + (long long)ix * N * NH;
-  for (int e = threadIdx.x; e < N * nc; e += NT) {
-    const int y = e / nc, cc = e % nc;
-    dst[y * NH + c0 + cc] = Cs[y * CWP + cc];
+  __syncthreads();
+  fft_smem<T, N, false, N / 2, NT, false>(B, ZP, 1, tw);
+  unpack_rows<T, N>(B);
+  fft_smem<T, N, false, P::NH, NT, true>(B, 1, P::NH, tw);
+  C* dst = out + (long long)s * out_stride + (long long)ix * P::SIZE;
+  if constexpr (sizeof(T) == 4) {
+    float4* d4 = reinterpret_cast<float4*>(dst);
+    const float4* s4 = reinterpret_cast<const float4*>(B);
+    for (int e = threadIdx.x; e < P::SIZE / 2; e += NT) d4[e] = s4[e];
+  } else {
+    for (int e = threadIdx.x; e < P::SIZE; e += NT) dst[e] = B[e];
   }
 }
 
 // ---------------------------------------------------------------------------
-// Plane pass, inverse: spectrum plane -> (y c2c, z c2r) -> real rows, then
+// Plane pass, inverse: spectrum plane -> (y c2c, z c2r) -> real plane, then
 // MODE 0: plain store; 1: gradient / leapfrog epilogue; 2: CIC gather of the
 // bucketed points (u and du partials of this plane and component).
 // ---------------------------------------------------------------------------
 enum C2RMode : int { C2R_STORE = 0, C2R_EPI = 1, C2R_GATHER = 2 };
 
 template <typename T, int N, int MODE>
-__global__ void __cluster_dims__(PlaneCfg<N>::K, 1, 1) __launch_bounds__(PlaneCfg<N>::NT)
+__global__ void __launch_bounds__(PlaneCfg<N>::NT, (sizeof(T) == 4 ? PlaneCfg<N>::MINB : 1))
 k_plane_c2r(const cplx<T>* __restrict__ in, long long in_stride, T* __restrict__ out,
-            long long out_stride, const cplx<T>* __restrict__ tw, FieldEpi epi, PlanePoints pts) {
+            long long out_stride, const cplx<T>* __restrict__ tw, FieldEpi epi, PlanePoints pts,
+            cplx<T>* __restrict__ next, long long next_stride) {
   using C = cplx<T>;
   using P = PlaneCfg<N>;
-  constexpr int NT = P::NT, K = P::K, RQ = P::RQ, NH = P::NH, CWP = P::CWP;
+  constexpr int NT = P::NT, ZP = P::ZP;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  C* R = reinterpret_cast<C*>(smem_raw);
-  C* Cs = R + P::ROWSLAB;
+  C* B = reinterpret_cast<C*>(smem_raw);
   __shared__ double red[2][NT / 32];
-  cg::cluster_group cl = cg::this_cluster();
-  const int q = (int)cl.block_rank();
-  const int ix = blockIdx.x / K;
+  const int ix = blockIdx.x;
   const int s = blockIdx.y;
-  const int row0 = q * RQ;
-  auto rem = [&](int k) -> C* { return cl.map_shared_rank(R, k); };   // CTA k's row slab
-  int c0, c1;
-  own_columns<N>(q, c0, c1);
-  const int nc = c1 - c0;
-  const C* src = in + (long long)s * in_stride + (long long)ix * N * NH;
-  for (int e = threadIdx.x; e < N * P::CW; e += NT) {
-    const int y = e / P::CW, cc = e % P::CW;
-    Cs[y * CWP + cc] = cc < nc ? src[y * NH + c0 + cc] : C{(T)0, (T)0};
+  const C* src = in + (long long)s * in_stride + (long long)ix * P::SIZE;
+  if constexpr (sizeof(T) == 4) {
+    const float4* s4 = reinterpret_cast<const float4*>(src);
+    float4* b4 = reinterpret_cast<float4*>(B);
+    for (int e = threadIdx.x; e < P::SIZE / 2; e += NT) b4[e] = __ldg(&s4[e]);
+  } else {
+    for (int e = threadIdx.x; e < P::SIZE; e += NT) B[e] = src[e];
   }
   __syncthreads();
-  fft_smem<T, N, true, P::CW, NT, true>(Cs, 1, CWP, tw);
-  cl.sync();   // every CTA of the cluster is running before remote stores
-  for (int e = threadIdx.x; e < N * nc; e += NT) {
-    const int y = e / nc, cc = e % nc;
-    const int o = y / RQ;
-    rem(o)[(y - o * RQ) * NH + c0 + cc] = Cs[y * CWP + cc];
-  }
-  cl.sync();   // own row slab complete
-  pack_rows<T, N>(R);
-  fft_smem<T, N, true, P::PR, NT, false>(R, P::ZP, 1, tw);
+  fft_smem<T, N, true, P::NH, NT, true>(B, 1, P::NH, tw);
+  pack_rows<T, N>(B);
+  fft_smem<T, N, true, N / 2, NT, false>(B, ZP, 1, tw);
   using V2 = typename Pair2<T>::type;
-  constexpr int ITEMS = P::PR * (N / 2);
+  constexpr int ITEMS = (N / 2) * (N / 2);
   if constexpr (MODE == C2R_STORE) {
-    T* dst = out + (long long)s * out_stride + ((long long)ix * N + row0) * N;
+    T* dst = out + (long long)s * out_stride + (long long)ix * N * N;
     for (int e = threadIdx.x; e < ITEMS; e += NT) {
       const int r = e / (N / 2), z = 2 * (e % (N / 2));
       T v[4];
-      read_item<T, N>(R, r, z, v);
+      read_item<T, N>(B, r, z, v);
       *reinterpret_cast<V2*>(dst + (2 * r) * N + z) = V2{v[0], v[2]};
       *reinterpret_cast<V2*>(dst + (2 * r + 1) * N + z) = V2{v[1], v[3]};
     }
   } else if constexpr (MODE == C2R_GATHER) {
-    cl.sync();   // every row slab holds its real rows before remote reads
     const int c = s / 3, j = s % 3;
-    const PlaneBuckets pb = plane_buckets<N>(pts.off, c, ix, q);
-    const PtRec<T>* Rp = static_cast<const PtRec<T>*>(pts.rec);
+    const PlaneBuckets pb = plane_buckets<N>(pts.off, c, ix);
+    const PtRec<T>* R = static_cast<const PtRec<T>*>(pts.rec);
     T* part = static_cast<T*>(pts.part);
     const T idl = (T)pts.inv_delta;
     for (int t = threadIdx.x; t < pb.n0 + pb.n1; t += NT) {
       const bool lower = t < pb.n0;
-      const int qq = lower ? pb.b0 + t : pb.b1 + (t - pb.n0);
-      const PtRec<T> p = Rp[qq];
+      const int q = lower ? pb.b0 + t : pb.b1 + (t - pb.n0);
+      const PtRec<T> p = R[q];
       const int iy = p.yz / N, iz = p.yz % N;
-      if (iy < row0 || iy >= row0 + RQ) continue;   // not this CTA's row (never for a consistent bucket)
       const int iy1 = (iy + 1) & (N - 1), iz1 = (iz + 1) & (N - 1);
-      const int o1 = iy1 / RQ;
-      const T v00 = *zreal_local<T, N>(R, iy - row0, iz), v01 = *zreal_local<T, N>(R, iy - row0, iz1);
-      const T v10 = *zreal_local<T, N>(rem(o1), iy1 - o1 * RQ, iz);
-      const T v11 = *zreal_local<T, N>(rem(o1), iy1 - o1 * RQ, iz1);
+      const T v00 = *zreal<T, N>(B, iy, iz), v01 = *zreal<T, N>(B, iy, iz1);
+      const T v10 = *zreal<T, N>(B, iy1, iz), v11 = *zreal<T, N>(B, iy1, iz1);
       const T wy1 = p.fy, wy0 = (T)1 - p.fy, wz1 = p.fz, wz0 = (T)1 - p.fz;
       const T a0 = wz0 * v00 + wz1 * v01, a1 = wz0 * v10 + wz1 * v11;
       const T S = wy0 * a0 + wy1 * a1;      // y-z interpolation on this plane
@@ -356,14 +309,13 @@ k_plane_c2r(const cplx<T>* __restrict__ in, long long in_stride, T* __restrict__
       const T sx = lower ? (T)-1 : (T)1;
       const T rj = rcomp(p, j);
       const int side = lower ? 0 : 1;
-      part[(long long)(side * 3 + j) * pts.ntot + qq] = rj * wx * S;
-      part[(long long)(6 + side * 3 + j) * pts.ntot + qq] =
+      part[(long long)(side * 3 + j) * pts.ntot + q] = rj * wx * S;
+      part[(long long)(6 + side * 3 + j) * pts.ntot + q] =
           rj * (p.rx * sx * S + p.ry * wx * Gy + p.rz * wx * Gz) * idl;
     }
-    cl.sync();   // remote reads done before any CTA exits
   } else {
     // ---- gradient / leapfrog epilogue (one chain per blockIdx.y) ----
-    const long long base = (long long)s * epi.grid_stride + ((long long)ix * N + row0) * N;
+    const long long base = (long long)s * epi.grid_stride + (long long)ix * N * N;
     T* w = reinterpret_cast<T*>(epi.w) + base;
     T* pw = reinterpret_cast<T*>(epi.pw) + base;
     T* gw = reinterpret_cast<T*>(epi.gw) + base;
@@ -374,9 +326,9 @@ k_plane_c2r(const cplx<T>* __restrict__ in, long long in_stride, T* __restrict__
     for (int e = threadIdx.x; e < ITEMS; e += NT) {
       const int r = e / (N / 2), z = 2 * (e % (N / 2));
       T g[4];
-      read_item<T, N>(R, r, z, g);
+      read_item<T, N>(B, r, z, g);
 #pragma unroll
-      for (int h = 0; h < 2; ++h) {   // local row 2r + h, columns z, z + 1
+      for (int h = 0; h < 2; ++h) {   // row 2r + h, columns z, z + 1
         const long long o = (long long)(2 * r + h) * N + z;
         const V2 wq = *reinterpret_cast<const V2*>(w + o);
         const T w0 = wq.x, w1 = wq.y;
@@ -390,7 +342,20 @@ k_plane_c2r(const cplx<T>* __restrict__ in, long long in_stride, T* __restrict__
           *reinterpret_cast<V2*>(pw + o) = V2{p0, p1};
           ap.add_half_sq(p0);
           ap.add_half_sq(p1);
-          if (mode == GM_KICK_DRIFT) *reinterpret_cast<V2*>(w + o) = V2{w0 + eps * p0, w1 + eps * p1};
+          if (mode == GM_KICK_DRIFT) {
+            const T n0 = w0 + eps * p0, n1 = w1 + eps * p1;
+            *reinterpret_cast<V2*>(w + o) = V2{n0, n1};
+            g[h] = n0;        // the drifted field replaces g in the plane buffer
+            g[2 + h] = n1;
+          }
+        }
+      }
+      if (next != nullptr && mode == GM_KICK_DRIFT) {
+        if constexpr (sizeof(T) == 4) {
+          *reinterpret_cast<float4*>(&B[r * ZP + z]) = make_float4(g[0], g[1], g[2], g[3]);
+        } else {
+          B[r * ZP + z] = cplx<T>{g[0], g[1]};
+          B[r * ZP + z + 1] = cplx<T>{g[2], g[3]};
         }
       }
     }
@@ -413,8 +378,23 @@ k_plane_c2r(const cplx<T>* __restrict__ in, long long in_stride, T* __restrict__
         a += red[0][i];
         b += red[1][i];
       }
-      epi.prior_part[(long long)s * N * K + ix * K + q] = a;
-      if (mode == GM_KICK_LAST) epi.kin_part[(long long)s * N * K + ix * K + q] = b;
+      epi.prior_part[(long long)s * N + ix] = a;
+      if (mode == GM_KICK_LAST) epi.kin_part[(long long)s * N + ix] = b;
+    }
+    if (next != nullptr && mode == GM_KICK_DRIFT) {
+      // forward plane transform of the drifted field for the next evaluation
+      __syncthreads();
+      fft_smem<T, N, false, N / 2, NT, false>(B, ZP, 1, tw);
+      unpack_rows<T, N>(B);
+      fft_smem<T, N, false, P::NH, NT, true>(B, 1, P::NH, tw);
+      C* dst = next + (long long)s * next_stride + (long long)ix * P::SIZE;
+      if constexpr (sizeof(T) == 4) {
+        float4* d4 = reinterpret_cast<float4*>(dst);
+        const float4* s4 = reinterpret_cast<const float4*>(B);
+        for (int e = threadIdx.x; e < P::SIZE / 2; e += NT) d4[e] = s4[e];
+      } else {
+        for (int e = threadIdx.x; e < P::SIZE; e += NT) dst[e] = B[e];
+      }
     }
   }
 }
@@ -424,8 +404,8 @@ k_plane_c2r(const cplx<T>* __restrict__ in, long long in_stride, T* __restrict__
 // amp[n2] = (2 pi/L) aHf sqrt(P(k)/Delta^3) / (k^2 N^3), amp[0] = 0, so that
 // the velocity spectrum of axis j is i n_j^odd amp[n^2] w_k.
 // ---------------------------------------------------------------------------
-constexpr int kTC = 8;        // (ky, kz) columns per tile
-constexpr int kPencilNT = 128;
+constexpr int kTC = 16;       // (ky, kz) columns per tile
+constexpr int kPencilNT = 256;
 
 template <typename T, int N, int MODE>
 __global__ void __launch_bounds__(kPencilNT)
@@ -504,7 +484,7 @@ template <typename T, int N, bool SC>
 static cudaError_t plane_r2c_t(const void* in, long long in_stride, void* out, long long out_stride,
                                int count, const void* tw, const PlanePoints& pts, cudaStream_t st) {
   constexpr size_t sm = plane_smem_bytes<T, N>();
-  dim3 grid(N * PlaneCfg<N>::K, count);
+  dim3 grid(N, count);
   k_plane_r2c<T, N, SC><<<grid, PlaneCfg<N>::NT, sm, st>>>(
       static_cast<const T*>(in), in_stride, static_cast<cplx<T>*>(out), out_stride,
       static_cast<const cplx<T>*>(tw), pts);
@@ -514,14 +494,14 @@ static cudaError_t plane_r2c_t(const void* in, long long in_stride, void* out, l
 template <typename T, int N, int MODE>
 static cudaError_t plane_c2r_t(const void* in, long long in_stride, void* out, long long out_stride,
                                int count, const void* tw, const FieldEpi* epi, const PlanePoints& pts,
-                               cudaStream_t st) {
+                               cudaStream_t st, void* next = nullptr) {
   constexpr size_t sm = plane_smem_bytes<T, N>();
-  dim3 grid(N * PlaneCfg<N>::K, count);
+  dim3 grid(N, count);
   FieldEpi e{};
   if (epi) e = *epi;
   k_plane_c2r<T, N, MODE><<<grid, PlaneCfg<N>::NT, sm, st>>>(
       static_cast<const cplx<T>*>(in), in_stride, static_cast<T*>(out), out_stride,
-      static_cast<const cplx<T>*>(tw), e, pts);
+      static_cast<const cplx<T>*>(tw), e, pts, static_cast<cplx<T>*>(next), in_stride);
   return cudaGetLastError();
 }
 
@@ -538,20 +518,15 @@ static cudaError_t pencil_t(const void* in, long long in_stride, void* out, long
   return cudaGetLastError();
 }
 
-// Supported grids: N in {8, 16, 32, 64, 128} at both precisions.
+// Supported grids: N in {8, 16, 32, 64, 128} at both precisions (one x-plane
+// of the half spectrum must fit in one CTA's shared memory).
 bool fft_supported(int prec, int N) {
   (void)prec;
   return N == 8 || N == 16 || N == 32 || N == 64 || N == 128;
 }
 
 int plane_split(int N) {
-  switch (N) {
-    case 8: return PlaneSplit<8>::K;
-    case 16: return PlaneSplit<16>::K;
-    case 32: return PlaneSplit<32>::K;
-    case 64: return PlaneSplit<64>::K;
-    case 128: return PlaneSplit<128>::K;
-  }
+  (void)N;
   return 1;
 }
 
@@ -613,11 +588,11 @@ cudaError_t launch_plane_r2c_scatter(int prec, int N, const PlanePoints& pts, vo
 
 cudaError_t launch_plane_c2r(int prec, int N, const void* in, long long in_stride, void* out,
                              long long out_stride, int count, const void* tw, const FieldEpi* epi,
-                             cudaStream_t st) {
+                             cudaStream_t st, void* next_spec) {
   PlanePoints none{};
   if (epi) {
-    HM_DISPATCH_N(prec, N, (plane_c2r_t<T, NN, C2R_EPI>(in, in_stride, out, out_stride, count, tw, epi, none, st)),
-                  (plane_c2r_t<T, NN, C2R_EPI>(in, in_stride, out, out_stride, count, tw, epi, none, st)));
+    HM_DISPATCH_N(prec, N, (plane_c2r_t<T, NN, C2R_EPI>(in, in_stride, out, out_stride, count, tw, epi, none, st, next_spec)),
+                  (plane_c2r_t<T, NN, C2R_EPI>(in, in_stride, out, out_stride, count, tw, epi, none, st, next_spec)));
   }
   HM_DISPATCH_N(prec, N, (plane_c2r_t<T, NN, C2R_STORE>(in, in_stride, out, out_stride, count, tw, nullptr, none, st)),
                 (plane_c2r_t<T, NN, C2R_STORE>(in, in_stride, out, out_stride, count, tw, nullptr, none, st)));

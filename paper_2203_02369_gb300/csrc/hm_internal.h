@@ -11,10 +11,10 @@ constexpr double kH0 = 100.0;      // km/s/(Mpc/h)
 
 enum PriorKind : int { PRIOR_TABLE = 0, PRIOR_POWER = 1 };
 
-// CTAs (one thread-block cluster) per x-plane in the plane passes; the
-// points of a plane are sub-bucketed by the CTA owning their row cy.
+// Sub-buckets of the points per x-plane (the plane passes run one CTA per
+// plane, so one bucket per plane: the points with lower CIC corner on it).
 template <int N> struct PlaneSplit {
-  static constexpr int K = N >= 128 ? 4 : (N >= 64 ? 2 : 1);
+  static constexpr int K = 1;
 };
 int plane_split(int N);
 
@@ -126,10 +126,12 @@ cudaError_t launch_plane_r2c(int prec, int N, const void* in, long long in_strid
 // 3C scatter planes built from the bucketed residuals, then transformed.
 cudaError_t launch_plane_r2c_scatter(int prec, int N, const PlanePoints& pts, void* out, long long out_stride,
                                      int count, const void* tw, cudaStream_t st);
-// count spectra -> real grids (plain store), or the gradient epilogue.
+// count spectra -> real grids (plain store), or the gradient epilogue; with
+// the epilogue and next_spec != nullptr (GM_KICK_DRIFT), the drifted field's
+// forward plane transform is written to next_spec for the next evaluation.
 cudaError_t launch_plane_c2r(int prec, int N, const void* in, long long in_stride, void* out,
                              long long out_stride, int count, const void* tw, const FieldEpi* epi,
-                             cudaStream_t st);
+                             cudaStream_t st, void* next_spec = nullptr);
 // 3C velocity spectra -> CIC partials of u and du at the bucketed points.
 cudaError_t launch_plane_c2r_gather(int prec, int N, const void* in, long long in_stride,
                                     const PlanePoints& pts, int count, const void* tw, cudaStream_t st);
@@ -148,18 +150,16 @@ cudaError_t launch_points_prep(int n_chains, int max_pts, const PointParams* pp,
                                cudaStream_t st);
 // bucket offsets, full cells, bucket-ordered records, and the FP64 terms of
 // the likelihood that depend on d alone (distance modulus, observed velocity,
-// kappa, prior) with their derivatives
+// kappa, prior) with their derivatives; clears pa.cnt_next
 cudaError_t launch_points_place(int prec, int n_chains, int max_pts, const PointParams* pp,
                                 PointArrays pa, ChainScal* cs, cudaStream_t st);
 // u, du from the plane partials, the velocity term, residuals, distance
-// gradient and Psi partials; zeroes pa.cnt_next for the kick's counting
+// gradient and Psi partials; then (mode != GM_GRAD) the leapfrog update of
+// p_d and d, the kinetic partials (GM_KICK_LAST) and the bucket counts of
+// the new distances into pa.cnt_next (GM_KICK_DRIFT).
 cudaError_t launch_points_lik(int prec, int n_chains, int max_pts, const PointParams* pp, PointArrays pa,
-                              double* pts_part, int part_stride, cudaStream_t st);
-// p_d/d update after the gradient (mode as GradMode), kinetic partials, and
-// (GM_KICK_DRIFT) the bucket counts of the new distances into pa.cnt_next.
-cudaError_t launch_points_kick(int n_chains, int max_pts, const PointParams* pp, PointArrays pa,
-                               int mode, double* kin_part, int part_stride, ChainScal* cs,
-                               cudaStream_t st);
+                              double* pts_part, int part_stride, int mode, double* kin_part, ChainScal* cs,
+                              cudaStream_t st);
 int points_blocks(int max_pts);
 cudaError_t launch_cells(int n_chains, int max_pts, const PointParams* pp, const double* d,
                          PointArrays pa, int* cell_out, cudaStream_t st);

@@ -127,8 +127,11 @@ k_points_place(const PointParams* __restrict__ pp, PointArrays pa, ChainScal* __
     }
     __syncthreads();
   }
-  if (blockIdx.x == 0)
+  if (blockIdx.x == 0) {
     for (int b = threadIdx.x; b <= NB; b += kPtsNT) pa.off[(long long)c * (NB + 1) + b] = (int)P.pt_off + excl[b];
+    // the other count half is free now: clear it for the likelihood kernel's counting
+    for (int b = threadIdx.x; b < NB; b += kPtsNT) pa.cnt_next[(long long)c * NB + b] = 0;
+  }
   const long long il = (long long)blockIdx.x * kPtsNT + threadIdx.x;
   if (il >= P.pt_n) return;
   const long long i = P.pt_off + il;
@@ -196,24 +199,23 @@ k_points_place(const PointParams* __restrict__ pp, PointArrays pa, ChainScal* __
 template <typename T>
 __global__ void __launch_bounds__(kPtsNT)
 k_points_lik(const PointParams* __restrict__ pp, PointArrays pa, double* __restrict__ pts_part,
-             int part_stride) {
+             int part_stride, int mode, double* __restrict__ kin_part, ChainScal* __restrict__ cs) {
   __shared__ double red[kPtsNT / 32];
   const int c = blockIdx.y;
   const PointParams& P = pp[c];
-  if (blockIdx.x == 0)
-    for (int b = threadIdx.x; b < P.N * P.ksplit; b += kPtsNT) pa.cnt_next[c * P.N * P.ksplit + b] = 0;
   const long long il = (long long)blockIdx.x * kPtsNT + threadIdx.x;
-  double psi_i = 0.0;
+  double psi_i = 0.0, kin = 0.0;
   if (il < P.pt_n) {
     const long long i = P.pt_off + il;
     const long long nt = pa.ntot;
     const int pos = pa.pos[i];
     const double A = pa.lk[i];
     PtRec<T>* rec = static_cast<PtRec<T>*>(pa.rec);
+    double gd;
     if (!isfinite(A)) {
       psi_i = A;
       rec[pos].r = (T)0;
-      pa.gd[i] = 0.0;
+      gd = 0.0;
     } else {
       const T* part = static_cast<const T*>(pa.part);
       double u = 0.0, du = 0.0;
@@ -227,48 +229,37 @@ k_points_lik(const PointParams* __restrict__ pp, PointArrays pa, double* __restr
       const double res_v = vo - u;
       psi_i = A + 0.5 * res_v * res_v * ik2;
       rec[pos].r = (T)(-res_v * ik2);
-      pa.gd[i] = pa.lk[nt + i] + res_v * (vop - du) * ik2 - 0.5 * res_v * res_v * k2p * ik2 * ik2;
+      gd = pa.lk[nt + i] + res_v * (vop - du) * ik2 - 0.5 * res_v * res_v * k2p * ik2 * ik2;
+    }
+    pa.gd[i] = gd;
+    if (mode != GM_GRAD) {
+      // leapfrog update of the distance (the rest of this evaluation no
+      // longer reads d: the plane records were formed from the old one)
+      double d = pa.d[i];
+      const ChainScal& S = cs[c];
+      if (S.sample_d) {
+        const double ck = (mode == GM_KICK_DRIFT) ? S.eps : 0.5 * S.eps;
+        const double p = pa.pd[i] - ck * gd;
+        pa.pd[i] = p;
+        if (mode == GM_KICK_DRIFT) {
+          d = d + S.eps * P.minv_d * p;
+          pa.d[i] = d;
+        }
+        kin = 0.5 * P.minv_d * p * p;
+      }
+      if (mode == GM_KICK_DRIFT) {
+        // buckets of the new distance, for the next evaluation
+        const int key = bucket_key(P, d, pa.rx[i], pa.ry[i]);
+        pa.cx[i] = key;
+        pa.slot[i] = atomicAdd(&pa.cnt_next[c * P.N * P.ksplit + key], 1);
+      }
     }
   }
   const double s = block_sum(psi_i, red);
   if (threadIdx.x == 0) pts_part[(long long)c * part_stride + blockIdx.x] = s;
-}
-
-// ---------------------------------------------------------------------------
-// Leapfrog update of the distances after the gradient at q_l is known.
-// ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(kPtsNT)
-k_points_kick(const PointParams* __restrict__ pp, PointArrays pa, int mode, double* __restrict__ kin_part,
-              int part_stride, ChainScal* __restrict__ cs) {
-  __shared__ double red[kPtsNT / 32];
-  const int c = blockIdx.y;
-  const PointParams& P = pp[c];
-  const long long il = (long long)blockIdx.x * kPtsNT + threadIdx.x;
-  double k = 0.0;
-  const double eps = cs[c].eps;
-  if (il < P.pt_n) {
-    const long long i = P.pt_off + il;
-    double d = pa.d[i];
-    if (cs[c].sample_d) {
-      const double ck = (mode == GM_KICK_DRIFT) ? eps : 0.5 * eps;
-      const double p = pa.pd[i] - ck * pa.gd[i];
-      pa.pd[i] = p;
-      if (mode == GM_KICK_DRIFT) {
-        d = d + eps * P.minv_d * p;
-        pa.d[i] = d;
-      }
-      k = 0.5 * P.minv_d * p * p;
-    }
-    if (mode == GM_KICK_DRIFT) {
-      // buckets of the drifted distances, for the next evaluation
-      const int key = bucket_key(P, d, pa.rx[i], pa.ry[i]);
-      pa.cx[i] = key;
-      pa.slot[i] = atomicAdd(&pa.cnt_next[c * P.N * P.ksplit + key], 1);
-    }
-  }
   if (mode == GM_KICK_LAST) {
-    const double s = block_sum(k, red);
-    if (threadIdx.x == 0) kin_part[(long long)c * part_stride + blockIdx.x] = s;
+    const double k = block_sum(kin, red);
+    if (threadIdx.x == 0) kin_part[(long long)c * part_stride + blockIdx.x] = k;
   }
 }
 
@@ -379,18 +370,14 @@ cudaError_t launch_points_place(int prec, int n_chains, int max_pts, const Point
 }
 
 cudaError_t launch_points_lik(int prec, int n_chains, int max_pts, const PointParams* pp, PointArrays pa,
-                              double* pts_part, int part_stride, cudaStream_t st) {
+                              double* pts_part, int part_stride, int mode, double* kin_part, ChainScal* cs,
+                              cudaStream_t st) {
   if (prec == 0)
-    k_points_lik<float><<<pts_grid(n_chains, max_pts), kPtsNT, 0, st>>>(pp, pa, pts_part, part_stride);
+    k_points_lik<float><<<pts_grid(n_chains, max_pts), kPtsNT, 0, st>>>(pp, pa, pts_part, part_stride, mode,
+                                                                       kin_part, cs);
   else
-    k_points_lik<double><<<pts_grid(n_chains, max_pts), kPtsNT, 0, st>>>(pp, pa, pts_part, part_stride);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_points_kick(int n_chains, int max_pts, const PointParams* pp, PointArrays pa,
-                               int mode, double* kin_part, int part_stride, ChainScal* cs,
-                               cudaStream_t st) {
-  k_points_kick<<<pts_grid(n_chains, max_pts), kPtsNT, 0, st>>>(pp, pa, mode, kin_part, part_stride, cs);
+    k_points_lik<double><<<pts_grid(n_chains, max_pts), kPtsNT, 0, st>>>(pp, pa, pts_part, part_stride, mode,
+                                                                        kin_part, cs);
   return cudaGetLastError();
 }
 
