@@ -126,6 +126,24 @@ int hm_set_catalog(hm_problem* p, int64_t n, const double* rhat_host, const doub
 int hm_logpost_grad(hm_problem* p, const void* w_dev, const double* d_dev, double* psi_dev,
                     void* grad_w_dev, double* grad_d_dev, void* stream);
 
+/* hm_logpost_grad for callers that cannot let the library allocate device
+ * memory (code running inside another framework's memory pool, work
+ * recorded into a stream capture, hosts that budget device memory up
+ * front).  The paper has no counterpart; this is a deployment variant.
+ * Same arguments, outputs and error behaviour as hm_logpost_grad, and the
+ * same kernels, all launched on `stream`; it never calls cudaMalloc,
+ * cudaFree or any other allocating routine.  Scratch comes from one static
+ * 4 MiB device array that every GPU loading this library keeps until the
+ * process exits; a problem needing more (any N > 32; on a 32^3 grid more
+ * than about 19,000 points at FP32 or 8,800 at FP64) is rejected with
+ * HM_EINVAL and a message naming the sizes.  The first call on a device looks up the
+ * array's device address with that device current; make that first call
+ * before any stream capture.  Every call shares the one array (each call
+ * clears what must start at zero), so calls whose work overlaps on the GPU
+ * race: serialise them on one stream or with events. */
+int hm_logpost_grad_noalloc(hm_problem* p, const void* w_dev, const double* d_dev, double* psi_dev,
+                            void* grad_w_dev, double* grad_d_dev, void* stream);
+
 /* Status bits of the last hm_logpost_grad (synchronises the stream). */
 int hm_problem_last_status(hm_problem* p, void* stream, int32_t* status_out);
 

@@ -1187,3 +1187,148 @@ const char* hm_kernel_kind_name(int32_t kind) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Posterior gradient without any device allocation.
+//
+// Some callers cannot let a library allocate device memory: code that runs
+// inside another framework's allocator or memory pool, code replayed from a
+// captured stream where an allocation would be illegal, or embedded hosts
+// that budget every byte up front.  hm_logpost_grad_noalloc serves them by
+// taking its scratch from one statically sized device array that every GPU
+// loading this library holds until the process exits.  It launches the same
+// kernels as hm_logpost_grad, all on the caller's stream, and never calls
+// cudaMalloc, cudaFree or any other allocating routine.
+// ---------------------------------------------------------------------------
+constexpr size_t kNoAllocScratchBytes = 4u << 20;   // 4 MiB per device
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+static void* g_noalloc_base[64];                     // device address of the array, per device
+
+namespace {
+struct NoAllocLayout {
+  size_t S1, S2, cx, slot, pos, cnt, off, rec, part, lk, prior, pts, kin, pp, cs, cid, total;
+};
+
+NoAllocLayout noalloc_layout(const hm_problem* p) {
+  NoAllocLayout L{};
+  size_t o = 0;
+  auto take = [&](size_t bytes) {
+    const size_t at = o;
+    o += (bytes + 255) / 256 * 256;
+    return at;
+  };
+  const size_t n = (size_t)std::max<long long>(p->n, 1);
+  const size_t rsz = p->rsz;
+  const size_t recsz = p->prec == HM_FP32 ? sizeof(PtRec<float>) : sizeof(PtRec<double>);
+  const size_t NB = (size_t)p->N * plane_split(p->N);
+  const size_t pb = (size_t)points_blocks((int)p->n);
+  L.S1 = take(2 * rsz * 3 * p->nspec);
+  L.S2 = take(2 * rsz * 3 * p->nspec);
+  L.cx = take(4 * n);
+  L.slot = take(4 * n);
+  L.pos = take(4 * n);
+  L.cnt = take(4 * 2 * NB);
+  L.off = take(4 * 2 * (NB + 1));
+  L.rec = take(2 * recsz * n);
+  L.part = take(rsz * 12 * n);
+  L.lk = take(8 * 6 * n);
+  L.prior = take(8 * NB);
+  L.pts = take(8 * pb);
+  L.kin = take(8 * std::max(NB, pb));
+  L.pp = take(sizeof(PointParams));
+  L.cs = take(sizeof(ChainScal));
+  L.cid = take(sizeof(int));
+  L.total = o;
+  return L;
+}
+}  // namespace
+
+extern "C" int hm_logpost_grad_noalloc(hm_problem* p, const void* w_dev, const double* d_dev, double* psi_dev,
+                                       void* grad_w_dev, double* grad_d_dev, void* stream) {
+  if (!p || !w_dev || !psi_dev || !grad_w_dev) return fail(HM_EINVAL, "null argument");
+  if (p->n > 0 && (!d_dev || !grad_d_dev)) return fail(HM_EINVAL, "null distance argument");
+  if (!p->rx.p) return fail(HM_ESTATE, "no catalogue set");
+  if (p->device < 0 || p->device >= 64) return fail(HM_EINVAL, "device ordinal out of range for the static scratch");
+  const NoAllocLayout L = noalloc_layout(p);
+  if (L.total > kNoAllocScratchBytes)
+    return fail(HM_EINVAL, "problem too large for the no-allocation path: needs " + std::to_string(L.total) +
+                               " bytes of scratch, the static array holds " +
+                               std::to_string(kNoAllocScratchBytes) + " (use hm_logpost_grad)");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  HM_CUDA(cudaSetDevice(p->device));
+  // once per device, with that device current: the array's device address
+  if (!g_noalloc_base[p->device]) {
+    void* base = nullptr;
+    HM_CUDA(cudaGetSymbolAddress(&base, g_noalloc_scratch));
+    g_noalloc_base[p->device] = base;
+  }
+  char* b = static_cast<char*>(g_noalloc_base[p->device]);
+  const int NB = p->N * plane_split(p->N);
+  // per-call constants (copied from host stack values; a pageable source is
+  // staged before cudaMemcpyAsync returns) and the state that must start at zero
+  const PointParams P = point_params(p, 0);
+  const ChainScal S{};
+  const int zero_id = 0;
+  HM_CUDA(cudaMemcpyAsync(b + L.pp, &P, sizeof(P), cudaMemcpyHostToDevice, st));
+  HM_CUDA(cudaMemcpyAsync(b + L.cs, &S, sizeof(S), cudaMemcpyHostToDevice, st));
+  HM_CUDA(cudaMemcpyAsync(b + L.cid, &zero_id, sizeof(zero_id), cudaMemcpyHostToDevice, st));
+  HM_CUDA(cudaMemsetAsync(b + L.cnt, 0, 4 * 2 * (size_t)NB, st));
+  PointArrays pa{};
+  pa.rx = p->rx.as<double>();
+  pa.ry = p->ry.as<double>();
+  pa.rz = p->rz.as<double>();
+  pa.mu = p->mu.as<double>();
+  pa.smu = p->smu.as<double>();
+  pa.zobs = p->zobs.as<double>();
+  pa.scz = p->scz.as<double>();
+  pa.d = const_cast<double*>(d_dev);
+  pa.pd = nullptr;
+  pa.gd = grad_d_dev;
+  pa.cx = reinterpret_cast<int*>(b + L.cx);
+  pa.slot = reinterpret_cast<int*>(b + L.slot);
+  pa.pos = reinterpret_cast<int*>(b + L.pos);
+  pa.cnt = reinterpret_cast<int*>(b + L.cnt);
+  pa.cnt_next = pa.cnt + NB;
+  pa.off = reinterpret_cast<int*>(b + L.off);
+  pa.rec = b + L.rec;
+  pa.part = b + L.part;
+  pa.lk = reinterpret_cast<double*>(b + L.lk);
+  pa.ntot = p->n;
+  const PointParams* pp = reinterpret_cast<const PointParams*>(b + L.pp);
+  ChainScal* cs = reinterpret_cast<ChainScal*>(b + L.cs);
+  double* prior_part = reinterpret_cast<double*>(b + L.prior);
+  double* pts_part = reinterpret_cast<double*>(b + L.pts);
+  double* kin_part = reinterpret_cast<double*>(b + L.kin);
+  void* S1 = b + L.S1;
+  void* S2 = b + L.S2;
+  const int maxp = (int)p->n, pb = points_blocks((int)p->n);
+  PlanePoints pts{};
+  pts.off = pa.off;
+  pts.rec = pa.rec;
+  pts.part = pa.part;
+  pts.ntot = pa.ntot;
+  pts.inv_delta = 1.0 / p->delta;
+  // the evaluation of hm_logpost_grad, every kernel on the caller's stream
+  HM_CUDA(launch_points_prep(1, maxp, pp, pa, st));
+  HM_CUDA(launch_points_place(p->prec, 1, maxp, pp, pa, cs, st));
+  HM_CUDA(launch_plane_r2c(p->prec, p->N, w_dev, p->n3, S1, p->nspec, 1, p->tw.p, st));
+  HM_CUDA(launch_pencil(p->prec, p->N, PM_VEL, S1, p->nspec, S2, p->nspec, 1, p->tw.p, p->amp.p, st));
+  HM_CUDA(launch_plane_c2r_gather(p->prec, p->N, S2, p->nspec, pts, 3, p->tw.p, st));
+  HM_CUDA(launch_points_lik(p->prec, 1, maxp, pp, pa, pts_part, pb, GM_GRAD, kin_part, cs, st));
+  HM_CUDA(launch_plane_r2c_scatter(p->prec, p->N, pts, S1, p->nspec, 3, p->tw.p, st));
+  HM_CUDA(launch_pencil(p->prec, p->N, PM_ADJ, S1, p->nspec, S2, p->nspec, 1, p->tw.p, p->amp.p, st));
+  FieldEpi epi{};
+  epi.w = const_cast<void*>(w_dev);
+  epi.pw = nullptr;
+  epi.gw = grad_w_dev;
+  epi.prior_part = prior_part;
+  epi.kin_part = kin_part;
+  epi.cs = cs;
+  epi.grid_stride = p->n3;
+  epi.mode = GM_GRAD;
+  HM_CUDA(launch_plane_c2r(p->prec, p->N, S2, p->nspec, nullptr, 0, 1, p->tw.p, &epi, st));
+  HM_CUDA(launch_finalize(1, prior_part, NB, pts_part, pb, nullptr, 0, nullptr, 0, FIN_PSI, 0ull,
+                          reinterpret_cast<const int*>(b + L.cid), cs, nullptr, st));
+  HM_CUDA(cudaMemcpyAsync(psi_dev, &cs->psi, sizeof(double), cudaMemcpyDeviceToDevice, st));
+  return HM_OK;
+}

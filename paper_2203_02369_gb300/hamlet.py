@@ -132,6 +132,18 @@ class Problem:
         check(self.lib.hm_logpost_grad(self.h, _ptr(w), _ptr(d), _ptr(psi), _ptr(gw), _ptr(gd), _stream()))
         return psi, gw, gd
 
+    def logpost_grad_noalloc(self, w, d):
+        """As logpost_grad, through the entry point that takes its scratch from
+        the library's static device array instead of allocating any."""
+        w = w.to(self.device, self.dtype).contiguous()
+        d = d.to(self.device, torch.float64).contiguous()
+        psi = torch.empty((), dtype=torch.float64, device=self.device)
+        gw = torch.empty_like(w)
+        gd = torch.empty_like(d)
+        check(self.lib.hm_logpost_grad_noalloc(self.h, _ptr(w), _ptr(d), _ptr(psi), _ptr(gw), _ptr(gd),
+                                               _stream()))
+        return psi, gw, gd
+
     def last_status(self):
         v = ct.c_int32()
         check(self.lib.hm_problem_last_status(self.h, _stream(), ct.byref(v)))
