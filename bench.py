@@ -51,6 +51,7 @@ def parse():
     ap.add_argument("--no-ess", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-graph", action="store_true")
+    ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--tune-eps", action="store_true", help="print acceptance for a sweep of eps and exit")
     return ap.parse_args()
 
@@ -230,6 +231,89 @@ def reference_arm(args):
 # --------------------------------------------------------------------------
 # our arm
 # --------------------------------------------------------------------------
+def run_batched(args, eps, L, use_graph):
+    """32 chains: 8 catalogues (2,000-30,000 points, each from its own seed),
+    4 chains each; even catalogues on 128^3, odd on 64^3 (box 500 Mpc/h).
+    One state per grid size; both replay their trajectory graphs at once."""
+    import torch
+    from paper_2203_02369_gb300.hamlet import Problem, State
+    from paper_2203_02369_gb300.ess import ess
+    specs = mock.batch_presets()
+    cats = [mock.make_catalog(s) for s in specs]
+    probs = [Problem.from_mock(s, c) for s, c in zip(specs, cats)]
+    states = []
+    cid = 0
+    for N in (128, 64):
+        idx = [i for i, s in enumerate(specs) if s.N == N]
+        cp, dinit, ids = [], [], []
+        for k, i in enumerate(idx):
+            for _ in range(4):
+                cp.append(k)
+                dinit.append(cats[i]["d_init"])
+                ids.append(cid)
+                cid += 1
+        states.append((N, State([probs[i] for i in idx], dinit, seed=4242, chain_problem=cp, chain_ids=ids)))
+    nch = sum(s.C for _, s in states)
+    stream = torch.cuda.current_stream()
+    for _, s in states:
+        s.run_chain(max(args.warmup, 3), L, eps, use_graph=use_graph, trace=False)
+    torch.cuda.synchronize()
+    K = max(4, args.steps // 5)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _, s in states:
+        s.run_chain(K, L, eps, use_graph=use_graph, trace=False)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    secs = e0.elapsed_time(e1) / 1e3
+    evals_per_s = nch * K * L / secs
+    # per-kernel times of the 128^3 state alone (events inside its graph)
+    s128 = states[0][1]
+    s128.profile(True)
+    s128.run_chain(1, L, eps, use_graph=use_graph, trace=False)
+    torch.cuda.synchronize()
+    s128.profile(True)
+    for _ in range(5):
+        s128.run_chain(1, L, eps, use_graph=use_graph, trace=False)
+        torch.cuda.synchronize()
+        s128.profile_collect()
+    prof = s128.profile_read()
+    s128.profile(False)
+    # ESS/s over a continuing run of all chains
+    M = 60
+    e2, e3 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e2.record(stream)
+    traces = [s.run_chain(M, L, eps, use_graph=use_graph, trace=True) for _, s in states]
+    e3.record(stream)
+    torch.cuda.synchronize()
+    msecs = e2.elapsed_time(e3) / 1e3
+    ess_tot = sum(ess(tr[:, c]["psi"]) for tr in traces for c in range(tr.shape[1]))
+    acc = float(np.mean(np.concatenate([tr["accept"].ravel() for tr in traces])))
+    n128 = states[0][1].C
+    ab = algorithmic_bytes(128, 30000, C=n128)
+    total_k = sum(v[0] for v in prof.values())
+    dname, (dms, dl) = max(prof.items(), key=lambda kv: kv[1][0])
+    peaks, src = measured_peaks()
+    kern = {k: {"us_per_launch": 1e3 * v[0] / v[1] if v[1] else None, "share": v[0] / total_k if total_k else None,
+                "gbs_algorithmic": (ab[k] / (v[0] / v[1] / 1e3) / 1e9) if v[1] and v[0] > 0 and ab.get(k) else None}
+            for k, v in prof.items()}
+    # points per chain differ: the 128^3 roofline uses the bytes of the grid terms only
+    ach = ab[dname] / (dms / dl / 1e3) / 1e9 if dl else None
+    out = {"chains": nch, "chains_128": n128, "chains_64": nch - n128, "trajectories_timed": K,
+           "grad_evals_per_s": evals_per_s, "ms_per_trajectory_all_chains": 1e3 * secs / K,
+           "ess_psi_sum": ess_tot, "ess_per_s": ess_tot / msecs, "ess_trajectories": M, "accept_rate": acc,
+           "kernels_128": kern,
+           "roofline_128": {"kernel": dname, "achieved": ach, "peak": peaks.get("hbm_gbs"), "unit": "GB/s",
+                            "frac": ach / peaks.get("hbm_gbs") if ach else None,
+                            "note": "16 chains of 128^3 in one launch; algorithmic bytes of the grid terms "
+                                    "(point terms at 3e4 points per chain, an upper bound for these catalogues)"}}
+    for _, s in states:
+        s.close()
+    for p in probs:
+        p.close()
+    return out
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -253,12 +337,19 @@ def main():
     use_graph = not args.no_graph
 
     if args.tune_eps:
-        for e in (0.005, 0.0075, 0.01, 0.0125, 0.015, 0.02, 0.03):
-            s2 = State(prob, [cat["d_init"]], seed=7)
-            s2.run_chain(30, L, e, use_graph=use_graph, trace=False)
-            tr = s2.run_chain(40, L, e, use_graph=use_graph)
+        # burn in at a small step, then measure the acceptance of each step size
+        # from the same burnt-in state (position copied into a fresh chain)
+        burn = State(prob, [cat["d_init"]], seed=7)
+        burn.run_chain(150, L, 0.01, use_graph=use_graph, trace=False)
+        g = burn.get(0)
+        for e in (0.01, 0.0125, 0.015, 0.0175, 0.02, 0.025, 0.03):
+            s2 = State(prob, [cat["d_init"]], seed=8)
+            s2.set(0, w=g["w"], d=g["d"])
+            s2.refresh()
+            tr = s2.run_chain(60, L, e, use_graph=use_graph)
             print(json.dumps({"eps": e, "accept": float(tr["accept"].mean()),
-                              "dH_median": float(np.median(np.abs(tr["H_new"] - tr["H_old"])))}), flush=True)
+                              "dH_median": float(np.median(np.abs(tr["H_new"] - tr["H_old"]))),
+                              "ess_psi": ess(tr[:, 0]["psi"])}), flush=True)
             s2.close()
         return
 
@@ -397,6 +488,13 @@ def main():
                "sample": f"{nev} oracle leapfrog steps (one gradient evaluation each) of this workload, "
                          "numpy FP64, 1 thread"}
 
+    batched = None
+    if not args.no_batched:
+        batched = run_batched(args, args.eps, L, use_graph)
+        batched["speedup_vs_plain_evals"] = batched["grad_evals_per_s"] / (args.steps * L / (my_ms / 1e3))
+        if ess_info:
+            batched["speedup_vs_plain_ess"] = batched["ess_per_s"] / ess_info["ess_per_s"]
+
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": max_ms / args.steps, "higher_is_better": True,
@@ -409,7 +507,7 @@ def main():
                            "ms_per_step_unprofiled": ms_unprof},
                 "gpu_launches": int(sum(v[1] * KERNELS_PER_PAIR.get(k, 1) for k, v in prof.items())),
                 "clocks": clk, "roofline": roofline, "kernels": kernels, "ess": ess_info,
-                "e2e": e2e, "cpu_baseline": cpu, "wall_s_timed": t_wall}
+                "e2e": e2e, "cpu_baseline": cpu, "batched": batched, "wall_s_timed": t_wall}
         print(json.dumps(line), flush=True)
     if ws > 1:
         dist.barrier()
