@@ -6,6 +6,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <memory>
 #include <string>
@@ -15,6 +16,16 @@
 #include "hm_internal.h"
 
 using namespace hm;
+
+namespace hm {
+bool pdl_enabled() {
+  static const bool on = [] {
+    const char* e = std::getenv("HM_PDL");
+    return !(e && e[0] == '0');
+  }();
+  return on;
+}
+}  // namespace hm
 
 // ---------------------------------------------------------------------------
 // errors

@@ -34,6 +34,13 @@ template <bool INV, typename C> __device__ __forceinline__ C mul_mi(C a) {
   return INV ? C{-a.y, a.x} : C{a.y, -a.x};
 }
 
+// Programmatic dependent launch: a kernel lets the next kernel in its
+// stream start launching (pdl_trigger) and waits for the previous kernel's
+// writes to be complete and visible (pdl_wait) before reading them.  Both
+// are no-ops for a launch without the programmatic-serialisation attribute.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 // Small DFTs in registers, natural order in and out.
 template <bool INV, typename C> __device__ __forceinline__ void dft2(C& a, C& b) {
   C t = a;

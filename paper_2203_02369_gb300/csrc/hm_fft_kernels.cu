@@ -200,6 +200,8 @@ template <typename T, int N, bool SCATTER>
 __global__ void __launch_bounds__(PlaneCfg<N>::NT, (sizeof(T) == 4 ? PlaneCfg<N>::MINB : 1))
 k_plane_r2c(const T* __restrict__ in, long long in_stride, cplx<T>* __restrict__ out,
             long long out_stride, const cplx<T>* __restrict__ tw, PlanePoints pts) {
+  pdl_wait();
+  pdl_trigger();
   using C = cplx<T>;
   using P = PlaneCfg<N>;
   constexpr int NT = P::NT, ZP = P::ZP;
@@ -255,6 +257,8 @@ __global__ void __launch_bounds__(PlaneCfg<N>::NT, (sizeof(T) == 4 ? PlaneCfg<N>
 k_plane_c2r(const cplx<T>* __restrict__ in, long long in_stride, T* __restrict__ out,
             long long out_stride, const cplx<T>* __restrict__ tw, FieldEpi epi, PlanePoints pts,
             cplx<T>* __restrict__ next, long long next_stride) {
+  pdl_wait();
+  pdl_trigger();
   using C = cplx<T>;
   using P = PlaneCfg<N>;
   constexpr int NT = P::NT, ZP = P::ZP;
@@ -411,6 +415,8 @@ template <typename T, int N, int MODE>
 __global__ void __launch_bounds__(kPencilNT)
 k_pencil(const cplx<T>* __restrict__ in, long long in_stride, cplx<T>* __restrict__ out,
          long long out_stride, const cplx<T>* __restrict__ tw, const T* __restrict__ amp) {
+  pdl_wait();
+  pdl_trigger();
   using C = cplx<T>;
   constexpr int NH = N / 2 + 1;
   constexpr int NCOL = N * NH;
@@ -485,10 +491,8 @@ static cudaError_t plane_r2c_t(const void* in, long long in_stride, void* out, l
                                int count, const void* tw, const PlanePoints& pts, cudaStream_t st) {
   constexpr size_t sm = plane_smem_bytes<T, N>();
   dim3 grid(N, count);
-  k_plane_r2c<T, N, SC><<<grid, PlaneCfg<N>::NT, sm, st>>>(
-      static_cast<const T*>(in), in_stride, static_cast<cplx<T>*>(out), out_stride,
-      static_cast<const cplx<T>*>(tw), pts);
-  return cudaGetLastError();
+  return launch_k(k_plane_r2c<T, N, SC>, grid, dim3(PlaneCfg<N>::NT), sm, st, static_cast<const T*>(in), in_stride,
+                  static_cast<cplx<T>*>(out), out_stride, static_cast<const cplx<T>*>(tw), pts);
 }
 
 template <typename T, int N, int MODE>
@@ -499,10 +503,9 @@ static cudaError_t plane_c2r_t(const void* in, long long in_stride, void* out, l
   dim3 grid(N, count);
   FieldEpi e{};
   if (epi) e = *epi;
-  k_plane_c2r<T, N, MODE><<<grid, PlaneCfg<N>::NT, sm, st>>>(
-      static_cast<const cplx<T>*>(in), in_stride, static_cast<T*>(out), out_stride,
-      static_cast<const cplx<T>*>(tw), e, pts, static_cast<cplx<T>*>(next), in_stride);
-  return cudaGetLastError();
+  return launch_k(k_plane_c2r<T, N, MODE>, grid, dim3(PlaneCfg<N>::NT), sm, st, static_cast<const cplx<T>*>(in),
+                  in_stride, static_cast<T*>(out), out_stride, static_cast<const cplx<T>*>(tw), e, pts,
+                  static_cast<cplx<T>*>(next), in_stride);
 }
 
 template <typename T, int N, int MODE>
@@ -512,10 +515,9 @@ static cudaError_t pencil_t(const void* in, long long in_stride, void* out, long
   constexpr int NCOMP = (MODE == PM_VEL || MODE == PM_ADJ) ? 3 : 1;
   constexpr size_t sm = sizeof(cplx<T>) * N * NCOMP * kTC;
   dim3 grid((N * NH + kTC - 1) / kTC, count);
-  k_pencil<T, N, MODE><<<grid, kPencilNT, sm, st>>>(
-      static_cast<const cplx<T>*>(in), in_stride, static_cast<cplx<T>*>(out), out_stride,
-      static_cast<const cplx<T>*>(tw), static_cast<const T*>(amp));
-  return cudaGetLastError();
+  return launch_k(k_pencil<T, N, MODE>, grid, dim3(kPencilNT), sm, st, static_cast<const cplx<T>*>(in), in_stride,
+                  static_cast<cplx<T>*>(out), out_stride, static_cast<const cplx<T>*>(tw),
+                  static_cast<const T*>(amp));
 }
 
 // Supported grids: N in {8, 16, 32, 64, 128} at both precisions (one x-plane

@@ -99,6 +99,8 @@ k_traj_begin_field(long long n3, T* __restrict__ w, T* __restrict__ pw, const T*
                    T* __restrict__ w0, T* __restrict__ gw0, unsigned long long seed,
                    const int* __restrict__ chain_id, double* __restrict__ kin_part, int draw,
                    ChainScal* __restrict__ cs) {
+  pdl_wait();
+  pdl_trigger();
   __shared__ double red[kEwNT / 32];
   const int c = blockIdx.y;
   const long long off = (long long)c * n3;
@@ -137,6 +139,8 @@ __global__ void __launch_bounds__(kEwNT)
 k_traj_begin_points(const PointParams* __restrict__ pp, PointArrays pa, double* __restrict__ d0,
                     double* __restrict__ gd0, unsigned long long seed, const int* __restrict__ chain_id,
                     double* __restrict__ kin_part, int draw, ChainScal* __restrict__ cs) {
+  pdl_wait();
+  pdl_trigger();
   __shared__ double red[kEwNT / 32];
   const int c = blockIdx.y;
   const PointParams& P = pp[c];
@@ -198,6 +202,8 @@ __global__ void k_finalize(const double* __restrict__ prior_part, int n_prior,
                            const double* __restrict__ kin_pts_part, int n_kin_pts, int what,
                            unsigned long long seed, const int* __restrict__ chain_id,
                            ChainScal* __restrict__ cs, hm_trace* __restrict__ trace) {
+  pdl_wait();
+  pdl_trigger();
   const int c = blockIdx.x;
   double a = 0.0, b = 0.0, k = 0.0, kp = 0.0;
   if (what & FIN_PSI) {
@@ -250,6 +256,8 @@ template <typename T>
 __global__ void __launch_bounds__(kEwNT)
 k_restore_field(long long n3, T* __restrict__ w, T* __restrict__ gw, const T* __restrict__ w0,
                 const T* __restrict__ gw0, const ChainScal* __restrict__ cs) {
+  pdl_wait();
+  pdl_trigger();
   const int c = blockIdx.y;
   if (cs[c].accept) return;
   const long long off = (long long)c * n3;
@@ -262,6 +270,8 @@ k_restore_field(long long n3, T* __restrict__ w, T* __restrict__ gw, const T* __
 __global__ void __launch_bounds__(kEwNT)
 k_restore_points(const PointParams* __restrict__ pp, PointArrays pa, const double* __restrict__ d0,
                  const double* __restrict__ gd0, const ChainScal* __restrict__ cs) {
+  pdl_wait();
+  pdl_trigger();
   const int c = blockIdx.y;
   if (cs[c].accept) return;
   const PointParams& P = pp[c];
@@ -275,6 +285,8 @@ k_restore_points(const PointParams* __restrict__ pp, PointArrays pa, const doubl
 
 __global__ void k_set_run(int n_chains, const double* __restrict__ eps, int sample_d,
                           ChainScal* __restrict__ cs) {
+  pdl_wait();
+  pdl_trigger();
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= n_chains) return;
   cs[c].eps = eps[c];
@@ -303,13 +315,10 @@ cudaError_t launch_traj_begin_field(int prec, int n_chains, long long n3, void* 
                                     ChainScal* cs, cudaStream_t st) {
   dim3 g(nparts, n_chains);
   if (prec == 0)
-    k_traj_begin_field<float><<<g, kEwNT, 0, st>>>(n3, (float*)w, (float*)pw, (const float*)gw, (float*)w0,
-                                                   (float*)gw0, seed, chain_id, kin_part, draw, cs);
-  else
-    k_traj_begin_field<double><<<g, kEwNT, 0, st>>>(n3, (double*)w, (double*)pw, (const double*)gw,
-                                                    (double*)w0, (double*)gw0, seed, chain_id, kin_part,
-                                                    draw, cs);
-  return cudaGetLastError();
+    return launch_k(k_traj_begin_field<float>, g, dim3(kEwNT), 0, st, n3, (float*)w, (float*)pw, (const float*)gw,
+                    (float*)w0, (float*)gw0, seed, chain_id, kin_part, draw, cs);
+  return launch_k(k_traj_begin_field<double>, g, dim3(kEwNT), 0, st, n3, (double*)w, (double*)pw,
+                  (const double*)gw, (double*)w0, (double*)gw0, seed, chain_id, kin_part, draw, cs);
 }
 
 cudaError_t launch_traj_begin_points(int n_chains, int /*max_pts*/, const PointParams* pp,
@@ -318,23 +327,20 @@ cudaError_t launch_traj_begin_points(int n_chains, int /*max_pts*/, const PointP
                                      double* kin_part, int nparts, int draw, ChainScal* cs,
                                      cudaStream_t st) {
   dim3 g(nparts, n_chains);
-  k_traj_begin_points<<<g, kEwNT, 0, st>>>(pp, pa, d0, gd0, seed, chain_id, kin_part, draw, cs);
-  return cudaGetLastError();
+  return launch_k(k_traj_begin_points, g, dim3(kEwNT), 0, st, pp, pa, d0, gd0, seed, chain_id, kin_part, draw, cs);
 }
 
 cudaError_t launch_set_run(int n_chains, const double* eps, int sample_d, ChainScal* cs,
                            cudaStream_t st) {
-  k_set_run<<<(n_chains + 127) / 128, 128, 0, st>>>(n_chains, eps, sample_d, cs);
-  return cudaGetLastError();
+  return launch_k(k_set_run, dim3((n_chains + 127) / 128), dim3(128), 0, st, n_chains, eps, sample_d, cs);
 }
 
 cudaError_t launch_finalize(int n_chains, const double* prior_part, int n_prior, const double* pts_part,
                             int n_pts, const double* kin_part, int n_kin, const double* kin_pts_part,
                             int n_kin_pts, int what, unsigned long long seed, const int* chain_id,
                             ChainScal* cs, void* trace_dev, cudaStream_t st) {
-  k_finalize<<<n_chains, 32, 0, st>>>(prior_part, n_prior, pts_part, n_pts, kin_part, n_kin, kin_pts_part,
-                                      n_kin_pts, what, seed, chain_id, cs, static_cast<hm_trace*>(trace_dev));
-  return cudaGetLastError();
+  return launch_k(k_finalize, dim3(n_chains), dim3(32), 0, st, prior_part, n_prior, pts_part, n_pts, kin_part, n_kin,
+                  kin_pts_part, n_kin_pts, what, seed, chain_id, cs, static_cast<hm_trace*>(trace_dev));
 }
 
 cudaError_t launch_restore(int prec, int n_chains, long long n3, void* w, void* gw, const void* w0,
@@ -344,19 +350,20 @@ cudaError_t launch_restore(int prec, int n_chains, long long n3, void* w, void* 
   long long nb = (n3 + kEwNT - 1) / kEwNT;
   if (nb > 1024) nb = 1024;
   dim3 g((unsigned)nb, n_chains);
+  cudaError_t e;
   if (prec == 0)
-    k_restore_field<float><<<g, kEwNT, 0, st>>>(n3, (float*)w, (float*)gw, (const float*)w0, (const float*)gw0, cs);
+    e = launch_k(k_restore_field<float>, g, dim3(kEwNT), 0, st, n3, (float*)w, (float*)gw, (const float*)w0,
+                 (const float*)gw0, cs);
   else
-    k_restore_field<double><<<g, kEwNT, 0, st>>>(n3, (double*)w, (double*)gw, (const double*)w0,
-                                                 (const double*)gw0, cs);
-  cudaError_t e = cudaGetLastError();
+    e = launch_k(k_restore_field<double>, g, dim3(kEwNT), 0, st, n3, (double*)w, (double*)gw, (const double*)w0,
+                 (const double*)gw0, cs);
   if (e != cudaSuccess) return e;
   if (max_pts > 0) {
     long long pb = (max_pts + kEwNT - 1) / kEwNT;
     if (pb > 256) pb = 256;
-    k_restore_points<<<dim3((unsigned)pb, n_chains), kEwNT, 0, st>>>(pp, pa, d0, gd0, cs);
+    return launch_k(k_restore_points, dim3((unsigned)pb, n_chains), dim3(kEwNT), 0, st, pp, pa, d0, gd0, cs);
   }
-  return cudaGetLastError();
+  return cudaSuccess;
 }
 
 cudaError_t launch_philox_raw(unsigned long long seed, long long n, unsigned int c1, unsigned int c2,

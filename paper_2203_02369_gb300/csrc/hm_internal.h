@@ -6,6 +6,27 @@
 
 namespace hm {
 
+// Kernel launch with programmatic stream serialisation (the kernel may start
+// while its predecessor in the stream finishes; it calls pdl_wait before
+// reading the predecessor's output).  pdl_enabled() is false when the
+// environment sets HM_PDL=0.
+bool pdl_enabled();
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_k(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                            Args... args) {
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cfg.attrs = attr;
+  cfg.numAttrs = pdl_enabled() ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...);
+}
+
 constexpr double kC = 299792.458;  // speed of light, km/s
 constexpr double kH0 = 100.0;      // km/s/(Mpc/h)
 

@@ -70,6 +70,8 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(kPtsNT)
 k_points_prep(const PointParams* __restrict__ pp, PointArrays pa) {
+  pdl_wait();
+  pdl_trigger();
   const int c = blockIdx.y;
   const PointParams& P = pp[c];
   const long long il = (long long)blockIdx.x * kPtsNT + threadIdx.x;
@@ -88,6 +90,8 @@ k_points_prep(const PointParams* __restrict__ pp, PointArrays pa) {
 template <typename T>
 __global__ void __launch_bounds__(kPtsNT)
 k_points_place(const PointParams* __restrict__ pp, PointArrays pa, ChainScal* __restrict__ cs) {
+  pdl_wait();
+  pdl_trigger();
   constexpr int kMaxNB = 1024;          // sub-buckets per chain (N * ksplit)
   constexpr int PERT = kMaxNB / kPtsNT;
   __shared__ int excl[kMaxNB + 1];
@@ -200,6 +204,8 @@ template <typename T>
 __global__ void __launch_bounds__(kPtsNT)
 k_points_lik(const PointParams* __restrict__ pp, PointArrays pa, double* __restrict__ pts_part,
              int part_stride, int mode, double* __restrict__ kin_part, ChainScal* __restrict__ cs) {
+  pdl_wait();
+  pdl_trigger();
   __shared__ double red[kPtsNT / 32];
   const int c = blockIdx.y;
   const PointParams& P = pp[c];
@@ -357,28 +363,24 @@ int points_blocks(int max_pts) { return max_pts > 0 ? (max_pts + kPtsNT - 1) / k
 cudaError_t launch_points_prep(int n_chains, int max_pts, const PointParams* pp, PointArrays pa,
                                cudaStream_t st) {
   if (max_pts <= 0) return cudaSuccess;
-  k_points_prep<<<pts_grid(n_chains, max_pts), kPtsNT, 0, st>>>(pp, pa);
-  return cudaGetLastError();
+  return launch_k(k_points_prep, pts_grid(n_chains, max_pts), dim3(kPtsNT), 0, st, pp, pa);
 }
 
 cudaError_t launch_points_place(int prec, int n_chains, int max_pts, const PointParams* pp,
                                 PointArrays pa, ChainScal* cs, cudaStream_t st) {
   // runs even without points: block 0 writes the (empty) bucket offsets
-  if (prec == 0) k_points_place<float><<<pts_grid(n_chains, max_pts), kPtsNT, 0, st>>>(pp, pa, cs);
-  else k_points_place<double><<<pts_grid(n_chains, max_pts), kPtsNT, 0, st>>>(pp, pa, cs);
-  return cudaGetLastError();
+  if (prec == 0) return launch_k(k_points_place<float>, pts_grid(n_chains, max_pts), dim3(kPtsNT), 0, st, pp, pa, cs);
+  return launch_k(k_points_place<double>, pts_grid(n_chains, max_pts), dim3(kPtsNT), 0, st, pp, pa, cs);
 }
 
 cudaError_t launch_points_lik(int prec, int n_chains, int max_pts, const PointParams* pp, PointArrays pa,
                               double* pts_part, int part_stride, int mode, double* kin_part, ChainScal* cs,
                               cudaStream_t st) {
   if (prec == 0)
-    k_points_lik<float><<<pts_grid(n_chains, max_pts), kPtsNT, 0, st>>>(pp, pa, pts_part, part_stride, mode,
-                                                                       kin_part, cs);
-  else
-    k_points_lik<double><<<pts_grid(n_chains, max_pts), kPtsNT, 0, st>>>(pp, pa, pts_part, part_stride, mode,
-                                                                        kin_part, cs);
-  return cudaGetLastError();
+    return launch_k(k_points_lik<float>, pts_grid(n_chains, max_pts), dim3(kPtsNT), 0, st, pp, pa, pts_part,
+                    part_stride, mode, kin_part, cs);
+  return launch_k(k_points_lik<double>, pts_grid(n_chains, max_pts), dim3(kPtsNT), 0, st, pp, pa, pts_part,
+                  part_stride, mode, kin_part, cs);
 }
 
 cudaError_t launch_cells(int n_chains, int max_pts, const PointParams* pp, const double* d,
