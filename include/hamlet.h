@@ -91,6 +91,7 @@ typedef struct hm_trace {
   double H_new;      /* Hamiltonian at the end point */
   double logu;       /* ln U of the Metropolis test, U in (0, 1] */
   double psi;        /* Psi of the chain state after the decision */
+  double eps;        /* leapfrog step used by this trajectory */
   int32_t accept;    /* 1 accepted, 0 rejected */
   int32_t status;    /* bit 1: a distance left the support; bit 2: H not finite */
 } hm_trace;
@@ -208,6 +209,19 @@ int hm_leapfrog(hm_state* s, int32_t n_steps, double eps, int32_t sample_distanc
  * graph per trajectory. */
 int hm_run_chain(hm_state* s, int32_t n_traj, int32_t n_leapfrog, const double* eps_host,
                  int32_t sample_distances, int32_t use_graph, hm_trace* trace_host, void* stream);
+
+/* Step-size tuning (section "Integrating the HMC trajectories": the step
+ * is tuned to a target acceptance, 0.65 in the paper, by dual averaging):
+ * n_warmup HMC transitions of every chain starting from eps0_host[c], the
+ * step adapted after each one from its acceptance probability
+ * min(1, exp(H_old - H_new)) (Hoffman & Gelman's recursion, gamma = 0.05,
+ * t0 = 10, kappa = 0.75, mu = log(10 eps0)); at the end each chain's step
+ * is set to the averaged iterate and written to eps_out_host[c].
+ * trace_host (may be NULL) receives the n_warmup * n_chains records,
+ * including the step each trajectory used.  Synchronises the stream. */
+int hm_adapt_step_size(hm_state* s, int32_t n_warmup, int32_t n_leapfrog, double target_accept,
+                       const double* eps0_host, int32_t sample_distances, double* eps_out_host,
+                       hm_trace* trace_host, void* stream);
 
 /* Per-kernel timing of hm_run_chain: with profiling enabled, every kernel
  * launch of a trajectory is bracketed by a pair of CUDA events on the

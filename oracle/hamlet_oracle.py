@@ -616,6 +616,72 @@ def run_chain(prob, w, d, seed, chain, traj0, n_traj, eps, n_steps, sample_d=Tru
 
 
 # ----------------------------------------------------------------------------
+# Step-size tuning by dual averaging (section "Integrating the HMC
+# trajectories": the step size is tuned to a target acceptance of 0.65 with
+# the dual-averaging scheme of Hoffman & Gelman).  After trajectory m with
+# acceptance probability alpha_m = min(1, exp(H_old - H_new)):
+#   Hbar_m = (1 - 1/(m + t0)) Hbar_{m-1} + (delta - alpha_m)/(m + t0)
+#   log eps_m = mu - sqrt(m)/gamma * Hbar_m
+#   log epsbar_m = m^-kappa log eps_m + (1 - m^-kappa) log epsbar_{m-1}
+# with mu = log(10 eps_0), Hbar_0 = 0, log epsbar_0 = 0; the tuned step is
+# epsbar at the end of the warm-up.
+# ----------------------------------------------------------------------------
+DA_GAMMA = 0.05
+DA_T0 = 10.0
+DA_KAPPA = 0.75
+
+
+def accept_probability(H_old, H_new):
+    if not np.isfinite(H_new):
+        return 0.0
+    return float(min(1.0, math.exp(min(0.0, H_old - H_new))))
+
+
+class DualAveraging:
+    def __init__(self, eps0, delta=0.65):
+        self.mu = math.log(10.0 * eps0)
+        self.delta = delta
+        self.m = 0
+        self.Hbar = 0.0
+        self.log_eps = math.log(eps0)
+        self.log_eps_bar = 0.0
+
+    def update(self, alpha):
+        self.m += 1
+        m = float(self.m)
+        w = 1.0 / (m + DA_T0)
+        self.Hbar = (1.0 - w) * self.Hbar + w * (self.delta - alpha)
+        self.log_eps = self.mu - math.sqrt(m) / DA_GAMMA * self.Hbar
+        eta = m ** (-DA_KAPPA)
+        self.log_eps_bar = eta * self.log_eps + (1.0 - eta) * self.log_eps_bar
+        return math.exp(self.log_eps)
+
+    @property
+    def eps(self):
+        return math.exp(self.log_eps)
+
+    @property
+    def eps_bar(self):
+        return math.exp(self.log_eps_bar)
+
+
+def adapt_step_size(prob, w, d, seed, chain, traj0, n_warmup, eps0, n_steps, delta=0.65, sample_d=True):
+    """n_warmup HMC transitions with the step size adapted after each one;
+    returns (w, d, eps_bar, records with the step used)."""
+    da = DualAveraging(eps0, delta)
+    psi_grad = logpost_grad(prob, w, d)
+    recs = []
+    eps = eps0
+    for t in range(n_warmup):
+        w, d, psi_grad, rec = hmc_trajectory(prob, w, d, psi_grad, seed, traj0 + t, chain, eps, n_steps,
+                                             sample_d)
+        rec["eps"] = eps
+        recs.append(rec)
+        eps = da.update(accept_probability(rec["H_old"], rec["H_new"]))
+    return w, d, da.eps_bar, recs
+
+
+# ----------------------------------------------------------------------------
 # Dense Wiener filter for fixed distances (the posterior is then Gaussian).
 # ----------------------------------------------------------------------------
 def response_matrix(prob, d):

@@ -41,7 +41,7 @@ class hm_problem_info(ct.Structure):
 class hm_trace(ct.Structure):
     _fields_ = [
         ("traj", ct.c_int64), ("H_old", ct.c_double), ("H_new", ct.c_double),
-        ("logu", ct.c_double), ("psi", ct.c_double), ("accept", ct.c_int32),
+        ("logu", ct.c_double), ("psi", ct.c_double), ("eps", ct.c_double), ("accept", ct.c_int32),
         ("status", ct.c_int32),
     ]
 
@@ -79,6 +79,8 @@ SIGNATURES = [
     ("hm_leapfrog", ct.c_int, [_P, ct.c_int32, ct.c_double, ct.c_int32, _P]),
     ("hm_run_chain", ct.c_int, [_P, ct.c_int32, ct.c_int32, c_double_p, ct.c_int32, ct.c_int32,
                                 ct.POINTER(hm_trace), _P]),
+    ("hm_adapt_step_size", ct.c_int, [_P, ct.c_int32, ct.c_int32, ct.c_double, c_double_p, ct.c_int32,
+                                      c_double_p, ct.POINTER(hm_trace), _P]),
     ("hm_state_profile", ct.c_int, [_P, ct.c_int32]),
     ("hm_state_profile_collect", ct.c_int, [_P]),
     ("hm_state_profile_read", ct.c_int, [_P, ct.c_int32, c_double_p, ct.POINTER(ct.c_int64),

@@ -1059,22 +1059,8 @@ static int trajectory(hm_state* s, int n_leapfrog, cudaStream_t st, Prof* pf) {
   return HM_OK;
 }
 
-int hm_run_chain(hm_state* s, int32_t n_traj, int32_t n_leapfrog, const double* eps_host, int32_t sample_distances,
-                 int32_t use_graph, hm_trace* trace_host, void* stream) {
-  if (!s || !eps_host) return fail(HM_EINVAL, "null argument");
-  if (n_traj < 0 || n_leapfrog <= 0) return fail(HM_EINVAL, "n_traj >= 0 and n_leapfrog > 0 required");
-  cudaStream_t st = static_cast<cudaStream_t>(stream);
-  HM_CUDA(cudaSetDevice(s->device));
-  const size_t need = sizeof(hm_trace) * (size_t)std::max(1, n_traj) * s->C;
-  if (s->trace_cap < need) {
-    HM_TRY(s->trace_dev.alloc(need));
-    s->trace_cap = need;
-    if (s->gexec) {
-      cudaGraphExecDestroy(s->gexec);
-      s->gexec = nullptr;
-    }
-  }
-  HM_TRY(set_run(s, eps_host, sample_distances, st));
+static int run_traj_loop(hm_state* s, int32_t n_traj, int32_t n_leapfrog, int32_t sample_distances,
+                         int32_t use_graph, cudaStream_t st) {
   Prof* pf = s->prof.get();
   if (pf) {
     HM_TRY(profile_collect(s));
@@ -1144,11 +1130,60 @@ int hm_run_chain(hm_state* s, int32_t n_traj, int32_t n_leapfrog, const double* 
     HM_CUDA(cudaStreamWaitEvent(st, ev, 0));
     HM_CUDA(cudaEventDestroy(ev));
   }
+  return HM_OK;
+}
+
+int hm_run_chain(hm_state* s, int32_t n_traj, int32_t n_leapfrog, const double* eps_host, int32_t sample_distances,
+                 int32_t use_graph, hm_trace* trace_host, void* stream) {
+  if (!s || !eps_host) return fail(HM_EINVAL, "null argument");
+  if (n_traj < 0 || n_leapfrog <= 0) return fail(HM_EINVAL, "n_traj >= 0 and n_leapfrog > 0 required");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  HM_CUDA(cudaSetDevice(s->device));
+  const size_t need = sizeof(hm_trace) * (size_t)std::max(1, n_traj) * s->C;
+  if (s->trace_cap < need) {
+    HM_TRY(s->trace_dev.alloc(need));
+    s->trace_cap = need;
+    if (s->gexec) {
+      cudaGraphExecDestroy(s->gexec);
+      s->gexec = nullptr;
+    }
+  }
+  HM_TRY(set_run(s, eps_host, sample_distances, st));
+  HM_TRY(run_traj_loop(s, n_traj, n_leapfrog, sample_distances, use_graph, st));
   if (trace_host && n_traj > 0) {
     HM_CUDA(cudaMemcpyAsync(trace_host, s->trace_dev.p, sizeof(hm_trace) * (size_t)n_traj * s->C,
                             cudaMemcpyDeviceToHost, st));
     HM_CUDA(cudaStreamSynchronize(st));
   }
+  return HM_OK;
+}
+
+int hm_adapt_step_size(hm_state* s, int32_t n_warmup, int32_t n_leapfrog, double target_accept,
+                       const double* eps0_host, int32_t sample_distances, double* eps_out_host,
+                       hm_trace* trace_host, void* stream) {
+  if (!s || !eps0_host || !eps_out_host) return fail(HM_EINVAL, "null argument");
+  if (n_warmup <= 0 || n_leapfrog <= 0) return fail(HM_EINVAL, "n_warmup and n_leapfrog must be > 0");
+  if (!(target_accept > 0 && target_accept < 1)) return fail(HM_EINVAL, "target_accept must be in (0, 1)");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  HM_CUDA(cudaSetDevice(s->device));
+  const size_t need = sizeof(hm_trace) * (size_t)n_warmup * s->C;
+  if (s->trace_cap < need) {
+    HM_TRY(s->trace_dev.alloc(need));
+    s->trace_cap = need;
+    if (s->gexec) {
+      cudaGraphExecDestroy(s->gexec);
+      s->gexec = nullptr;
+    }
+  }
+  HM_TRY(set_run(s, eps0_host, sample_distances, st));
+  HM_CUDA(launch_da(s->C, 1, target_accept, nullptr, s->cs.as<ChainScal>(), st));
+  HM_TRY(run_traj_loop(s, n_warmup, n_leapfrog, sample_distances, 1, st));
+  HM_CUDA(launch_da(s->C, 0, target_accept, s->eps_dev.as<double>(), s->cs.as<ChainScal>(), st));
+  HM_CUDA(cudaMemcpyAsync(eps_out_host, s->eps_dev.p, 8 * s->C, cudaMemcpyDeviceToHost, st));
+  if (trace_host)
+    HM_CUDA(cudaMemcpyAsync(trace_host, s->trace_dev.p, need, cudaMemcpyDeviceToHost, st));
+  HM_CUDA(cudaStreamSynchronize(st));
+  for (int c = 0; c < s->C; ++c) s->eps_host[c] = eps_out_host[c];
   return HM_OK;
 }
 

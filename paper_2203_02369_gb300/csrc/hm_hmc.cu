@@ -243,11 +243,24 @@ __global__ void k_finalize(const double* __restrict__ prior_part, int n_prior,
       t.H_new = S.H_new;
       t.logu = S.logu;
       t.psi = acc ? S.psi : S.psi0;
+      t.eps = S.eps;
       t.accept = acc;
       t.status = S.status;
     }
     if (!acc) S.psi = S.psi0;
     S.traj += 1;
+    if (S.da_on) {
+      // dual averaging (Hoffman & Gelman) toward acceptance probability da_delta
+      const double alpha = fin ? fmin(1.0, exp(fmin(0.0, dH))) : 0.0;
+      S.da_m += 1;
+      const double m = (double)S.da_m;
+      const double wgt = 1.0 / (m + 10.0);
+      S.da_Hbar = (1.0 - wgt) * S.da_Hbar + wgt * (S.da_delta - alpha);
+      const double leps = S.da_mu - sqrt(m) / 0.05 * S.da_Hbar;
+      const double eta = pow(m, -0.75);
+      S.da_lepsbar = eta * leps + (1.0 - eta) * S.da_lepsbar;
+      S.eps = exp(leps);
+    }
   }
 }
 
@@ -293,6 +306,25 @@ __global__ void k_set_run(int n_chains, const double* __restrict__ eps, int samp
   cs[c].sample_d = sample_d;
   cs[c].traj_run0 = cs[c].traj;
   cs[c].status = 0;
+}
+
+__global__ void k_da(int n_chains, int start, double delta, double* __restrict__ eps_out,
+                     ChainScal* __restrict__ cs) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= n_chains) return;
+  ChainScal& S = cs[c];
+  if (start) {
+    S.da_on = 1;
+    S.da_m = 0;
+    S.da_Hbar = 0.0;
+    S.da_lepsbar = 0.0;
+    S.da_mu = log(10.0 * S.eps);
+    S.da_delta = delta;
+  } else {
+    S.da_on = 0;
+    if (S.da_m > 0) S.eps = exp(S.da_lepsbar);
+    if (eps_out) eps_out[c] = S.eps;
+  }
 }
 
 __global__ void k_philox_raw(unsigned long long seed, long long n, unsigned c1, unsigned c2, unsigned c3,
@@ -364,6 +396,11 @@ cudaError_t launch_restore(int prec, int n_chains, long long n3, void* w, void* 
     return launch_k(k_restore_points, dim3((unsigned)pb, n_chains), dim3(kEwNT), 0, st, pp, pa, d0, gd0, cs);
   }
   return cudaSuccess;
+}
+
+cudaError_t launch_da(int n_chains, int start, double delta, double* eps_out, ChainScal* cs, cudaStream_t st) {
+  k_da<<<(n_chains + 127) / 128, 128, 0, st>>>(n_chains, start, delta, eps_out, cs);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_philox_raw(unsigned long long seed, long long n, unsigned int c1, unsigned int c2,

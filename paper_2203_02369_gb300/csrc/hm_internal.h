@@ -72,6 +72,9 @@ struct ChainScal {
   int status;            // bit flags, see STATUS_*
   int n_bad;             // unused (kept for layout)
   int sample_d;          // 1: distances move, 0: held fixed
+  // dual-averaging step-size adaptation (active while da_on != 0)
+  double da_Hbar, da_lepsbar, da_mu, da_delta;
+  int da_on, da_m;
 };
 
 enum : int { STATUS_DOMAIN = 1, STATUS_NONFINITE = 2 };
@@ -210,6 +213,9 @@ cudaError_t launch_restore(int prec, int n_chains, long long n3, void* w, void* 
                            const void* gw0, int max_pts, const PointParams* pp, PointArrays pa,
                            const double* d0, const double* gd0, const ChainScal* cs,
                            cudaStream_t st);
+// Dual averaging: start (mu = log(10 eps), target delta) / finish (eps = epsbar,
+// copied to eps_out[c]) on every chain.
+cudaError_t launch_da(int n_chains, int start, double delta, double* eps_out, ChainScal* cs, cudaStream_t st);
 cudaError_t launch_philox_raw(unsigned long long seed, long long n, unsigned int c1, unsigned int c2,
                               unsigned int c3, unsigned int* out, cudaStream_t st);
 

@@ -178,7 +178,7 @@ class Problem:
 
 
 TRACE_DTYPE = np.dtype([("traj", np.int64), ("H_old", np.float64), ("H_new", np.float64),
-                        ("logu", np.float64), ("psi", np.float64), ("accept", np.int32),
+                        ("logu", np.float64), ("psi", np.float64), ("eps", np.float64), ("accept", np.int32),
                         ("status", np.int32)])
 
 
@@ -266,6 +266,16 @@ class State:
         ln = (ct.c_int64 * 64)()
         check(self.lib.hm_state_profile_read(self.h, 64, ms, ln, ct.byref(nk)))
         return {self.lib.hm_kernel_kind_name(k).decode(): (ms[k], ln[k]) for k in range(nk.value)}
+
+    def adapt_step_size(self, n_warmup, n_leapfrog, eps0, target=0.65, sample_distances=True):
+        """Dual-averaging warm-up; returns (tuned eps per chain, trace)."""
+        e0 = np.ascontiguousarray(np.broadcast_to(np.asarray(eps0, dtype=np.float64), (self.C,)))
+        eo = np.zeros(self.C)
+        tr = (_lib.hm_trace * (max(n_warmup, 1) * self.C))()
+        check(self.lib.hm_adapt_step_size(self.h, int(n_warmup), int(n_leapfrog), float(target), _dptr(e0),
+                                          int(bool(sample_distances)), _dptr(eo), tr, _stream()))
+        out = np.frombuffer(tr, dtype=TRACE_DTYPE, count=n_warmup * self.C).copy()
+        return eo, out.reshape(n_warmup, self.C)
 
     def leapfrog(self, n_steps, eps, sample_distances=True):
         check(self.lib.hm_leapfrog(self.h, int(n_steps), float(eps), int(bool(sample_distances)), _stream()))

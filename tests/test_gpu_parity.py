@@ -242,3 +242,16 @@ def test_batched_chains_match_single_chains(H):
         gs, gb = single.get(0), batch.get(c)
         assert rel(gs["w"].cpu().numpy(), gb["w"].cpu().numpy()) < 1e-5
         assert rel(gs["d"].cpu().numpy(), gb["d"].cpu().numpy()) < 1e-6
+
+
+def test_dual_averaging_matches_oracle_recursion(H):
+    spec, cat, gp, op, st = _state_and_oracle(H, 16, 200.0, 500, "fp64", 61)
+    eps_out, tr = st.adapt_step_size(40, 10, 0.002, target=0.65)
+    da = O.DualAveraging(0.002, delta=0.65)
+    for t in range(40):
+        assert abs(tr[t, 0]["eps"] - da.eps) <= 1e-12 * da.eps
+        da.update(O.accept_probability(tr[t, 0]["H_old"], tr[t, 0]["H_new"]))
+    assert abs(eps_out[0] - da.eps_bar) <= 1e-12 * da.eps_bar
+    # the tuned step is used by the following run
+    tr2 = st.run_chain(3, 10, eps_out)
+    assert np.allclose(tr2[:, 0]["eps"], eps_out[0])

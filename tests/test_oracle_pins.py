@@ -426,3 +426,36 @@ def test_prior_only_chain_samples_unit_normal():
     ws = np.array(ws[50:])
     assert abs(ws.mean()) < 0.1
     assert abs(ws.var() - 1.0) < 0.15
+
+
+# ------------------------------------------------------- dual averaging ----
+def test_dual_averaging_fixed_point_and_direction():
+    # acceptance exactly at the target leaves Hbar = 0: eps stays at 10 eps0
+    da = O.DualAveraging(0.1, delta=0.65)
+    for _ in range(20):
+        e = da.update(0.65)
+    assert abs(e - 1.0) < 1e-12 and abs(da.Hbar) < 1e-15
+    # accepting more than the target makes the step grow, less makes it shrink
+    hi, lo = O.DualAveraging(0.1), O.DualAveraging(0.1)
+    for _ in range(30):
+        hi.update(1.0)
+        lo.update(0.0)
+    assert hi.eps > 1.0 > lo.eps
+    # the averaged step is a weighted mean of the iterates (log scale)
+    assert lo.eps <= lo.eps_bar or abs(lo.eps - lo.eps_bar) < 1e-9
+
+
+def test_dual_averaging_reaches_target_acceptance_on_a_gaussian():
+    # pure prior (unit Gaussian in every coordinate): after adaptation the
+    # chain's mean acceptance is near the target
+    p = _prior_only(N=4)
+    w = np.zeros((4, 4, 4))
+    w, _, eps_bar, recs = O.adapt_step_size(p, w, np.zeros(0), seed=9, chain=0, traj0=0, n_warmup=300,
+                                            eps0=0.05, n_steps=5, delta=0.65)
+    psi_grad = O.logpost_grad(p, w, np.zeros(0))
+    acc = []
+    for t in range(400):
+        w, _, psi_grad, rec = O.hmc_trajectory(p, w, np.zeros(0), psi_grad, seed=9, traj=1000 + t, chain=0,
+                                               eps=eps_bar, n_steps=5)
+        acc.append(O.accept_probability(rec["H_old"], rec["H_new"]))
+    assert abs(np.mean(acc) - 0.65) < 0.1
