@@ -243,6 +243,16 @@ int hm_state_profile_read(hm_state* s, int32_t max_kinds, double* ms_out, int64_
                           int32_t* n_kinds);
 const char* hm_kernel_kind_name(int32_t kind);
 
+/* The distance prior of eq. D from the observed redshifts (host only, no
+ * device work): d_z of each cz_host[i]/c by eq. e:dz (flat LCDM, composite
+ * Simpson with 64 intervals), histogram on [0, max d_z + pad) in bins of
+ * bin_width, each count + 0.5, normalised to a density; logdens_out[b] =
+ * ln density (the table of hm_problem_desc, d0 = 0).  *nbins_out receives
+ * the bin count; with logdens_out NULL or max_bins too small only the count
+ * is returned (HM_EINVAL in the latter case). */
+int hm_dz_prior_table(double omega_m, int64_t n, const double* cz_host, double bin_width, double pad,
+                      int32_t max_bins, double* logdens_out, int32_t* nbins_out);
+
 /* Raw Philox-4x32-10 blocks for counters (q, c1, c2, c3), q = 0..n-1, key
  * seed: out_dev receives 4 n uint32 words. */
 int hm_philox(uint64_t seed, int64_t n, uint32_t c1, uint32_t c2, uint32_t c3, uint32_t* out_dev,

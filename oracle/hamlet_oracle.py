@@ -461,6 +461,38 @@ def log_prior_d(prob, d):
     raise ValueError(kind)
 
 
+DZ_SIMPSON_INTERVALS = 64
+
+
+def redshift_distance(z, omega_m):
+    """eq. e:dz: d_z = (c/H0) int_0^z dz'/sqrt(Om (1+z')^3 + 1 - Om), Mpc/h;
+    composite Simpson with DZ_SIMPSON_INTERVALS intervals on [0, z]."""
+    z = np.atleast_1d(np.asarray(z, dtype=np.float64))
+    out = np.empty_like(z)
+    n = DZ_SIMPSON_INTERVALS
+    wts = np.ones(n + 1)
+    wts[1:-1:2] = 4.0
+    wts[2:-1:2] = 2.0
+    for i, zi in enumerate(z):
+        x = np.linspace(0.0, zi, n + 1)
+        f = 1.0 / np.sqrt(omega_m * (1.0 + x) ** 3 + 1.0 - omega_m)
+        out[i] = C_KMS / H0 * (zi / n) / 3.0 * float(np.sum(wts * f))
+    return out
+
+
+def dz_prior_table(cz, omega_m, bin_width, pad):
+    """eq. D: histogram of the observed redshift distances on [0, max d_z +
+    pad) in bins of bin_width, each count + 0.5, normalised to a density;
+    returns ln density per bin (the table the distance prior interpolates)."""
+    dz = redshift_distance(np.maximum(np.asarray(cz, float), 0.0) / C_KMS, omega_m)
+    nb = int(np.ceil((dz.max() + pad) / bin_width))
+    counts = np.zeros(nb)
+    b = np.minimum((dz / bin_width).astype(np.int64), nb - 1)
+    np.add.at(counts, b, 1.0)
+    dens = (counts + 0.5) / ((counts + 0.5).sum() * bin_width)
+    return np.log(dens)
+
+
 def in_domain(prob, d):
     """d > 0 and 1 - 3 Om H0 d / c > 0 (zbar real)."""
     return (d > 0) & (1.0 - 3.0 * prob.omega_m * H0 * d / C_KMS > 0)

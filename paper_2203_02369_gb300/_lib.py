@@ -86,6 +86,8 @@ SIGNATURES = [
     ("hm_state_profile_read", ct.c_int, [_P, ct.c_int32, c_double_p, ct.POINTER(ct.c_int64),
                                          ct.POINTER(ct.c_int32)]),
     ("hm_kernel_kind_name", ct.c_char_p, [ct.c_int32]),
+    ("hm_dz_prior_table", ct.c_int, [ct.c_double, ct.c_int64, c_double_p, ct.c_double, ct.c_double, ct.c_int32,
+                                     c_double_p, ct.POINTER(ct.c_int32)]),
     ("hm_philox", ct.c_int, [ct.c_uint64, ct.c_int64, ct.c_uint32, ct.c_uint32, ct.c_uint32, _P, _P]),
     ("hm_last_error", ct.c_char_p, []),
 ]

@@ -757,6 +757,39 @@ int hm_cells(hm_problem* p, const double* d_dev, int32_t* cell_dev, int32_t* per
   return HM_OK;
 }
 
+int hm_dz_prior_table(double omega_m, int64_t n, const double* cz_host, double bin_width, double pad,
+                      int32_t max_bins, double* logdens_out, int32_t* nbins_out) {
+  if (n <= 0 || !cz_host || !nbins_out) return fail(HM_EINVAL, "need n > 0 redshifts and nbins_out");
+  if (!(bin_width > 0) || !(pad >= 0) || !(omega_m > 0)) return fail(HM_EINVAL, "bad bin width, pad or omega_m");
+  HM_TRY(check_finite(cz_host, n, "cz"));
+  // eq. e:dz by composite Simpson, 64 intervals on [0, z]
+  auto dz = [&](double z) {
+    const int m = 64;
+    double s = 0.0;
+    for (int i = 0; i <= m; ++i) {
+      const double x = z * i / m;
+      const double f = 1.0 / std::sqrt(omega_m * (1.0 + x) * (1.0 + x) * (1.0 + x) + 1.0 - omega_m);
+      s += ((i == 0 || i == m) ? 1.0 : ((i & 1) ? 4.0 : 2.0)) * f;
+    }
+    return kC / kH0 * (z / m) / 3.0 * s;
+  };
+  std::vector<double> d(n);
+  double dmax = 0.0;
+  for (long long i = 0; i < n; ++i) {
+    d[i] = dz(std::max(cz_host[i], 0.0) / kC);
+    dmax = std::max(dmax, d[i]);
+  }
+  const long long nb = (long long)std::ceil((dmax + pad) / bin_width);
+  *nbins_out = (int32_t)nb;
+  if (nb > max_bins || !logdens_out) return nb > max_bins ? fail(HM_EINVAL, "max_bins too small (see nbins_out)") : HM_OK;
+  std::vector<double> cnt(nb, 0.0);
+  for (long long i = 0; i < n; ++i) cnt[std::min<long long>((long long)(d[i] / bin_width), nb - 1)] += 1.0;
+  double tot = 0.0;
+  for (long long b = 0; b < nb; ++b) tot += cnt[b] + 0.5;
+  for (long long b = 0; b < nb; ++b) logdens_out[b] = std::log((cnt[b] + 0.5) / (tot * bin_width));
+  return HM_OK;
+}
+
 int hm_philox(uint64_t seed, int64_t n, uint32_t c1, uint32_t c2, uint32_t c3, uint32_t* out_dev, void* stream) {
   if (n < 0 || (n > 0 && !out_dev)) return fail(HM_EINVAL, "bad argument");
   HM_CUDA(launch_philox_raw(seed, n, c1, c2, c3, out_dev, static_cast<cudaStream_t>(stream)));

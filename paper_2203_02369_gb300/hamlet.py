@@ -296,3 +296,17 @@ def philox(seed, n, c1, c2, c3, device=0):
     out = torch.empty(4 * n, dtype=torch.int32, device=torch.device("cuda", device))
     check(lib.hm_philox(ct.c_uint64(int(seed)), int(n), c1, c2, c3, _ptr(out), _stream()))
     return out.view(torch.int32)
+
+
+def dz_prior_table(cz, omega_m=0.3, bin_width=5.0, pad=10.0):
+    """ln density table of the redshift-distance histogram prior (eq. D),
+    computed by libhamlet on the host; use as ("table", 0.0, bin_width, table)."""
+    lib = _lib.load()
+    cz = np.ascontiguousarray(cz, dtype=np.float64)
+    nb = ct.c_int32()
+    lib.hm_dz_prior_table(float(omega_m), cz.shape[0], _dptr(cz), float(bin_width), float(pad), 0, None,
+                          ct.byref(nb))
+    out = np.zeros(nb.value)
+    check(lib.hm_dz_prior_table(float(omega_m), cz.shape[0], _dptr(cz), float(bin_width), float(pad), nb.value,
+                                _dptr(out), ct.byref(nb)))
+    return out

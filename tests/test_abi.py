@@ -60,3 +60,14 @@ def test_invalid_problem_rejected_before_any_device_call():
     assert lib.hm_init_problem(ct.byref(d), ct.byref(h)) == _lib.HM_EINVAL
     assert lib.hm_set_catalog(None, 0, None, None, None, None, None) == _lib.HM_EINVAL
     assert lib.hm_run_chain(None, 1, 1, None, 1, 0, None, None) == _lib.HM_EINVAL
+
+
+def test_dz_prior_table_host_entry_matches_oracle():
+    from oracle import hamlet_oracle as O
+    from paper_2203_02369_gb300 import mock
+    from paper_2203_02369_gb300.hamlet import dz_prior_table
+    cat = mock.make_catalog(mock.PRESETS["cfg2_64"])
+    got = dz_prior_table(cat["cz"], 0.3, 5.0, 12.0)
+    ref = O.dz_prior_table(cat["cz"], 0.3, 5.0, 12.0)
+    assert got.shape == ref.shape
+    assert np.max(np.abs(got - ref)) < 1e-12

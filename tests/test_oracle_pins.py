@@ -459,3 +459,29 @@ def test_dual_averaging_reaches_target_acceptance_on_a_gaussian():
                                                eps=eps_bar, n_steps=5)
         acc.append(O.accept_probability(rec["H_old"], rec["H_new"]))
     assert abs(np.mean(acc) - 0.65) < 0.1
+
+
+# --------------------------------------------- redshift-distance prior ----
+def test_redshift_distance_quadrature_and_expansion():
+    om = 0.3
+    z = np.array([1e-4, 0.01, 0.05, 0.1])
+    got = O.redshift_distance(z, om)
+    for zi, g in zip(z, got):
+        ref, _ = integrate.quad(lambda x: 1.0 / np.sqrt(om * (1 + x) ** 3 + 1 - om), 0, zi, epsabs=0, epsrel=1e-13)
+        assert abs(g - O.C_KMS / 100.0 * ref) < 1e-10 * g
+        # d_z = (c/H0) (z - (3 Om/4) z^2 + O(z^3))
+        series = O.C_KMS / 100.0 * (zi - 0.75 * om * zi ** 2)
+        assert abs(g - series) < O.C_KMS / 100.0 * 2.0 * zi ** 3
+
+
+def test_dz_prior_table_counts_and_normalisation():
+    cz = np.array([1000.0, 1500.0, 2900.0, 3100.0, 12000.0])
+    ld = O.dz_prior_table(cz, 0.3, 5.0, 10.0)
+    dens = np.exp(ld)
+    assert abs(np.sum(dens) * 5.0 - 1.0) < 1e-12
+    dz = O.redshift_distance(cz / O.C_KMS, 0.3)
+    assert len(ld) == int(np.ceil((dz.max() + 10.0) / 5.0))
+    # bins with points have (count + 0.5) / (count' + 0.5) density ratios
+    b = (dz / 5.0).astype(int)
+    empty = [k for k in range(len(ld)) if k not in set(b)][0]
+    assert abs(dens[b[0]] / dens[empty] - (np.sum(b == b[0]) + 0.5) / 0.5) < 1e-12
