@@ -210,6 +210,18 @@ int hm_leapfrog(hm_state* s, int32_t n_steps, double eps, int32_t sample_distanc
 int hm_run_chain(hm_state* s, int32_t n_traj, int32_t n_leapfrog, const double* eps_host,
                  int32_t sample_distances, int32_t use_graph, hm_trace* trace_host, void* stream);
 
+/* sigma_NL as a sampled parameter (eq. q; section "The Likelihood function:
+ * velocities" makes it a model parameter, eq. M_ab gives it unit mass): with
+ * enable != 0 every chain carries sigma_NL (starting at sigma0_host[c], or
+ * the problem's value when NULL) and its momentum through the leapfrog, with
+ * a flat prior on sigma_NL > 0 (the paper states none; sigma_NL <= 0 gives
+ * Psi = +inf).  Psi and the gradient are re-evaluated before returning
+ * (synchronises the stream).  enable = 0 returns to the problem's fixed
+ * value.  hm_state_get_sigma_nl copies each chain's current sigma_NL and
+ * dPsi/dsigma_NL (grad_out_host may be NULL; synchronises). */
+int hm_state_sample_sigma_nl(hm_state* s, int32_t enable, const double* sigma0_host, void* stream);
+int hm_state_get_sigma_nl(hm_state* s, double* sigma_out_host, double* grad_out_host, void* stream);
+
 /* Step-size tuning (section "Integrating the HMC trajectories": the step
  * is tuned to a target acceptance, 0.65 in the paper, by dual averaging):
  * n_warmup HMC transitions of every chain starting from eps0_host[c], the

@@ -501,8 +501,16 @@ def in_domain(prob, d):
 # ----------------------------------------------------------------------------
 # Posterior: Psi = -ln Pi (eq. Psi) and its gradient.
 # ----------------------------------------------------------------------------
-def point_terms(prob, d, u, du):
-    """Per-point Psi_i, r_i = dPsi_i/du_i and dPsi_i/dd_i (u' = du given)."""
+def point_terms(prob, d, u, du, sigma_nl=None):
+    """Per-point Psi_i, r_i = dPsi_i/du_i and dPsi_i/dd_i (u' = du given);
+    sigma_nl overrides the problem's value (sampled sigma_NL)."""
+    psi_i, r, gd, _ = point_terms_s(prob, d, u, du, sigma_nl)
+    return psi_i, r, gd
+
+
+def point_terms_s(prob, d, u, du, sigma_nl=None):
+    """point_terms plus dPsi_i/dsigma_NL = (sigma/kappa^2)(1 - (v_obs-u)^2/kappa^2)."""
+    snl = prob.sigma_nl if sigma_nl is None else float(sigma_nl)
     om = prob.omega_m
     ok = in_domain(prob, d)
     dd = np.where(ok, d, 1.0)
@@ -510,7 +518,7 @@ def point_terms(prob, d, u, du):
     mup = distance_modulus_prime(dd, om)
     vo = v_observed(prob.z, dd, om)
     vop = v_observed_prime(prob.z, dd, om)
-    k2 = kappa2(dd, prob.sigma_nl, prob.sigma_cz, om)
+    k2 = kappa2(dd, snl, prob.sigma_cz, om)
     k2p = kappa2_prime(dd, prob.sigma_cz, om)
     lp, dlp = log_prior_d(prob, dd)
     res_mu = prob.mu - mu_d
@@ -520,10 +528,12 @@ def point_terms(prob, d, u, du):
     r = -res_v / k2
     gd = (-res_mu * mup / prob.sigma_mu ** 2 + res_v * (vop - du) / k2
           - res_v ** 2 * k2p / (2.0 * k2 * k2) + k2p / (2.0 * k2) - dlp)
+    gs = snl / k2 * (1.0 - res_v ** 2 / k2)
     psi_i = np.where(ok, psi_i, np.inf)
     r = np.where(ok & np.isfinite(psi_i), r, 0.0)
     gd = np.where(ok & np.isfinite(psi_i), gd, 0.0)
-    return psi_i, r, gd
+    gs = np.where(ok & np.isfinite(psi_i), gs, 0.0)
+    return psi_i, r, gd, gs
 
 
 def predicted_u(prob, v, d):
@@ -558,6 +568,46 @@ def logpost_grad(prob, w, d):
     s = np.stack([cic_scatter(prob, r * prob.rhat[:, j], cell, frac) for j in range(3)])
     gw = w + velocity_adjoint(prob, s)
     return psi, gw, gd
+
+
+def logpost_grad_s(prob, w, d, sigma_nl):
+    """Psi and its gradient with sigma_NL as a parameter of q (eq. q): flat
+    prior on sigma_NL > 0 (the paper gives none), Psi = +inf for sigma_NL <= 0.
+    Returns (psi, dPsi/dw, dPsi/dd, dPsi/dsigma_NL)."""
+    w = np.asarray(w, float)
+    d = np.asarray(d, float)
+    if not sigma_nl > 0:
+        return np.inf, np.zeros_like(w), np.zeros_like(d), 0.0
+    v = velocity_field(prob, w)
+    u, du, cell, frac = predicted_u(prob, v, d)
+    psi_i, r, gd, gs = point_terms_s(prob, d, u, du, sigma_nl)
+    psi = 0.5 * float(np.sum(w * w)) + float(np.sum(psi_i))
+    s = np.stack([cic_scatter(prob, r * prob.rhat[:, j], cell, frac) for j in range(3)])
+    gw = w + velocity_adjoint(prob, s)
+    return psi, gw, gd, float(np.sum(gs))
+
+
+def leapfrog_s(prob, w, d, s, pw, pd, ps, eps, n_steps):
+    """Kick-drift-kick leapfrog of (w, d, sigma_NL) with unit mass on
+    sigma_NL (eq. M_ab).  Returns (w, d, s, pw, pd, ps, psi)."""
+    w = np.array(w, float, copy=True)
+    d = np.array(d, float, copy=True)
+    pw = np.array(pw, float, copy=True)
+    pd = np.array(pd, float, copy=True)
+    psi, gw, gd, gs = logpost_grad_s(prob, w, d, s)
+    pw -= 0.5 * eps * gw
+    pd -= 0.5 * eps * gd
+    ps -= 0.5 * eps * gs
+    for l in range(n_steps):
+        w += eps * pw
+        d += eps * prob.minv_d * pd
+        s += eps * ps
+        psi, gw, gd, gs = logpost_grad_s(prob, w, d, s)
+        c = eps if l < n_steps - 1 else 0.5 * eps
+        pw -= c * gw
+        pd -= c * gd
+        ps -= c * gs
+    return w, d, s, pw, pd, ps, psi
 
 
 def data_gradient_w(prob, d, r):

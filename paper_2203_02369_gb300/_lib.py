@@ -79,6 +79,8 @@ SIGNATURES = [
     ("hm_leapfrog", ct.c_int, [_P, ct.c_int32, ct.c_double, ct.c_int32, _P]),
     ("hm_run_chain", ct.c_int, [_P, ct.c_int32, ct.c_int32, c_double_p, ct.c_int32, ct.c_int32,
                                 ct.POINTER(hm_trace), _P]),
+    ("hm_state_sample_sigma_nl", ct.c_int, [_P, ct.c_int32, c_double_p, _P]),
+    ("hm_state_get_sigma_nl", ct.c_int, [_P, c_double_p, c_double_p, _P]),
     ("hm_adapt_step_size", ct.c_int, [_P, ct.c_int32, ct.c_int32, ct.c_double, c_double_p, ct.c_int32,
                                       c_double_p, ct.POINTER(hm_trace), _P]),
     ("hm_state_profile", ct.c_int, [_P, ct.c_int32]),

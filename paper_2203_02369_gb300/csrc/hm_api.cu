@@ -292,7 +292,8 @@ struct hm_state {
   DevBuf rx, ry, rz, mu, smu, zobs, scz, d, pd, gd, d0, gd0;
   PtWork work;
   DevBuf prior_part, pts_part, kinb_f, kinb_p, kinl_f, kinl_p;
-  DevBuf pp, cs, chain_id, eps_dev, trace_dev;
+  DevBuf pp, cs, chain_id, eps_dev, trace_dev, gsig_part, sig_dev;
+  bool sample_sig = false;
   size_t trace_cap = 0;
   std::vector<PointParams> pp_host;
   std::vector<double> eps_host;
@@ -368,6 +369,8 @@ struct GradArgs {
   ChainScal* cs;
   const PtWork* work;
   Prof* prof;
+  double* gsig_part;   // [C][pts_blocks] dPsi/dsigma_NL partials (sampled sigma_NL)
+  bool sample_sig;
 };
 
 // The gradient evaluations of a leapfrog run (or one standalone evaluation)
@@ -417,7 +420,8 @@ static int eval_run(const GradArgs& a, int n, int last_mode, cudaStream_t st) {
     HM_PROF(pf, KK_C2R_GATHER, st, launch_plane_c2r_gather(a.prec, a.N, a.S2, a.nspec, pts, 3 * a.C, a.tw, st));
     HM_PROF(pf, KK_LIK, st,
             launch_points_lik(a.prec, a.C, a.max_pts, a.pp, pa, a.pts_part, a.pts_blocks, mode, a.kinl_p, a.cs,
-                              st));
+                              a.gsig_part, st));
+    if (a.sample_sig) HM_CUDA(launch_sig_update(a.C, a.gsig_part, a.pts_blocks, mode, a.cs, st));
     if (l < n) HM_TRY(place_points(a, par ^ 1, st));   // next evaluation's buckets, off the critical path
     // adjoint: residuals scattered plane by plane, forward transform, weights
     HM_PROF(pf, KK_R2C_SCATTER, st, launch_plane_r2c_scatter(a.prec, a.N, pts, a.S1, a.nspec, 3 * a.C, a.tw, st));
@@ -824,6 +828,8 @@ static GradArgs state_args(hm_state* s) {
   a.kinl_p = s->kinl_p.as<double>();
   a.cs = s->cs.as<ChainScal>();
   a.work = &s->work;
+  a.gsig_part = s->gsig_part.as<double>();
+  a.sample_sig = s->sample_sig;
   return a;
 }
 
@@ -934,6 +940,8 @@ int hm_state_create_batch(hm_problem* const* problems, int32_t n_problems, int32
   HM_CUDA(cudaMemset(s->kinl_p.p, 0, 8 * C * s->pts_blocks));
   HM_CUDA(cudaMemset(s->kinb_p.p, 0, 8 * C * s->nparts_p));
   HM_TRY(s->eps_dev.alloc(8 * C));
+  HM_TRY(s->sig_dev.alloc(8 * C));
+  HM_TRY(s->gsig_part.alloc(8 * C * s->pts_blocks));
   s->eps_host.assign(C, 0.0);
   HM_TRY(state_refresh(s.get(), nullptr));
   HM_CUDA(cudaDeviceSynchronize());
@@ -1049,6 +1057,7 @@ static int leapfrog_body(hm_state* s, int n_steps, int draw, cudaStream_t st, Pr
     HM_CUDA(launch_traj_begin_points(s->C, s->max_pts, a.pp, pa, s->d0.as<double>(), s->gd0.as<double>(), s->seed,
                                      s->chain_id.as<int>(), s->kinb_p.as<double>(), s->nparts_p, draw, a.cs, st));
   }
+  if (s->sample_sig) HM_CUDA(launch_sig_begin(s->C, s->seed, s->chain_id.as<int>(), draw, a.cs, st));
   HM_CUDA(launch_finalize(s->C, nullptr, 0, nullptr, 0, s->kinb_f.as<double>(), s->nparts_f,
                           s->kinb_p.as<double>(), s->max_pts > 0 ? s->nparts_p : 0, FIN_HOLD, s->seed,
                           s->chain_id.as<int>(), a.cs, nullptr, st));
@@ -1217,6 +1226,40 @@ int hm_adapt_step_size(hm_state* s, int32_t n_warmup, int32_t n_leapfrog, double
     HM_CUDA(cudaMemcpyAsync(trace_host, s->trace_dev.p, need, cudaMemcpyDeviceToHost, st));
   HM_CUDA(cudaStreamSynchronize(st));
   for (int c = 0; c < s->C; ++c) s->eps_host[c] = eps_out_host[c];
+  return HM_OK;
+}
+
+int hm_state_sample_sigma_nl(hm_state* s, int32_t enable, const double* sigma0_host, void* stream) {
+  if (!s) return fail(HM_EINVAL, "null state");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  HM_CUDA(cudaSetDevice(s->device));
+  std::vector<double> sig(s->C);
+  for (int c = 0; c < s->C; ++c) {
+    sig[c] = sigma0_host ? sigma0_host[c] : s->chain_prob[c]->desc.sigma_nl;
+    if (enable && !(sig[c] > 0) ) return fail(HM_EINVAL, "sigma_NL must start > 0");
+  }
+  HM_CUDA(cudaMemcpyAsync(s->sig_dev.p, sig.data(), 8 * s->C, cudaMemcpyHostToDevice, st));
+  HM_CUDA(launch_sig_set(s->C, enable ? 1 : 0, s->sig_dev.as<double>(), s->cs.as<ChainScal>(), st));
+  HM_CUDA(cudaStreamSynchronize(st));   // the host copy of sig must outlive the transfer
+  s->sample_sig = enable != 0;
+  if (s->gexec) {
+    cudaGraphExecDestroy(s->gexec);
+    s->gexec = nullptr;
+  }
+  return state_refresh(s, st);
+}
+
+int hm_state_get_sigma_nl(hm_state* s, double* sigma_out_host, double* grad_out_host, void* stream) {
+  if (!s || !sigma_out_host) return fail(HM_EINVAL, "null argument");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  HM_CUDA(cudaSetDevice(s->device));
+  std::vector<ChainScal> cs(s->C);
+  HM_CUDA(cudaMemcpyAsync(cs.data(), s->cs.p, sizeof(ChainScal) * s->C, cudaMemcpyDeviceToHost, st));
+  HM_CUDA(cudaStreamSynchronize(st));
+  for (int c = 0; c < s->C; ++c) {
+    sigma_out_host[c] = s->sample_sig ? cs[c].sig : s->chain_prob[c]->desc.sigma_nl;
+    if (grad_out_host) grad_out_host[c] = s->sample_sig ? cs[c].g_sig : 0.0;
+  }
   return HM_OK;
 }
 
@@ -1393,7 +1436,7 @@ extern "C" int hm_logpost_grad_noalloc(hm_problem* p, const void* w_dev, const d
   HM_CUDA(launch_plane_r2c(p->prec, p->N, w_dev, p->n3, S1, p->nspec, 1, p->tw.p, st));
   HM_CUDA(launch_pencil(p->prec, p->N, PM_VEL, S1, p->nspec, S2, p->nspec, 1, p->tw.p, p->amp.p, st));
   HM_CUDA(launch_plane_c2r_gather(p->prec, p->N, S2, p->nspec, pts, 3, p->tw.p, st));
-  HM_CUDA(launch_points_lik(p->prec, 1, maxp, pp, pa, pts_part, pb, GM_GRAD, kin_part, cs, st));
+  HM_CUDA(launch_points_lik(p->prec, 1, maxp, pp, pa, pts_part, pb, GM_GRAD, kin_part, cs, nullptr, st));
   HM_CUDA(launch_plane_r2c_scatter(p->prec, p->N, pts, S1, p->nspec, 3, p->tw.p, st));
   HM_CUDA(launch_pencil(p->prec, p->N, PM_ADJ, S1, p->nspec, S2, p->nspec, 1, p->tw.p, p->amp.p, st));
   FieldEpi epi{};

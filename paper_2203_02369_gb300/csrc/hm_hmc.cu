@@ -221,7 +221,7 @@ __global__ void k_finalize(const double* __restrict__ prior_part, int n_prior,
     S.psi_pts = b;
     S.psi = a + b;
   }
-  if (what & (FIN_HOLD | FIN_ACCEPT | FIN_KIN)) S.kin = S.sample_d ? k + kp : k;
+  if (what & (FIN_HOLD | FIN_ACCEPT | FIN_KIN)) S.kin = (S.sample_d ? k + kp : k) + (S.sample_sig ? S.kin_sig : 0.0);
   if (what & FIN_HOLD) {
     S.psi0 = S.psi;
     S.H_old = S.psi + S.kin;
@@ -247,7 +247,13 @@ __global__ void k_finalize(const double* __restrict__ prior_part, int n_prior,
       t.accept = acc;
       t.status = S.status;
     }
-    if (!acc) S.psi = S.psi0;
+    if (!acc) {
+      S.psi = S.psi0;
+      if (S.sample_sig) {
+        S.sig = S.sig0;
+        S.g_sig = S.g_sig0;
+      }
+    }
     S.traj += 1;
     if (S.da_on) {
       // dual averaging (Hoffman & Gelman) toward acceptance probability da_delta
@@ -306,6 +312,54 @@ __global__ void k_set_run(int n_chains, const double* __restrict__ eps, int samp
   cs[c].sample_d = sample_d;
   cs[c].traj_run0 = cs[c].traj;
   cs[c].status = 0;
+}
+
+// sigma_NL updates (one warp per chain; fixed-order reduction of the partials)
+__global__ void k_sig_update(const double* __restrict__ gsig_part, int nparts, int mode, ChainScal* __restrict__ cs) {
+  pdl_wait();
+  pdl_trigger();
+  const int c = blockIdx.x;
+  ChainScal& S = cs[c];
+  if (!S.sample_sig) return;
+  double g = 0.0;
+  for (int i = threadIdx.x; i < nparts; i += 32) g += gsig_part[(long long)c * nparts + i];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) g += __shfl_down_sync(0xffffffffu, g, o);
+  if (threadIdx.x != 0) return;
+  S.g_sig = g;
+  if (mode == GM_GRAD) return;
+  const double ck = (mode == GM_KICK_DRIFT) ? S.eps : 0.5 * S.eps;
+  S.p_sig -= ck * g;
+  if (mode == GM_KICK_DRIFT) S.sig += S.eps * S.p_sig;
+  if (mode == GM_KICK_LAST) S.kin_sig = 0.5 * S.p_sig * S.p_sig;
+}
+
+__global__ void k_sig_begin(unsigned long long seed, const int* __restrict__ chain_id, int draw,
+                            ChainScal* __restrict__ cs) {
+  pdl_wait();
+  pdl_trigger();
+  const int c = blockIdx.x;
+  ChainScal& S = cs[c];
+  if (threadIdx.x != 0 || !S.sample_sig) return;
+  double p = S.p_sig;
+  if (draw) {
+    double n1;
+    normal_pair(seed, 0u, (unsigned)S.traj, (unsigned)chain_id[c], 3u, p, n1);
+  }
+  S.kin_sig = 0.5 * p * p;
+  S.sig0 = S.sig;
+  S.g_sig0 = S.g_sig;
+  S.p_sig = p - 0.5 * S.eps * S.g_sig;
+  S.sig += S.eps * S.p_sig;
+}
+
+__global__ void k_sig_set(int n_chains, int enable, const double* __restrict__ sig, ChainScal* __restrict__ cs) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= n_chains) return;
+  cs[c].sample_sig = enable;
+  if (sig) cs[c].sig = sig[c];
+  cs[c].p_sig = 0.0;
+  cs[c].kin_sig = 0.0;
 }
 
 __global__ void k_da(int n_chains, int start, double delta, double* __restrict__ eps_out,
@@ -396,6 +450,21 @@ cudaError_t launch_restore(int prec, int n_chains, long long n3, void* w, void* 
     return launch_k(k_restore_points, dim3((unsigned)pb, n_chains), dim3(kEwNT), 0, st, pp, pa, d0, gd0, cs);
   }
   return cudaSuccess;
+}
+
+cudaError_t launch_sig_update(int n_chains, const double* gsig_part, int nparts, int mode, ChainScal* cs,
+                              cudaStream_t st) {
+  return launch_k(k_sig_update, dim3(n_chains), dim3(32), 0, st, gsig_part, nparts, mode, cs);
+}
+
+cudaError_t launch_sig_begin(int n_chains, unsigned long long seed, const int* chain_id, int draw, ChainScal* cs,
+                             cudaStream_t st) {
+  return launch_k(k_sig_begin, dim3(n_chains), dim3(32), 0, st, seed, chain_id, draw, cs);
+}
+
+cudaError_t launch_sig_set(int n_chains, int enable, const double* sig, ChainScal* cs, cudaStream_t st) {
+  k_sig_set<<<(n_chains + 127) / 128, 128, 0, st>>>(n_chains, enable, sig, cs);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_da(int n_chains, int start, double delta, double* eps_out, ChainScal* cs, cudaStream_t st) {

@@ -75,6 +75,9 @@ struct ChainScal {
   // dual-averaging step-size adaptation (active while da_on != 0)
   double da_Hbar, da_lepsbar, da_mu, da_delta;
   int da_on, da_m;
+  // sigma_NL as a sampled coordinate (eq. q), unit mass (eq. M_ab)
+  double sig, p_sig, g_sig, sig0, g_sig0, kin_sig;
+  int sample_sig, pad1;
 };
 
 enum : int { STATUS_DOMAIN = 1, STATUS_NONFINITE = 2 };
@@ -183,7 +186,7 @@ cudaError_t launch_points_place(int prec, int n_chains, int max_pts, const Point
 // the new distances into pa.cnt_next (GM_KICK_DRIFT).
 cudaError_t launch_points_lik(int prec, int n_chains, int max_pts, const PointParams* pp, PointArrays pa,
                               double* pts_part, int part_stride, int mode, double* kin_part, ChainScal* cs,
-                              cudaStream_t st);
+                              double* gsig_part, cudaStream_t st);
 int points_blocks(int max_pts);
 cudaError_t launch_cells(int n_chains, int max_pts, const PointParams* pp, const double* d,
                          PointArrays pa, int* cell_out, cudaStream_t st);
@@ -213,6 +216,13 @@ cudaError_t launch_restore(int prec, int n_chains, long long n3, void* w, void* 
                            const void* gw0, int max_pts, const PointParams* pp, PointArrays pa,
                            const double* d0, const double* gd0, const ChainScal* cs,
                            cudaStream_t st);
+// sigma_NL: reduce the per-block dPsi/dsigma partials, then (mode) kick and
+// drift it; begin: momentum draw (Philox tag 3), save, half kick and drift.
+cudaError_t launch_sig_update(int n_chains, const double* gsig_part, int nparts, int mode, ChainScal* cs,
+                              cudaStream_t st);
+cudaError_t launch_sig_begin(int n_chains, unsigned long long seed, const int* chain_id, int draw, ChainScal* cs,
+                             cudaStream_t st);
+cudaError_t launch_sig_set(int n_chains, int enable, const double* sig, ChainScal* cs, cudaStream_t st);
 // Dual averaging: start (mu = log(10 eps), target delta) / finish (eps = epsbar,
 // copied to eps_out[c]) on every chain.
 cudaError_t launch_da(int n_chains, int start, double delta, double* eps_out, ChainScal* cs, cudaStream_t st);

@@ -159,7 +159,7 @@ k_points_place(const PointParams* __restrict__ pp, PointArrays pa, ChainScal* __
   const double om = P.omega_m;
   const double x = 1.0 - 3.0 * om * kH0 * d / kC;
   double lp = 0.0, dlp = 0.0;
-  const bool ok = d > 0.0 && x > 0.0 && log_prior(P, d, lp, dlp);
+  const bool ok = d > 0.0 && x > 0.0 && log_prior(P, d, lp, dlp) && !(cs[c].sample_sig && !(cs[c].sig > 0.0));
   const long long nt = pa.ntot;
   if (!ok) {
     pa.lk[i] = __longlong_as_double(0x7ff0000000000000LL);  // +inf
@@ -181,7 +181,8 @@ k_points_place(const PointParams* __restrict__ pp, PointArrays pa, ChainScal* __
   const double z = pa.zobs[i];
   const double scz = pa.scz[i];
   const double scz2 = scz * scz;
-  const double k2 = P.sigma_nl2 + scz2 * iopz * iopz;
+  const double snl2 = cs[c].sample_sig ? cs[c].sig * cs[c].sig : P.sigma_nl2;
+  const double k2 = snl2 + scz2 * iopz * iopz;
   const double ik2 = 1.0 / k2;
   const double k2p = -2.0 * scz2 * zbp * iopz * iopz * iopz;
   const double smu = pa.smu[i];
@@ -203,14 +204,16 @@ k_points_place(const PointParams* __restrict__ pp, PointArrays pa, ChainScal* __
 template <typename T>
 __global__ void __launch_bounds__(kPtsNT)
 k_points_lik(const PointParams* __restrict__ pp, PointArrays pa, double* __restrict__ pts_part,
-             int part_stride, int mode, double* __restrict__ kin_part, ChainScal* __restrict__ cs) {
+             int part_stride, int mode, double* __restrict__ kin_part, ChainScal* __restrict__ cs,
+             double* __restrict__ gsig_part) {
   pdl_wait();
   pdl_trigger();
   __shared__ double red[kPtsNT / 32];
   const int c = blockIdx.y;
   const PointParams& P = pp[c];
   const long long il = (long long)blockIdx.x * kPtsNT + threadIdx.x;
-  double psi_i = 0.0, kin = 0.0;
+  double psi_i = 0.0, kin = 0.0, gsig = 0.0;
+  const bool ssig = cs[c].sample_sig != 0;
   if (il < P.pt_n) {
     const long long i = P.pt_off + il;
     const long long nt = pa.ntot;
@@ -235,6 +238,7 @@ k_points_lik(const PointParams* __restrict__ pp, PointArrays pa, double* __restr
       const double res_v = vo - u;
       psi_i = A + 0.5 * res_v * res_v * ik2;
       rec[pos].r = (T)(-res_v * ik2);
+      if (ssig) gsig = cs[c].sig * ik2 * (1.0 - res_v * res_v * ik2);
       gd = pa.lk[nt + i] + res_v * (vop - du) * ik2 - 0.5 * res_v * res_v * k2p * ik2 * ik2;
     }
     pa.gd[i] = gd;
@@ -266,6 +270,10 @@ k_points_lik(const PointParams* __restrict__ pp, PointArrays pa, double* __restr
   if (mode == GM_KICK_LAST) {
     const double k = block_sum(kin, red);
     if (threadIdx.x == 0) kin_part[(long long)c * part_stride + blockIdx.x] = k;
+  }
+  if (ssig) {
+    const double g = block_sum(gsig, red);
+    if (threadIdx.x == 0) gsig_part[(long long)c * part_stride + blockIdx.x] = g;
   }
 }
 
@@ -375,12 +383,12 @@ cudaError_t launch_points_place(int prec, int n_chains, int max_pts, const Point
 
 cudaError_t launch_points_lik(int prec, int n_chains, int max_pts, const PointParams* pp, PointArrays pa,
                               double* pts_part, int part_stride, int mode, double* kin_part, ChainScal* cs,
-                              cudaStream_t st) {
+                              double* gsig_part, cudaStream_t st) {
   if (prec == 0)
     return launch_k(k_points_lik<float>, pts_grid(n_chains, max_pts), dim3(kPtsNT), 0, st, pp, pa, pts_part,
-                    part_stride, mode, kin_part, cs);
+                    part_stride, mode, kin_part, cs, gsig_part);
   return launch_k(k_points_lik<double>, pts_grid(n_chains, max_pts), dim3(kPtsNT), 0, st, pp, pa, pts_part,
-                  part_stride, mode, kin_part, cs);
+                  part_stride, mode, kin_part, cs, gsig_part);
 }
 
 cudaError_t launch_cells(int n_chains, int max_pts, const PointParams* pp, const double* d,

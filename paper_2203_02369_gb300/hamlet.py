@@ -267,6 +267,19 @@ class State:
         check(self.lib.hm_state_profile_read(self.h, 64, ms, ln, ct.byref(nk)))
         return {self.lib.hm_kernel_kind_name(k).decode(): (ms[k], ln[k]) for k in range(nk.value)}
 
+    def sample_sigma_nl(self, enable=True, sigma0=None):
+        s0 = None if sigma0 is None else np.ascontiguousarray(
+            np.broadcast_to(np.asarray(sigma0, dtype=np.float64), (self.C,)))
+        check(self.lib.hm_state_sample_sigma_nl(self.h, int(bool(enable)), _dptr(s0) if s0 is not None else None,
+                                                _stream()))
+
+    def sigma_nl(self):
+        """(current sigma_NL per chain, dPsi/dsigma_NL per chain)."""
+        s = np.zeros(self.C)
+        g = np.zeros(self.C)
+        check(self.lib.hm_state_get_sigma_nl(self.h, _dptr(s), _dptr(g), _stream()))
+        return s, g
+
     def adapt_step_size(self, n_warmup, n_leapfrog, eps0, target=0.65, sample_distances=True):
         """Dual-averaging warm-up; returns (tuned eps per chain, trace)."""
         e0 = np.ascontiguousarray(np.broadcast_to(np.asarray(eps0, dtype=np.float64), (self.C,)))

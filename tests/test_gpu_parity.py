@@ -255,3 +255,29 @@ def test_dual_averaging_matches_oracle_recursion(H):
     # the tuned step is used by the following run
     tr2 = st.run_chain(3, 10, eps_out)
     assert np.allclose(tr2[:, 0]["eps"], eps_out[0])
+
+
+def test_sampled_sigma_nl_gradient_and_leapfrog_vs_oracle(H):
+    spec, cat, gp, op, st = _state_and_oracle(H, 16, 200.0, 500, "fp64", 71)
+    rng = np.random.default_rng(9)
+    w0 = 0.5 * rng.normal(size=(16, 16, 16))
+    pw0 = rng.normal(size=(16, 16, 16))
+    d0 = cat["d_init"]
+    pd0 = rng.normal(size=d0.size) / math.sqrt(op.minv_d)
+    st.set(0, w=torch.tensor(w0), d=torch.tensor(d0), pw=torch.tensor(pw0), pd=torch.tensor(pd0))
+    st.sample_sigma_nl(True, 180.0)
+    s, gs = st.sigma_nl()
+    psi, gw, gd, rgs = O.logpost_grad_s(op, w0, d0, 180.0)
+    assert s[0] == 180.0
+    assert abs(gs[0] - rgs) <= 1e-12 * max(1.0, abs(rgs))
+    st.leapfrog(8, 0.02)
+    g = st.get(0)
+    s1, _ = st.sigma_nl()
+    w1, d1, rs1, pw1, pd1, ps1, psi1 = O.leapfrog_s(op, w0, d0, 180.0, pw0, pd0, 0.0, 0.02, 8)
+    assert rel(g["w"].cpu().numpy(), w1) < 1e-12
+    assert rel(g["d"].cpu().numpy(), d1) < 1e-12
+    assert abs(s1[0] - rs1) <= 1e-11 * rs1
+    assert abs(st.scalars(0)["psi"] - psi1) <= 1e-12 * abs(psi1)
+    # a chain with sigma_NL sampled runs and moves it
+    tr = st.run_chain(5, 10, 0.02)
+    assert np.all(np.isfinite(tr[:, 0]["H_new"]))

@@ -485,3 +485,32 @@ def test_dz_prior_table_counts_and_normalisation():
     b = (dz / 5.0).astype(int)
     empty = [k for k in range(len(ld)) if k not in set(b)][0]
     assert abs(dens[b[0]] / dens[empty] - (np.sum(b == b[0]) + 0.5) / 0.5) < 1e-12
+
+
+# ------------------------------------------------------ sampled sigma_NL ----
+def test_sigma_nl_gradient_central_differences_and_consistency():
+    p, d = tiny_problem(N=8, L=80.0, n=40, sigma_cz=50.0)
+    rng = np.random.default_rng(17)
+    w = rng.normal(size=(8, 8, 8))
+    s = 180.0
+    psi, gw, gd, gs = O.logpost_grad_s(p, w, d, s)
+    h = 1e-3
+    fd = (O.logpost_grad_s(p, w, d, s + h)[0] - O.logpost_grad_s(p, w, d, s - h)[0]) / (2 * h)
+    assert abs(fd - gs) < 1e-6 * max(1.0, abs(gs))
+    # at the problem's own sigma_NL it is the ordinary posterior
+    p.sigma_nl = s
+    psi2, gw2, gd2 = O.logpost_grad(p, w, d)
+    assert psi == psi2 and np.array_equal(gw, gw2) and np.array_equal(gd, gd2)
+    assert np.isinf(O.logpost_grad_s(p, w, d, -1.0)[0])
+
+
+def test_leapfrog_with_sigma_is_reversible():
+    p, d = tiny_problem(N=8, L=80.0, n=30)
+    rng = np.random.default_rng(18)
+    w0 = 0.3 * rng.normal(size=(8, 8, 8))
+    pw0 = rng.normal(size=(8, 8, 8))
+    pd0 = rng.normal(size=p.n) / math.sqrt(p.minv_d)
+    s0, ps0 = 200.0, 0.7
+    w1, d1, s1, pw1, pd1, ps1, _ = O.leapfrog_s(p, w0, d, s0, pw0, pd0, ps0, 0.02, 6)
+    w2, d2, s2, *_ = O.leapfrog_s(p, w1, d1, s1, -pw1, -pd1, -ps1, 0.02, 6)
+    assert np.max(np.abs(w2 - w0)) < 1e-12 and abs(s2 - s0) < 1e-9
