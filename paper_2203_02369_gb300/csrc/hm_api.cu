@@ -943,8 +943,15 @@ int hm_state_create_batch(hm_problem* const* problems, int32_t n_problems, int32
   HM_TRY(s->sig_dev.alloc(8 * C));
   HM_TRY(s->gsig_part.alloc(8 * C * s->pts_blocks));
   s->eps_host.assign(C, 0.0);
-  HM_TRY(state_refresh(s.get(), nullptr));
-  HM_CUDA(cudaDeviceSynchronize());
+  // evaluate at the start on a private stream: a device-wide synchronisation
+  // would be illegal while another thread captures a trajectory graph
+  cudaStream_t init_st = nullptr;
+  HM_CUDA(cudaStreamCreateWithFlags(&init_st, cudaStreamNonBlocking));
+  int rc = state_refresh(s.get(), init_st);
+  cudaError_t se = cudaStreamSynchronize(init_st);
+  cudaStreamDestroy(init_st);
+  if (rc != HM_OK) return rc;
+  if (se != cudaSuccess) return fail(HM_ECUDA, std::string("state creation: ") + cudaGetErrorString(se));
   *out = s.release();
   return HM_OK;
 }
