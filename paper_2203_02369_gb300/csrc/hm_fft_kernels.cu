@@ -521,16 +521,13 @@ static cudaError_t pencil_t(const void* in, long long in_stride, void* out, long
 }
 
 // Supported grids: N in {8, 16, 32, 64, 128} at both precisions (one x-plane
-// of the half spectrum must fit in one CTA's shared memory).
+// of the half spectrum fits one CTA's shared memory), and N = 256 at FP32
+// (plane passes as 4-CTA clusters, hm_fft_cluster.cu).
 bool fft_supported(int prec, int N) {
-  (void)prec;
-  return N == 8 || N == 16 || N == 32 || N == 64 || N == 128;
+  return N == 8 || N == 16 || N == 32 || N == 64 || N == 128 || (N == 256 && prec == 0);
 }
 
-int plane_split(int N) {
-  (void)N;
-  return 1;
-}
+int plane_split(int N) { return N == 256 ? 4 : 1; }
 
 #define HM_DISPATCH_N(PREC, N, CALL_F, CALL_D)                          \
   do {                                                                  \
@@ -554,6 +551,23 @@ int plane_split(int N) {
     return cudaErrorInvalidValue;                                       \
   } while (0)
 
+#define HM_DISPATCH_PENCIL(PREC, N, CALL)                                       \
+  do {                                                                          \
+    if ((PREC) == 0 && (N) == 256) { using T = float; constexpr int NN = 256; return CALL; } \
+    HM_DISPATCH_N(PREC, N, CALL, CALL);                                         \
+  } while (0)
+
+template <typename T, int N>
+static cudaError_t prepare_pencil_t() {
+  cudaError_t e;
+  const cudaFuncAttribute A = cudaFuncAttributeMaxDynamicSharedMemorySize;
+  constexpr int s1 = (int)(sizeof(cplx<T>) * N * kTC), s3 = (int)(sizeof(cplx<T>) * N * 3 * kTC);
+  if ((e = cudaFuncSetAttribute(k_pencil<T, N, PM_FWD>, A, s1)) != cudaSuccess) return e;
+  if ((e = cudaFuncSetAttribute(k_pencil<T, N, PM_INV>, A, s1)) != cudaSuccess) return e;
+  if ((e = cudaFuncSetAttribute(k_pencil<T, N, PM_VEL>, A, s3)) != cudaSuccess) return e;
+  return cudaFuncSetAttribute(k_pencil<T, N, PM_ADJ>, A, s3);
+}
+
 template <typename T, int N>
 static cudaError_t prepare_t() {
   cudaError_t e;
@@ -572,11 +586,18 @@ static cudaError_t prepare_t() {
 }
 
 cudaError_t fft_prepare(int prec, int N) {
+  if (N == 256) {
+    if (prec != 0) return cudaErrorInvalidValue;
+    cudaError_t e = prepare_pencil_t<float, 256>();
+    return e != cudaSuccess ? e : plane_cl_prepare();
+  }
   HM_DISPATCH_N(prec, N, (prepare_t<T, NN>()), (prepare_t<T, NN>()));
 }
 
 cudaError_t launch_plane_r2c(int prec, int N, const void* in, long long in_stride, void* out,
                              long long out_stride, int count, const void* tw, cudaStream_t st) {
+  if (N == 256) return prec == 0 ? launch_plane_r2c_cl(in, in_stride, out, out_stride, count, tw, nullptr, st)
+                                 : cudaErrorInvalidValue;
   PlanePoints none{};
   HM_DISPATCH_N(prec, N, (plane_r2c_t<T, NN, false>(in, in_stride, out, out_stride, count, tw, none, st)),
                 (plane_r2c_t<T, NN, false>(in, in_stride, out, out_stride, count, tw, none, st)));
@@ -584,6 +605,8 @@ cudaError_t launch_plane_r2c(int prec, int N, const void* in, long long in_strid
 
 cudaError_t launch_plane_r2c_scatter(int prec, int N, const PlanePoints& pts, void* out, long long out_stride,
                                      int count, const void* tw, cudaStream_t st) {
+  if (N == 256) return prec == 0 ? launch_plane_r2c_cl(nullptr, 0, out, out_stride, count, tw, &pts, st)
+                                 : cudaErrorInvalidValue;
   HM_DISPATCH_N(prec, N, (plane_r2c_t<T, NN, true>(nullptr, 0, out, out_stride, count, tw, pts, st)),
                 (plane_r2c_t<T, NN, true>(nullptr, 0, out, out_stride, count, tw, pts, st)));
 }
@@ -591,6 +614,10 @@ cudaError_t launch_plane_r2c_scatter(int prec, int N, const PlanePoints& pts, vo
 cudaError_t launch_plane_c2r(int prec, int N, const void* in, long long in_stride, void* out,
                              long long out_stride, int count, const void* tw, const FieldEpi* epi,
                              cudaStream_t st, void* next_spec) {
+  if (N == 256)
+    return prec == 0 ? launch_plane_c2r_cl(epi ? C2R_EPI : C2R_STORE, in, in_stride, out, out_stride, count, tw, epi,
+                                           nullptr, next_spec, st)
+                     : cudaErrorInvalidValue;
   PlanePoints none{};
   if (epi) {
     HM_DISPATCH_N(prec, N, (plane_c2r_t<T, NN, C2R_EPI>(in, in_stride, out, out_stride, count, tw, epi, none, st, next_spec)),
@@ -602,6 +629,9 @@ cudaError_t launch_plane_c2r(int prec, int N, const void* in, long long in_strid
 
 cudaError_t launch_plane_c2r_gather(int prec, int N, const void* in, long long in_stride,
                                     const PlanePoints& pts, int count, const void* tw, cudaStream_t st) {
+  if (N == 256)
+    return prec == 0 ? launch_plane_c2r_cl(C2R_GATHER, in, in_stride, nullptr, 0, count, tw, nullptr, &pts, nullptr, st)
+                     : cudaErrorInvalidValue;
   HM_DISPATCH_N(prec, N, (plane_c2r_t<T, NN, C2R_GATHER>(in, in_stride, nullptr, 0, count, tw, nullptr, pts, st)),
                 (plane_c2r_t<T, NN, C2R_GATHER>(in, in_stride, nullptr, 0, count, tw, nullptr, pts, st)));
 }
@@ -622,8 +652,7 @@ static cudaError_t pencil_mode(int mode, const void* in, long long in_stride, vo
 cudaError_t launch_pencil(int prec, int N, int mode, const void* in, long long in_stride, void* out,
                           long long out_stride, int count, const void* tw, const void* amp,
                           cudaStream_t st) {
-  HM_DISPATCH_N(prec, N, (pencil_mode<T, NN>(mode, in, in_stride, out, out_stride, count, tw, amp, st)),
-                (pencil_mode<T, NN>(mode, in, in_stride, out, out_stride, count, tw, amp, st)));
+  HM_DISPATCH_PENCIL(prec, N, (pencil_mode<T, NN>(mode, in, in_stride, out, out_stride, count, tw, amp, st)));
 }
 
 }  // namespace hm

@@ -167,6 +167,15 @@ cudaError_t launch_pencil(int prec, int N, int mode, const void* in, long long i
                           long long out_stride, int count, const void* tw, const void* amp,
                           cudaStream_t st);
 bool fft_supported(int prec, int N);
+// N = 256 plane passes (thread-block clusters, FP32): pts == nullptr loads
+// real grids, else scatters the bucketed residuals; mode is C2R_STORE (0),
+// C2R_EPI (1) or C2R_GATHER (2).
+cudaError_t plane_cl_prepare();
+cudaError_t launch_plane_r2c_cl(const void* in, long long in_stride, void* out, long long out_stride, int count,
+                                const void* tw, const PlanePoints* pts, cudaStream_t st);
+cudaError_t launch_plane_c2r_cl(int mode, const void* in, long long in_stride, void* out, long long out_stride,
+                                int count, const void* tw, const FieldEpi* epi, const PlanePoints* pts,
+                                void* next, cudaStream_t st);
 // Raise the dynamic shared-memory limit of every FFT kernel for (prec, N) on
 // the current device; call once per device before any launch or capture.
 cudaError_t fft_prepare(int prec, int N);

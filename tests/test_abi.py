@@ -35,7 +35,9 @@ def test_supported_sizes():
         assert lib.hm_supported(N, 0) == 1
     for N in (8, 16, 32, 64, 128):
         assert lib.hm_supported(N, 1) == 1
+    assert lib.hm_supported(256, 0) == 1
     assert lib.hm_supported(256, 1) == 0
+    assert lib.hm_supported(512, 0) == 0
     assert lib.hm_supported(48, 0) == 0
 
 

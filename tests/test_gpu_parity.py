@@ -55,7 +55,8 @@ def make_case(H, N, L, n, precision, seed, mask=0.0, r_max=None, sigma_mu=(0.2, 
 
 # ------------------------------------------------------------------ FFT ----
 @pytest.mark.parametrize("N,prec", [(8, "fp32"), (16, "fp32"), (32, "fp32"), (64, "fp32"), (128, "fp32"),
-                                    (8, "fp64"), (16, "fp64"), (32, "fp64"), (64, "fp64"), (128, "fp64")])
+                                    (256, "fp32"), (8, "fp64"), (16, "fp64"), (32, "fp64"), (64, "fp64"),
+                                    (128, "fp64")])
 def test_fft_roundtrip_vs_numpy(H, N, prec):
     p = H.Problem(N, 100.0, precision=prec)
     rng = np.random.default_rng(N)
@@ -280,4 +281,25 @@ def test_sampled_sigma_nl_gradient_and_leapfrog_vs_oracle(H):
     assert abs(st.scalars(0)["psi"] - psi1) <= 1e-12 * abs(psi1)
     # a chain with sigma_NL sampled runs and moves it
     tr = st.run_chain(5, 10, 0.02)
+    assert np.all(np.isfinite(tr[:, 0]["H_new"]))
+
+
+def test_logpost_grad_256_cluster_planes(H):
+    """256^3 (box 1000 Mpc/h), 2e4 points: the 4-CTA cluster plane passes."""
+    spec = mock.MockSpec(N=256, L=1000.0, n_points=20000, r_max=300.0, mask_deg=10.0, sigma_mu=(0.2, 0.45),
+                         sigma_nl=250.0, seed=81)
+    cat = mock.make_catalog(spec)
+    gp = H.Problem.from_mock(spec, cat)
+    op = O.problem_from_catalog(spec.N, spec.L, mock.spec_dict(spec)["cosmo"], spec.sigma_nl, cat)
+    w = mock.white_field(256, 82).astype(np.float32).astype(np.float64)
+    d = cat["d_init"]
+    psi, gw, gd = gp.logpost_grad(torch.tensor(w, device="cuda"), torch.tensor(d, device="cuda"))
+    rpsi, rgw, rgd = O.logpost_grad(op, w, d)
+    assert abs(psi.item() - rpsi) / abs(rpsi) < 1e-5
+    assert rel(gw.cpu().numpy(), rgw) < 1e-5
+    assert rel(gd.cpu().numpy(), rgd) < 1e-5
+    v = gp.velocity_field(torch.tensor(w, device="cuda")).cpu().numpy()
+    assert rel(v, O.velocity_field(op, w)) < 1e-5
+    st = H.State(gp, [d], seed=3)
+    tr = st.run_chain(2, 5, 0.01, use_graph=True)
     assert np.all(np.isfinite(tr[:, 0]["H_new"]))
