@@ -53,6 +53,7 @@ def parse():
     ap.add_argument("--no-graph", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--batched-only", action="store_true", help="run only the 32-chain batched measurement")
+    ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--tune-eps", action="store_true", help="print acceptance for a sweep of eps and exit")
     return ap.parse_args()
 
@@ -315,6 +316,23 @@ def run_batched(args, eps, L, use_graph):
     return out
 
 
+def run_serving(eps, L):
+    """Poisson stream of reconstruction jobs (64^3 / 128^3 at 500 Mpc/h,
+    256^3 at 1000 Mpc/h; 1e3-1e5 points), all arriving within a fraction of
+    a second so that the GPU is saturated; served with 4 slots (continuous
+    batching) and, for reference, the same jobs one at a time."""
+    from paper_2203_02369_gb300.serve import ServingLoop, poisson_jobs
+    def jobs():
+        return poisson_jobs(12, rate_per_s=40.0, seed=7, n_traj=12, grids=(64, 128, 256), eps=eps)
+    served = ServingLoop(max_slots=4).run(jobs())
+    plain = ServingLoop(max_slots=1).run(jobs())
+    served["plain_one_at_a_time"] = {k: plain[k] for k in ("makespan_s", "grad_evals_per_s", "ess_per_s",
+                                                           "trajectory_latency_ms", "job_latency_s")}
+    served["speedup_vs_plain_evals"] = served["grad_evals_per_s"] / plain["grad_evals_per_s"]
+    served["workload"] = "12 jobs, Poisson arrivals at 40/s, grids 64/128/256, 1e3-1e5 points, 12 trajectories x 20 steps each"
+    return served
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -500,6 +518,10 @@ def main():
         if ess_info:
             batched["speedup_vs_plain_ess"] = batched["ess_per_s"] / ess_info["ess_per_s"]
 
+    serving = None
+    if not args.no_serve and ws == 1:
+        serving = run_serving(args.eps, L)
+
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": max_ms / args.steps, "higher_is_better": True,
@@ -512,7 +534,8 @@ def main():
                            "ms_per_step_unprofiled": ms_unprof},
                 "gpu_launches": int(sum(v[1] * KERNELS_PER_PAIR.get(k, 1) for k, v in prof.items())),
                 "clocks": clk, "roofline": roofline, "kernels": kernels, "ess": ess_info,
-                "e2e": e2e, "cpu_baseline": cpu, "batched": batched, "wall_s_timed": t_wall}
+                "e2e": e2e, "cpu_baseline": cpu, "batched": batched, "serving": serving,
+                "wall_s_timed": t_wall}
         print(json.dumps(line), flush=True)
     if ws > 1:
         dist.barrier()

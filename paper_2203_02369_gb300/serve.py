@@ -169,9 +169,10 @@ def summarize(jobs, makespan):
     }
 
 
-def poisson_jobs(n_jobs, rate_per_s, seed=7, n_traj=30, grids=(64, 128), n_range=(1e3, 1e5)):
+def poisson_jobs(n_jobs, rate_per_s, seed=7, n_traj=30, grids=(64, 128), n_range=(1e3, 1e5), eps=0.025):
     """Synthetic arrival stream: Poisson arrivals, grid 64^3 or 128^3 (box
-    500 Mpc/h), catalogue sizes log-uniform in n_range."""
+    500 Mpc/h) or 256^3 (box 1000 Mpc/h), catalogue sizes log-uniform in
+    n_range."""
     rng = np.random.default_rng(seed)
     t = 0.0
     jobs = []
@@ -179,7 +180,7 @@ def poisson_jobs(n_jobs, rate_per_s, seed=7, n_traj=30, grids=(64, 128), n_range
         t += rng.exponential(1.0 / rate_per_s)
         N = int(rng.choice(grids))
         n = int(round(np.exp(rng.uniform(np.log(n_range[0]), np.log(n_range[1])))))
-        spec = mock.MockSpec(N=N, L=500.0, n_points=n, r_max=160.0, mask_deg=10.0, sigma_mu=(0.2, 0.45),
-                             sigma_nl=250.0, seed=1000 + k)
-        jobs.append(Job(job_id=k, spec=spec, n_traj=n_traj, seed=seed, arrival=t))
+        spec = mock.MockSpec(N=N, L=1000.0 if N == 256 else 500.0, n_points=n, r_max=160.0, mask_deg=10.0,
+                             sigma_mu=(0.2, 0.45), sigma_nl=250.0, seed=1000 + k)
+        jobs.append(Job(job_id=k, spec=spec, n_traj=n_traj, seed=seed, arrival=t, eps=eps))
     return jobs
