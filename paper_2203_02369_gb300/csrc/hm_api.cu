@@ -21,7 +21,7 @@ namespace hm {
 bool pdl_enabled() {
   static const bool on = [] {
     const char* e = std::getenv("HM_PDL");
-    return !(e && e[0] == '0');
+    return e && e[0] == '1';
   }();
   return on;
 }

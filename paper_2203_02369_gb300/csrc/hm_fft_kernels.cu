@@ -14,23 +14,13 @@
 
 namespace hm {
 
-template <typename T> struct Vec16;
-template <> struct Vec16<float> { using type = float4; static constexpr int W = 4; };
-template <> struct Vec16<double> { using type = double2; static constexpr int W = 2; };
-
-template <typename T> __device__ __forceinline__ T vget(const typename Vec16<T>::type& v, int q);
-template <> __device__ __forceinline__ float vget<float>(const float4& v, int q) {
-  return q == 0 ? v.x : (q == 1 ? v.y : (q == 2 ? v.z : v.w));
-}
-template <> __device__ __forceinline__ double vget<double>(const double2& v, int q) {
-  return q == 0 ? v.x : v.y;
-}
-
 template <int N> struct PlaneCfg {
-  static constexpr int NH = N / 2 + 1;
-  static constexpr int ZP = 2 * NH;                // pitch of packed z rows (= 2 spectrum rows)
+  static constexpr int NH = N / 2 + 1;             // kz = 0..N/2 in the global half spectrum
+  static constexpr int NC = N / 2;                 // spectrum columns per row in shared memory (see below)
+  static constexpr int NR = N / 2;                 // packed z rows (two real rows each)
+  static constexpr int ZP = N + 1;                 // odd pitch of a packed z row
   static constexpr int NT = N >= 128 ? 512 : (N >= 64 ? 256 : 128);
-  static constexpr int SIZE = N * NH;              // complex elements of the plane buffer
+  static constexpr int SIZE = NR * ZP;             // complex elements of the plane buffer
   static constexpr int MINB = N >= 128 ? 2 : 1;    // CTAs per SM the register budget aims at
 };
 
@@ -38,136 +28,287 @@ template <typename T, int N> constexpr size_t plane_smem_bytes() {
   return sizeof(cplx<T>) * PlaneCfg<N>::SIZE;
 }
 
-// The plane buffer B holds N*(N/2+1) complex values and is read through two
-// views that share memory:
-//   spectrum view  H[y][k] = B[y*NH + k]            (y < N, k <= N/2)
-//   packed view    Z[r][z] = B[r*ZP + z], ZP = 2 NH (r < N/2, z < N), whose
-//                  real/imaginary parts are the real rows y = 2r and 2r+1.
-// Z row r and H rows 2r, 2r+1 occupy the same addresses, so the real <->
-// half-spectrum (un)packing runs in place, row pair by row pair.
+// The plane buffer B (N/2 rows of pitch ZP = N + 1) is read through two views
+// that share memory:
+//   packed view   Z[r][z] = B[r*ZP + z] (r < N/2, z < N): real and imaginary
+//                 parts are the real rows y = 2r and 2r + 1;
+//   spectrum view H[y][c] = B[hoff(y) + c] (y < N, c < N/2), hoff(y) =
+//                 (y/2) ZP + (y odd) N/2: rows 2r and 2r + 1 fill Z row r.
+// Column c = 0 of the spectrum view carries two real-symmetric lines at once:
+// kz = 0 in its real part and kz = N/2 in its imaginary part (both are real
+// after the z transform of real rows), so every y transform runs over N/2
+// columns and all thread counts divide the work without a ragged tail.  The
+// pitch ZP is odd, so a row-per-thread access (the z transform) hits
+// distinct shared-memory banks.
+template <int N> __device__ __forceinline__ int hoff(int y) {
+  return (y >> 1) * PlaneCfg<N>::ZP + (y & 1) * (N / 2);
+}
+
 template <typename T, int N>
 __device__ __forceinline__ T* zreal(cplx<T>* B, int y, int z) {
   return reinterpret_cast<T*>(&B[(y >> 1) * PlaneCfg<N>::ZP + z]) + (y & 1);
 }
 
-// Z rows (after the forward z FFT) -> H rows (half spectra of the real rows).
+// z transform of the N/2 packed rows in place, one row per thread in both
+// radix stages (conflict-free with the odd pitch).
+template <typename T, int N, bool INV>
+__device__ __forceinline__ void zfft(cplx<T>* B, const cplx<T>* __restrict__ tw) {
+  using P = PlaneCfg<N>;
+  fft_smem<T, N, INV, P::NR, P::NT, true>(B, P::ZP, 1, tw);
+}
+
+// Stage-1 radix-R1 group (offset m): DFT over j of a[j] = x[m + M j], then the
+// twiddles W_N^{m k2}; the result a[k2] belongs at m + M k2.
+template <typename T, int N, bool INV>
+__device__ __forceinline__ void stage1_group(cplx<T>* a, int m, const cplx<T>* __restrict__ tw) {
+  using C = cplx<T>;
+  constexpr int R1 = Radix<N>::R1, M = Radix<N>::M;
+  dft_reg<R1, INV>(a);
+  if constexpr (M > 1) {
+#pragma unroll
+    for (int k2 = 1; k2 < R1; ++k2) {
+      C wv = __ldg(&tw[m * k2]);
+      if (INV) wv.y = -wv.y;
+      a[k2] = cmul(a[k2], wv);
+    }
+  }
+}
+
+// Offset in the spectrum view of row y for a compile-time y relative to an
+// even base row.
+template <int N> __device__ __forceinline__ constexpr int yo(int y) {
+  return (y >> 1) * PlaneCfg<N>::ZP + (y & 1) * (N / 2);
+}
+
+// Z rows (after the forward z transform) -> spectrum view.  For a packed row
+// pair Z = X_a + i X_b (X_a, X_b the spectra of the real rows 2r, 2r+1):
+// X_a[k] = (Z[k] + conj Z[N-k]) / 2, X_b[k] = (Z[k] - conj Z[N-k]) / (2i);
+// column 0 receives (X[0], X[N/2]) of each row, both real.
 template <typename T, int N>
 __device__ __forceinline__ void unpack_rows(cplx<T>* B) {
   using C = cplx<T>;
   using P = PlaneCfg<N>;
-  constexpr int NH = P::NH, ZP = P::ZP, NT = P::NT;
-  constexpr int TOT = (N / 2) * NH;
+  constexpr int ZP = P::ZP, NT = P::NT, NC = P::NC;
+  constexpr int TOT = P::NR * NC;
   constexpr int PER = (TOT + NT - 1) / NT;
   C a[PER], b[PER];
 #pragma unroll
   for (int i = 0; i < PER; ++i) {
     const int e = threadIdx.x + i * NT;
-    if (e < TOT) {
-      const int r = e / NH, k = e % NH;
-      const C zk = B[r * ZP + k];
-      const C zm = cconj(B[r * ZP + ((N - k) & (N - 1))]);
-      const C sp = cadd(zk, zm), df = csub(zk, zm);
-      a[i] = C{(T)0.5 * sp.x, (T)0.5 * sp.y};
-      b[i] = C{(T)0.5 * df.y, (T)-0.5 * df.x};
+    if (TOT % NT == 0 || e < TOT) {
+      const int r = e / NC, k = e % NC;
+      const C* zr = B + r * ZP;
+      if (k == 0) {
+        const C z0 = zr[0], zn = zr[N / 2];
+        a[i] = C{z0.x, zn.x};
+        b[i] = C{z0.y, zn.y};
+      } else {
+        const C zk = zr[k], zm = cconj(zr[N - k]);
+        const C sp = cadd(zk, zm), df = csub(zk, zm);
+        a[i] = C{(T)0.5 * sp.x, (T)0.5 * sp.y};
+        b[i] = C{(T)0.5 * df.y, (T)-0.5 * df.x};
+      }
     }
   }
   __syncthreads();
 #pragma unroll
   for (int i = 0; i < PER; ++i) {
     const int e = threadIdx.x + i * NT;
-    if (e < TOT) {
-      const int r = e / NH, k = e % NH;
+    if (TOT % NT == 0 || e < TOT) {
+      const int r = e / NC, k = e % NC;
       B[r * ZP + k] = a[i];
-      B[r * ZP + NH + k] = b[i];
+      B[r * ZP + NC + k] = b[i];
     }
   }
   __syncthreads();
 }
 
-// H rows (inverse-transformed along y) -> Z rows ready for the inverse z FFT.
-// The imaginary parts at kz = 0 and N/2 are dropped (c2r semantics).
+// Spectrum view (inverse-transformed along y) -> Z rows for the inverse z
+// transform: Z[k] = X_a[k] + i X_b[k] with the Hermitian extension X[k] =
+// conj X[N-k] for k > N/2 and the real kz = 0, N/2 values from column 0.
 template <typename T, int N>
 __device__ __forceinline__ void pack_rows(cplx<T>* B) {
   using C = cplx<T>;
   using P = PlaneCfg<N>;
-  constexpr int NH = P::NH, ZP = P::ZP, NT = P::NT;
-  constexpr int TOT = (N / 2) * N;
+  constexpr int ZP = P::ZP, NT = P::NT, NC = P::NC;
+  constexpr int TOT = P::NR * N;
   constexpr int PER = (TOT + NT - 1) / NT;
   C o[PER];
 #pragma unroll
   for (int i = 0; i < PER; ++i) {
     const int e = threadIdx.x + i * NT;
-    if (e < TOT) {
+    if (TOT % NT == 0 || e < TOT) {
       const int r = e / N, k = e % N;
-      C a, b;
-      if (k <= N / 2) {
-        a = B[r * ZP + k];
-        b = B[r * ZP + NH + k];
-        if (k == 0 || k == N / 2) {
-          a.y = 0;
-          b.y = 0;
-        }
+      const C* zr = B + r * ZP;
+      if (k == 0 || k == N / 2) {
+        const C a = zr[0], b = zr[NC];
+        o[i] = (k == 0) ? C{a.x, b.x} : C{a.y, b.y};
       } else {
-        a = cconj(B[r * ZP + (N - k)]);
-        b = cconj(B[r * ZP + NH + (N - k)]);
+        C a, b;
+        if (k < N / 2) {
+          a = zr[k];
+          b = zr[NC + k];
+        } else {
+          a = cconj(zr[N - k]);
+          b = cconj(zr[NC + (N - k)]);
+        }
+        o[i] = C{a.x - b.y, a.y + b.x};
       }
-      o[i] = C{a.x - b.y, a.y + b.x};
     }
   }
   __syncthreads();
 #pragma unroll
   for (int i = 0; i < PER; ++i) {
     const int e = threadIdx.x + i * NT;
-    if (e < TOT) B[(e / N) * ZP + (e % N)] = o[i];
+    if (TOT % NT == 0 || e < TOT) B[(e / N) * ZP + (e % N)] = o[i];
   }
   __syncthreads();
 }
 
-// Real plane (rows y, contiguous z) <-> packed view.  Item (r, zp) covers
-// rows 2r, 2r+1 and columns z = 2zp, 2zp+1: two 2-wide global accesses per
-// row and one 16-byte (FP32) shared access, so consecutive threads touch
-// consecutive shared words (no bank conflicts).
+// Forward y transform of the spectrum view; the result goes to the global
+// half-spectrum plane dst[ky][kz] (pitch N/2 + 1).  Stage 2 stores columns
+// c >= 1 straight to global memory; the packed column 0 is transformed in
+// shared memory and split afterwards: with Y = DFT(a + i b) for real a, b,
+// DFT(a)[k] = (Y[k] + conj Y[-k]) / 2 and DFT(b)[k] = (Y[k] - conj Y[-k]) / (2i).
 template <typename T, int N>
-__device__ __forceinline__ void load_plane_packed(cplx<T>* B, const T* __restrict__ src) {
+__device__ __forceinline__ void yfft_fwd_store(cplx<T>* B, cplx<T>* __restrict__ dst,
+                                               const cplx<T>* __restrict__ tw) {
+  using C = cplx<T>;
   using P = PlaneCfg<N>;
-  constexpr int ITEMS = (N / 2) * (N / 2);
-  for (int e = threadIdx.x; e < ITEMS; e += P::NT) {
-    const int r = e / (N / 2), z = 2 * (e % (N / 2));
-    if constexpr (sizeof(T) == 4) {
-      const float2 a = __ldg(reinterpret_cast<const float2*>(src + (2 * r) * N + z));
-      const float2 b = __ldg(reinterpret_cast<const float2*>(src + (2 * r + 1) * N + z));
-      *reinterpret_cast<float4*>(&B[r * P::ZP + z]) = make_float4(a.x, b.x, a.y, b.y);
+  constexpr int R1 = Radix<N>::R1, M = Radix<N>::M;
+  constexpr int NT = P::NT, NC = P::NC, NH = P::NH, ZP = P::ZP;
+  constexpr int G1 = NC * M;
+  // ---- stage 1 (in place) ----
+#pragma unroll 1
+  for (int g = threadIdx.x; g < G1; g += NT) {
+    const int c = g % NC, m = (M == 1) ? 0 : g / NC;
+    C a[R1];
+    C* p = B + c + hoff<N>(m);
+#pragma unroll
+    for (int j = 0; j < R1; ++j) a[j] = p[(M == 1) ? yo<N>(j) : j * (M / 2) * ZP];
+    stage1_group<T, N, false>(a, m, tw);
+    if constexpr (M == 1) {      // natural order already: this is the output
+      if (c != 0) {
+#pragma unroll
+        for (int k = 0; k < R1; ++k) dst[k * NH + c] = a[k];
+      } else {
+#pragma unroll
+        for (int k = 0; k < R1; ++k) p[yo<N>(k)] = a[k];
+      }
     } else {
-      const double2 a = __ldg(reinterpret_cast<const double2*>(src + (2 * r) * N + z));
-      const double2 b = __ldg(reinterpret_cast<const double2*>(src + (2 * r + 1) * N + z));
-      B[r * P::ZP + z] = cplx<T>{a.x, b.x};
-      B[r * P::ZP + z + 1] = cplx<T>{a.y, b.y};
+#pragma unroll
+      for (int k2 = 0; k2 < R1; ++k2) p[k2 * (M / 2) * ZP] = a[k2];
     }
   }
-}
-
-// values of item (r, zp): v[0] = (2r, z), v[1] = (2r+1, z), v[2] = (2r, z+1), v[3] = (2r+1, z+1)
-template <typename T, int N>
-__device__ __forceinline__ void read_item(const cplx<T>* B, int r, int z, T* v) {
-  using P = PlaneCfg<N>;
-  if constexpr (sizeof(T) == 4) {
-    const float4 q = *reinterpret_cast<const float4*>(&B[r * P::ZP + z]);
-    v[0] = q.x;
-    v[1] = q.y;
-    v[2] = q.z;
-    v[3] = q.w;
-  } else {
-    const cplx<T> a = B[r * P::ZP + z], b = B[r * P::ZP + z + 1];
-    v[0] = a.x;
-    v[1] = a.y;
-    v[2] = b.x;
-    v[3] = b.y;
+  __syncthreads();
+  if constexpr (M > 1) {
+    // ---- stage 2 (load all groups, barrier, store in natural order) ----
+    constexpr int G2 = NC * R1;
+    constexpr int PER = (G2 + NT - 1) / NT;
+    C a[PER][M];
+#pragma unroll
+    for (int i = 0; i < PER; ++i) {
+      const int g = threadIdx.x + i * NT;
+      if (G2 % NT == 0 || g < G2) {
+        const int c = g % NC, k2 = g / NC;
+        const C* q = B + c + (M * k2 / 2) * ZP;
+#pragma unroll
+        for (int m = 0; m < M; ++m) a[i][m] = q[yo<N>(m)];
+        dft_reg<M, false>(a[i]);
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < PER; ++i) {
+      const int g = threadIdx.x + i * NT;
+      if (G2 % NT == 0 || g < G2) {
+        const int c = g % NC, k2 = g / NC;
+        if (c != 0) {
+#pragma unroll
+          for (int k1 = 0; k1 < M; ++k1) dst[(k2 + R1 * k1) * NH + c] = a[i][k1];
+        } else {
+          C* q = B + hoff<N>(k2);
+#pragma unroll
+          for (int k1 = 0; k1 < M; ++k1) q[k1 * (R1 / 2) * ZP] = a[i][k1];
+        }
+      }
+    }
+  }
+  __syncthreads();
+  for (int k = threadIdx.x; k < N; k += NT) {
+    const C y = B[hoff<N>(k)], ym = cconj(B[hoff<N>((N - k) & (N - 1))]);
+    const C sp = cadd(y, ym), df = csub(y, ym);
+    dst[k * NH] = C{(T)0.5 * sp.x, (T)0.5 * sp.y};
+    dst[k * NH + N / 2] = C{(T)0.5 * df.y, (T)-0.5 * df.x};
   }
 }
 
-template <typename T> struct Pair2;
-template <> struct Pair2<float> { using type = float2; };
-template <> struct Pair2<double> { using type = double2; };
+// Inverse y transform of the global half-spectrum plane src[ky][kz] into the
+// spectrum view.  Stage 1 reads global memory directly.  Column 0 packs the
+// kz = 0 and kz = N/2 lines as P0 + i PN, where P0 and PN are their Hermitian
+// parts along y: the inverse transform of P0 is the real part of the inverse
+// transform of the kz = 0 line, which is what a c2r transform keeps.
+template <typename T, int N>
+__device__ __forceinline__ void yfft_inv_load(cplx<T>* B, const cplx<T>* __restrict__ src,
+                                              const cplx<T>* __restrict__ tw) {
+  using C = cplx<T>;
+  using P = PlaneCfg<N>;
+  constexpr int R1 = Radix<N>::R1, M = Radix<N>::M;
+  constexpr int NT = P::NT, NC = P::NC, NH = P::NH, ZP = P::ZP;
+  constexpr int G1 = NC * M;
+#pragma unroll 1
+  for (int g = threadIdx.x; g < G1; g += NT) {
+    const int c = g % NC, m = (M == 1) ? 0 : g / NC;
+    C a[R1];
+    if (c != 0) {
+#pragma unroll
+      for (int j = 0; j < R1; ++j) a[j] = __ldg(&src[(m + M * j) * NH + c]);
+    } else {
+#pragma unroll
+      for (int j = 0; j < R1; ++j) {
+        const int y = m + M * j, ym = (N - y) & (N - 1);
+        const C h0 = __ldg(&src[y * NH]), h0m = __ldg(&src[ym * NH]);
+        const C hn = __ldg(&src[y * NH + N / 2]), hnm = __ldg(&src[ym * NH + N / 2]);
+        const C p0 = C{(T)0.5 * (h0.x + h0m.x), (T)0.5 * (h0.y - h0m.y)};
+        const C pn = C{(T)0.5 * (hn.x + hnm.x), (T)0.5 * (hn.y - hnm.y)};
+        a[j] = C{p0.x - pn.y, p0.y + pn.x};
+      }
+    }
+    stage1_group<T, N, true>(a, m, tw);
+    C* p = B + c + hoff<N>(m);
+#pragma unroll
+    for (int k2 = 0; k2 < R1; ++k2) p[(M == 1) ? yo<N>(k2) : k2 * (M / 2) * ZP] = a[k2];
+  }
+  __syncthreads();
+  if constexpr (M > 1) {
+    constexpr int G2 = NC * R1;
+    constexpr int PER = (G2 + NT - 1) / NT;
+    C a[PER][M];
+#pragma unroll
+    for (int i = 0; i < PER; ++i) {
+      const int g = threadIdx.x + i * NT;
+      if (G2 % NT == 0 || g < G2) {
+        const int c = g % NC, k2 = g / NC;
+        const C* q = B + c + (M * k2 / 2) * ZP;
+#pragma unroll
+        for (int m = 0; m < M; ++m) a[i][m] = q[yo<N>(m)];
+        dft_reg<M, true>(a[i]);
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < PER; ++i) {
+      const int g = threadIdx.x + i * NT;
+      if (G2 % NT == 0 || g < G2) {
+        const int c = g % NC, k2 = g / NC;
+        C* q = B + c + hoff<N>(k2);
+#pragma unroll
+        for (int k1 = 0; k1 < M; ++k1) q[k1 * (R1 / 2) * ZP] = a[i][k1];
+      }
+    }
+    __syncthreads();
+  }
+}
 
 // Bucket ranges of the plane's two point sets: side 0 has its lower CIC
 // corner on this plane (bucket ix), side 1 its upper corner (bucket ix-1).
@@ -210,7 +351,11 @@ k_plane_r2c(const T* __restrict__ in, long long in_stride, cplx<T>* __restrict__
   const int ix = blockIdx.x;
   const int s = blockIdx.y;
   if constexpr (!SCATTER) {
-    load_plane_packed<T, N>(B, in + (long long)s * in_stride + (long long)ix * N * N);
+    const T* src = in + (long long)s * in_stride + (long long)ix * N * N;
+    for (int e = threadIdx.x; e < P::NR * N; e += NT) {
+      const int r = e / N, z = e % N;
+      B[r * ZP + z] = C{__ldg(&src[(2 * r) * N + z]), __ldg(&src[(2 * r + 1) * N + z])};
+    }
   } else {
     for (int e = threadIdx.x; e < P::SIZE; e += NT) B[e] = C{(T)0, (T)0};
     __syncthreads();
@@ -232,17 +377,9 @@ k_plane_r2c(const T* __restrict__ in, long long in_stride, cplx<T>* __restrict__
     }
   }
   __syncthreads();
-  fft_smem<T, N, false, N / 2, NT, false>(B, ZP, 1, tw);
+  zfft<T, N, false>(B, tw);
   unpack_rows<T, N>(B);
-  fft_smem<T, N, false, P::NH, NT, true>(B, 1, P::NH, tw);
-  C* dst = out + (long long)s * out_stride + (long long)ix * P::SIZE;
-  if constexpr (sizeof(T) == 4) {
-    float4* d4 = reinterpret_cast<float4*>(dst);
-    const float4* s4 = reinterpret_cast<const float4*>(B);
-    for (int e = threadIdx.x; e < P::SIZE / 2; e += NT) d4[e] = s4[e];
-  } else {
-    for (int e = threadIdx.x; e < P::SIZE; e += NT) dst[e] = B[e];
-  }
+  yfft_fwd_store<T, N>(B, out + (long long)s * out_stride + (long long)ix * N * P::NH, tw);
 }
 
 // ---------------------------------------------------------------------------
@@ -267,28 +404,17 @@ k_plane_c2r(const cplx<T>* __restrict__ in, long long in_stride, T* __restrict__
   __shared__ double red[2][NT / 32];
   const int ix = blockIdx.x;
   const int s = blockIdx.y;
-  const C* src = in + (long long)s * in_stride + (long long)ix * P::SIZE;
-  if constexpr (sizeof(T) == 4) {
-    const float4* s4 = reinterpret_cast<const float4*>(src);
-    float4* b4 = reinterpret_cast<float4*>(B);
-    for (int e = threadIdx.x; e < P::SIZE / 2; e += NT) b4[e] = __ldg(&s4[e]);
-  } else {
-    for (int e = threadIdx.x; e < P::SIZE; e += NT) B[e] = src[e];
-  }
-  __syncthreads();
-  fft_smem<T, N, true, P::NH, NT, true>(B, 1, P::NH, tw);
+  yfft_inv_load<T, N>(B, in + (long long)s * in_stride + (long long)ix * N * P::NH, tw);
   pack_rows<T, N>(B);
-  fft_smem<T, N, true, N / 2, NT, false>(B, ZP, 1, tw);
-  using V2 = typename Pair2<T>::type;
-  constexpr int ITEMS = (N / 2) * (N / 2);
+  zfft<T, N, true>(B, tw);
+  constexpr int ITEMS = P::NR * N;   // item (r, z): real rows 2r, 2r+1 at column z
   if constexpr (MODE == C2R_STORE) {
     T* dst = out + (long long)s * out_stride + (long long)ix * N * N;
     for (int e = threadIdx.x; e < ITEMS; e += NT) {
-      const int r = e / (N / 2), z = 2 * (e % (N / 2));
-      T v[4];
-      read_item<T, N>(B, r, z, v);
-      *reinterpret_cast<V2*>(dst + (2 * r) * N + z) = V2{v[0], v[2]};
-      *reinterpret_cast<V2*>(dst + (2 * r + 1) * N + z) = V2{v[1], v[3]};
+      const int r = e / N, z = e % N;
+      const C v = B[r * ZP + z];
+      dst[(2 * r) * N + z] = v.x;
+      dst[(2 * r + 1) * N + z] = v.y;
     }
   } else if constexpr (MODE == C2R_GATHER) {
     const int c = s / 3, j = s % 3;
@@ -320,47 +446,58 @@ k_plane_c2r(const cplx<T>* __restrict__ in, long long in_stride, T* __restrict__
   } else {
     // ---- gradient / leapfrog epilogue (one chain per blockIdx.y) ----
     const long long base = (long long)s * epi.grid_stride + (long long)ix * N * N;
-    T* w = reinterpret_cast<T*>(epi.w) + base;
-    T* pw = reinterpret_cast<T*>(epi.pw) + base;
-    T* gw = reinterpret_cast<T*>(epi.gw) + base;
+    T* __restrict__ w = reinterpret_cast<T*>(epi.w) + base;
+    T* __restrict__ pw = reinterpret_cast<T*>(epi.pw) + base;
+    T* __restrict__ gw = reinterpret_cast<T*>(epi.gw) + base;
     const int mode = epi.mode;
     const T eps = (T)epi.cs[s].eps;
     const T ck = (mode == GM_KICK_DRIFT) ? eps : (T)0.5 * eps;
+    const bool fuse_next = next != nullptr && mode == GM_KICK_DRIFT;
+    const bool kick = mode != GM_GRAD;
     HalfSqAcc<T> aw, ap;
-    for (int e = threadIdx.x; e < ITEMS; e += NT) {
-      const int r = e / (N / 2), z = 2 * (e % (N / 2));
-      T g[4];
-      read_item<T, N>(B, r, z, g);
+    // U items per thread per round: all their global loads are issued before
+    // any store, so their latencies overlap
+    constexpr int U = ITEMS >= 4 * NT ? 4 : 1;
+    constexpr bool FULL = ITEMS % (U * NT) == 0;
+#pragma unroll 1
+    for (int e0 = threadIdx.x; e0 < ITEMS; e0 += U * NT) {
+      T wv[U][2], pv[U][2];
 #pragma unroll
-      for (int h = 0; h < 2; ++h) {   // row 2r + h, columns z, z + 1
-        const long long o = (long long)(2 * r + h) * N + z;
-        const V2 wq = *reinterpret_cast<const V2*>(w + o);
-        const T w0 = wq.x, w1 = wq.y;
-        const T g0 = w0 + g[h], g1 = w1 + g[2 + h];
-        aw.add_half_sq(w0);
-        aw.add_half_sq(w1);
-        if (mode == GM_GRAD || mode == GM_KICK_LAST) *reinterpret_cast<V2*>(gw + o) = V2{g0, g1};
-        if (mode != GM_GRAD) {
-          const V2 pq = *reinterpret_cast<const V2*>(pw + o);
-          const T p0 = pq.x - ck * g0, p1 = pq.y - ck * g1;
-          *reinterpret_cast<V2*>(pw + o) = V2{p0, p1};
-          ap.add_half_sq(p0);
-          ap.add_half_sq(p1);
-          if (mode == GM_KICK_DRIFT) {
-            const T n0 = w0 + eps * p0, n1 = w1 + eps * p1;
-            *reinterpret_cast<V2*>(w + o) = V2{n0, n1};
-            g[h] = n0;        // the drifted field replaces g in the plane buffer
-            g[2 + h] = n1;
-          }
+      for (int u = 0; u < U; ++u) {
+        const int e = e0 + u * NT, r = e / N, z = e % N;
+        if (!FULL && e >= ITEMS) continue;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int o = (2 * r + h) * N + z;
+          wv[u][h] = w[o];
+          pv[u][h] = kick ? pw[o] : (T)0;
         }
       }
-      if (next != nullptr && mode == GM_KICK_DRIFT) {
-        if constexpr (sizeof(T) == 4) {
-          *reinterpret_cast<float4*>(&B[r * ZP + z]) = make_float4(g[0], g[1], g[2], g[3]);
-        } else {
-          B[r * ZP + z] = cplx<T>{g[0], g[1]};
-          B[r * ZP + z + 1] = cplx<T>{g[2], g[3]};
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int e = e0 + u * NT, r = e / N, z = e % N;
+        if (!FULL && e >= ITEMS) continue;
+        const C g2 = B[r * ZP + z];
+        T nv[2];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {   // row 2r + h, column z
+          const int o = (2 * r + h) * N + z;
+          const T w0 = wv[u][h];
+          const T g0 = w0 + (h == 0 ? g2.x : g2.y);
+          aw.add_half_sq(w0);
+          nv[h] = w0;
+          if (mode == GM_GRAD || mode == GM_KICK_LAST) gw[o] = g0;
+          if (kick) {
+            const T p0 = pv[u][h] - ck * g0;
+            pw[o] = p0;
+            ap.add_half_sq(p0);
+            if (mode == GM_KICK_DRIFT) {
+              nv[h] = w0 + eps * p0;
+              w[o] = nv[h];
+            }
+          }
         }
+        if (fuse_next) B[r * ZP + z] = C{nv[0], nv[1]};   // the drifted field replaces g in the buffer
       }
     }
     double acc_w = aw.value(), acc_p = ap.value();
@@ -385,20 +522,11 @@ k_plane_c2r(const cplx<T>* __restrict__ in, long long in_stride, T* __restrict__
       epi.prior_part[(long long)s * N + ix] = a;
       if (mode == GM_KICK_LAST) epi.kin_part[(long long)s * N + ix] = b;
     }
-    if (next != nullptr && mode == GM_KICK_DRIFT) {
+    if (fuse_next) {
       // forward plane transform of the drifted field for the next evaluation
-      __syncthreads();
-      fft_smem<T, N, false, N / 2, NT, false>(B, ZP, 1, tw);
+      zfft<T, N, false>(B, tw);
       unpack_rows<T, N>(B);
-      fft_smem<T, N, false, P::NH, NT, true>(B, 1, P::NH, tw);
-      C* dst = next + (long long)s * next_stride + (long long)ix * P::SIZE;
-      if constexpr (sizeof(T) == 4) {
-        float4* d4 = reinterpret_cast<float4*>(dst);
-        const float4* s4 = reinterpret_cast<const float4*>(B);
-        for (int e = threadIdx.x; e < P::SIZE / 2; e += NT) d4[e] = s4[e];
-      } else {
-        for (int e = threadIdx.x; e < P::SIZE; e += NT) dst[e] = B[e];
-      }
+      yfft_fwd_store<T, N>(B, next + (long long)s * next_stride + (long long)ix * N * P::NH, tw);
     }
   }
 }
@@ -407,79 +535,195 @@ k_plane_c2r(const cplx<T>* __restrict__ in, long long in_stride, T* __restrict__
 // Pencil pass along x with the fused k-space operator.
 // amp[n2] = (2 pi/L) aHf sqrt(P(k)/Delta^3) / (k^2 N^3), amp[0] = 0, so that
 // the velocity spectrum of axis j is i n_j^odd amp[n^2] w_k.
+//
+// A CTA owns a tile of kTC contiguous (ky, kz) columns over all N x rows and
+// keeps one [N][kTC] buffer per component in shared memory.  The first radix
+// stage of a transform reads global memory directly, the last radix stage
+// of the final inverse writes global memory directly, and the k-space
+// weights are applied while the inverse transform's first stage loads its
+// operands, so only the middle of each transform passes through shared
+// memory.
 // ---------------------------------------------------------------------------
 constexpr int kTC = 16;       // (ky, kz) columns per tile
-constexpr int kPencilNT = 256;
+constexpr int kPencilNT = 128;
+
+template <typename T> struct PencilMinB { static constexpr int v = sizeof(T) == 4 ? 4 : 2; };
+
+// Stage 1 of the x transform for group (t, m), operands read from global
+// memory (zero for a column past the end), result to the component buffer.
+template <typename T, int N, bool INV, int W>
+__device__ __forceinline__ void px_s1_global(cplx<T>* buf, const cplx<T>* __restrict__ src, long long col,
+                                             bool ok, int t, int m, const cplx<T>* __restrict__ tw) {
+  using C = cplx<T>;
+  constexpr int R1 = Radix<N>::R1, M = Radix<N>::M, NCOL = N * (N / 2 + 1);
+  C a[R1];
+#pragma unroll
+  for (int j = 0; j < R1; ++j) a[j] = ok ? __ldg(&src[(long long)(m + M * j) * NCOL + col]) : C{(T)0, (T)0};
+  stage1_group<T, N, INV>(a, m, tw);
+#pragma unroll
+  for (int k2 = 0; k2 < R1; ++k2) buf[(m + M * k2) * W + t] = a[k2];
+}
+
+// Stage 2 of the x transform of one component, in place in shared memory
+// (natural order out).  Contains block barriers.
+template <typename T, int N, bool INV, int W>
+__device__ __forceinline__ void px_s2_smem(cplx<T>* buf) {
+  using C = cplx<T>;
+  constexpr int R1 = Radix<N>::R1, M = Radix<N>::M;
+  if constexpr (M > 1) {
+    constexpr int G2 = kTC * R1;
+    constexpr int PER = (G2 + kPencilNT - 1) / kPencilNT;
+    C a[PER][M];
+#pragma unroll
+    for (int i = 0; i < PER; ++i) {
+      const int g = threadIdx.x + i * kPencilNT;
+      if (G2 % kPencilNT == 0 || g < G2) {
+        const int t = g % kTC, k2 = g / kTC;
+#pragma unroll
+        for (int m = 0; m < M; ++m) a[i][m] = buf[(M * k2 + m) * W + t];
+        dft_reg<M, INV>(a[i]);
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < PER; ++i) {
+      const int g = threadIdx.x + i * kPencilNT;
+      if (G2 % kPencilNT == 0 || g < G2) {
+        const int t = g % kTC, k2 = g / kTC;
+#pragma unroll
+        for (int k1 = 0; k1 < M; ++k1) buf[(k2 + R1 * k1) * W + t] = a[i][k1];
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// Stage 2 of the x transform of one component, results straight to global
+// memory in natural order (a plain copy when N = R1).
+template <typename T, int N, bool INV, int W>
+__device__ __forceinline__ void px_s2_global(const cplx<T>* buf, cplx<T>* __restrict__ dst, int c0) {
+  using C = cplx<T>;
+  constexpr int R1 = Radix<N>::R1, M = Radix<N>::M, NCOL = N * (N / 2 + 1);
+#pragma unroll 1
+  for (int g = threadIdx.x; g < kTC * R1; g += kPencilNT) {
+    const int t = g % kTC, k2 = g / kTC;
+    C a[M];
+#pragma unroll
+    for (int m = 0; m < M; ++m) a[m] = buf[(M * k2 + m) * W + t];
+    dft_reg<M, INV>(a);
+    const long long col = c0 + t;
+    if (col < NCOL) {
+#pragma unroll
+      for (int k1 = 0; k1 < M; ++k1) dst[(long long)(k2 + R1 * k1) * NCOL + col] = a[k1];
+    }
+  }
+}
+
+// k-space geometry of column col of the tile: ny, nz (signed mode numbers)
+// and the odd factors of the y and z axes (0 on their Nyquist planes).
+template <int N> struct ColGeom {
+  int ny2nz2;
+  float oy, oz;
+};
+template <int N> __device__ __forceinline__ ColGeom<N> col_geom(long long col) {
+  constexpr int NH = N / 2 + 1;
+  const int ky = (int)(col / NH), kz = (int)(col % NH);
+  const int ny = ky < N / 2 ? ky : ky - N;
+  ColGeom<N> g;
+  g.ny2nz2 = ny * ny + kz * kz;
+  g.oy = (ky == N / 2) ? 0.f : (float)ny;
+  g.oz = (kz == N / 2) ? 0.f : (float)kz;
+  return g;
+}
 
 template <typename T, int N, int MODE>
-__global__ void __launch_bounds__(kPencilNT)
+__global__ void __launch_bounds__(kPencilNT, PencilMinB<T>::v)
 k_pencil(const cplx<T>* __restrict__ in, long long in_stride, cplx<T>* __restrict__ out,
          long long out_stride, const cplx<T>* __restrict__ tw, const T* __restrict__ amp) {
   pdl_wait();
   pdl_trigger();
   using C = cplx<T>;
-  constexpr int NH = N / 2 + 1;
-  constexpr int NCOL = N * NH;
+  constexpr int R1 = Radix<N>::R1, M = Radix<N>::M;
+  constexpr int NCOL = N * (N / 2 + 1);
   constexpr int NCOMP = (MODE == PM_VEL || MODE == PM_ADJ) ? 3 : 1;
   constexpr int W = NCOMP * kTC;   // smem row width: NCOMP tiles side by side
+  constexpr int NIN = (MODE == PM_ADJ) ? 3 : 1;
+  constexpr bool INV1 = (MODE == PM_INV);
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* buf = reinterpret_cast<C*>(smem_raw);   // [N][W]
   const int c0 = blockIdx.x * kTC;
   const int s = blockIdx.y;
-  const int tid = threadIdx.x;
-  constexpr int NIN = (MODE == PM_ADJ) ? 3 : 1;
-  // load input component(s)
-  for (int e = tid; e < NIN * N * kTC; e += kPencilNT) {
-    const int t = e % kTC;
-    const int x = (e / kTC) % N;
-    const int j = e / (kTC * N);
-    const int col = c0 + t;
-    C v = C{(T)0, (T)0};
-    if (col < NCOL) v = in[(long long)(s * NIN + j) * in_stride + (long long)x * NCOL + col];
-    buf[x * W + j * kTC + t] = v;
+  // first transform (forward; inverse for PM_INV), stage 1 from global memory
+#pragma unroll 1
+  for (int g = threadIdx.x; g < NIN * kTC * M; g += kPencilNT) {
+    const int t = g % kTC, m = (g / kTC) % M, j = g / (kTC * M);
+    const long long col = c0 + t;
+    px_s1_global<T, N, INV1, W>(buf + j * kTC, in + (long long)(s * NIN + j) * in_stride, col, col < NCOL, t, m,
+                                tw);
   }
   __syncthreads();
-  if constexpr (MODE == PM_INV) {
-    fft_smem<T, N, true, kTC, kPencilNT, true>(buf, 1, W, tw);
+  if constexpr (MODE == PM_FWD || MODE == PM_INV) {
+    px_s2_global<T, N, INV1, W>(buf, out + (long long)s * out_stride, c0);
   } else {
-    fft_smem<T, N, false, NIN * kTC, kPencilNT, true>(buf, 1, W, tw);
-  }
-  if constexpr (MODE == PM_VEL || MODE == PM_ADJ) {
-    for (int e = tid; e < N * kTC; e += kPencilNT) {
-      const int t = e % kTC, kx = e / kTC;
-      const int col = c0 + t;
-      if (col >= NCOL) continue;   // ragged last tile: nothing stored
-      const int ky = col / NH, kz = col % NH;
-      const int nx = kx < N / 2 ? kx : kx - N;
-      const int ny = ky < N / 2 ? ky : ky - N;
-      const int nz = kz;
-      const T a = __ldg(&amp[nx * nx + ny * ny + nz * nz]);
-      const T ox = (kx == N / 2) ? (T)0 : (T)nx;
-      const T oy = (ky == N / 2) ? (T)0 : (T)ny;
-      const T oz = (kz == N / 2) ? (T)0 : (T)nz;
-      if constexpr (MODE == PM_VEL) {
-        const C wk = buf[kx * W + t];
-        const C iw = C{-a * wk.y, a * wk.x};   // i amp w_k
-        buf[kx * W + t] = C{ox * iw.x, ox * iw.y};
-        buf[kx * W + kTC + t] = C{oy * iw.x, oy * iw.y};
-        buf[kx * W + 2 * kTC + t] = C{oz * iw.x, oz * iw.y};
-      } else {
-        const C sx = buf[kx * W + t], sy = buf[kx * W + kTC + t], sz = buf[kx * W + 2 * kTC + t];
-        const C sum = C{ox * sx.x + oy * sy.x + oz * sz.x, ox * sx.y + oy * sy.y + oz * sz.y};
-        buf[kx * W + t] = C{a * sum.y, -a * sum.x};   // -i amp sum_j n_j s_j
+#pragma unroll 1
+    for (int j = 0; j < NIN; ++j) px_s2_smem<T, N, false, W>(buf + j * kTC);
+    // inverse transform(s): stage 1 loads the natural-order spectra and
+    // applies the k-space operator on the way in
+    if constexpr (MODE == PM_VEL) {
+      // component order y, z, x: x is written over the input spectrum, and
+      // each group reads and writes only its own elements
+#pragma unroll 1
+      for (int q = 0; q < 3; ++q) {
+        const int jo = q == 2 ? 0 : q + 1;
+#pragma unroll 1
+        for (int g = threadIdx.x; g < kTC * M; g += kPencilNT) {
+          const int t = g % kTC, m = g / kTC;
+          const long long col = c0 + t;
+          const ColGeom<N> cg = col_geom<N>(col < NCOL ? col : 0);
+          C a[R1];
+#pragma unroll
+          for (int jj = 0; jj < R1; ++jj) {
+            const int kx = m + M * jj;
+            const int nx = kx < N / 2 ? kx : kx - N;
+            const T am = __ldg(&amp[nx * nx + cg.ny2nz2]);
+            const T o = (T)(jo == 0 ? ((kx == N / 2) ? 0.f : (float)nx) : (jo == 1 ? cg.oy : cg.oz));
+            const C wk = buf[kx * W + t];
+            a[jj] = C{-am * o * wk.y, am * o * wk.x};   // i amp n_j w_k
+          }
+          stage1_group<T, N, true>(a, m, tw);
+#pragma unroll
+          for (int k2 = 0; k2 < R1; ++k2) buf[(m + M * k2) * W + jo * kTC + t] = a[k2];
+        }
       }
+      __syncthreads();
+#pragma unroll 1
+      for (int jo = 0; jo < 3; ++jo)
+        px_s2_global<T, N, true, W>(buf + jo * kTC, out + (long long)(s * 3 + jo) * out_stride, c0);
+    } else {
+      // PM_ADJ: -i amp sum_j n_j s_j, written over component 0
+#pragma unroll 1
+      for (int g = threadIdx.x; g < kTC * M; g += kPencilNT) {
+        const int t = g % kTC, m = g / kTC;
+        const long long col = c0 + t;
+        const ColGeom<N> cg = col_geom<N>(col < NCOL ? col : 0);
+        C a[R1];
+#pragma unroll
+        for (int jj = 0; jj < R1; ++jj) {
+          const int kx = m + M * jj;
+          const int nx = kx < N / 2 ? kx : kx - N;
+          const T am = __ldg(&amp[nx * nx + cg.ny2nz2]);
+          const T ox = (kx == N / 2) ? (T)0 : (T)nx;
+          const C sx = buf[kx * W + t], sy = buf[kx * W + kTC + t], sz = buf[kx * W + 2 * kTC + t];
+          const C sum = C{ox * sx.x + (T)cg.oy * sy.x + (T)cg.oz * sz.x, ox * sx.y + (T)cg.oy * sy.y + (T)cg.oz * sz.y};
+          a[jj] = C{am * sum.y, -am * sum.x};
+        }
+        stage1_group<T, N, true>(a, m, tw);
+#pragma unroll
+        for (int k2 = 0; k2 < R1; ++k2) buf[(m + M * k2) * W + t] = a[k2];
+      }
+      __syncthreads();
+      px_s2_global<T, N, true, W>(buf, out + (long long)s * out_stride, c0);
     }
-    __syncthreads();
-    constexpr int NOUT = (MODE == PM_VEL) ? 3 : 1;
-    fft_smem<T, N, true, NOUT * kTC, kPencilNT, true>(buf, 1, W, tw);
-  }
-  constexpr int NOUT = (MODE == PM_VEL) ? 3 : 1;
-  for (int e = tid; e < NOUT * N * kTC; e += kPencilNT) {
-    const int t = e % kTC;
-    const int x = (e / kTC) % N;
-    const int j = e / (kTC * N);
-    const int col = c0 + t;
-    if (col < NCOL) out[(long long)(s * NOUT + j) * out_stride + (long long)x * NCOL + col] = buf[x * W + j * kTC + t];
   }
 }
 

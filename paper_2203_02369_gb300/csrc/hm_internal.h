@@ -6,10 +6,12 @@
 
 namespace hm {
 
-// Kernel launch with programmatic stream serialisation (the kernel may start
-// while its predecessor in the stream finishes; it calls pdl_wait before
-// reading the predecessor's output).  pdl_enabled() is false when the
-// environment sets HM_PDL=0.
+// Kernel launch, optionally with programmatic stream serialisation (the
+// kernel may start while its predecessor in the stream finishes; it calls
+// pdl_wait before reading the predecessor's output).  Off unless the
+// environment sets HM_PDL=1: measured on the 128^3 trajectory it was slower
+// (dependents launched early hold shared memory on SMs that the draining
+// plane pass still needs).
 bool pdl_enabled();
 template <typename... KArgs, typename... Args>
 inline cudaError_t launch_k(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,

@@ -71,6 +71,23 @@ def test_fft_roundtrip_vs_numpy(H, N, prec):
     assert rel(back, x) < tol
 
 
+@pytest.mark.parametrize("N,prec", [(8, "fp64"), (32, "fp64"), (128, "fp64"), (64, "fp32"), (128, "fp32"),
+                                    (256, "fp32")])
+def test_fft_c2r_general_half_spectrum(H, N, prec):
+    """A half spectrum that is not the transform of a real field (random
+    values everywhere, including the imaginary parts of the kz = 0 and N/2
+    lines): c2r keeps the real part of those lines after the complex y and x
+    transforms, as numpy's irfftn does."""
+    p = H.Problem(N, 100.0, precision=prec)
+    rng = np.random.default_rng(N + 5)
+    X = rng.normal(size=(1, N, N, N // 2 + 1)) + 1j * rng.normal(size=(1, N, N, N // 2 + 1))
+    if prec == "fp32":
+        X = X.astype(np.complex64).astype(np.complex128)
+    ref = np.fft.irfftn(X, s=(N, N, N), axes=(1, 2, 3)) * N ** 3
+    got = p.fft_c2r(torch.tensor(X, device="cuda")).cpu().numpy()
+    assert rel(got, ref) < (2e-6 if prec == "fp32" else 1e-13)
+
+
 # ---------------------------------------------------------- velocity ----
 @pytest.mark.parametrize("N,L,prec", [(16, 200.0, "fp64"), (64, 500.0, "fp32"), (32, 300.0, "fp64")])
 def test_velocity_field_vs_oracle(H, N, L, prec):
