@@ -121,27 +121,41 @@ class Clocks:
 # --------------------------------------------------------------------------
 # algorithmic bytes per launch of each kernel kind (FP32, one chain)
 # --------------------------------------------------------------------------
-def algorithmic_bytes(N, n, C=1, rsz=4):
+def algorithmic_bytes(N, n, C=1, rsz=4, fo=1.0):
     """Bytes each kernel kind must move per launch if every array it touches
     is read or written once: R = one real N^3 grid, S = one half spectrum,
-    plus the per-point records (32 B), partials and catalogue fields."""
+    plus the per-point records (32 B), partials and catalogue fields.  fo is
+    the fraction of x-planes that carry a CIC corner of some point: the
+    gather reads, the scatter writes and the adjoint pencil reads only
+    those planes of the three component spectra."""
     R = rsz * N ** 3
     S = 2 * rsz * N * N * (N // 2 + 1)
     return {
         "plane_r2c_field": C * (R + S),
         "pencil_velocity": C * (S + 3 * S),
-        "plane_c2r_velocity_gather": C * (3 * S + 3 * 2 * n * (32 + 8)),
+        "plane_c2r_velocity_gather": C * (fo * 3 * S + 3 * 2 * n * (32 + 8)),
         "memset_bucket_counts": 0,
         "points_bucket_count_standalone": C * n * 24,
         "points_bucket_place": C * n * (72 + 48 + 40),
         "points_likelihood_kick": C * n * (104 + 40 + 24),
-        "plane_r2c_scatter_adjoint": C * (3 * S + 3 * 2 * n * 32),
-        "pencil_adjoint": C * (3 * S + S),
+        "plane_r2c_scatter_adjoint": C * (fo * 3 * S + 3 * 2 * n * 32),
+        "pencil_adjoint": C * (fo * 3 * S + S),
         "plane_c2r_gradient_kick": C * (S + 4 * R + S),
         "trajectory_begin": C * (6 * R + 56 * n),
         "finalize_energy": 0,
         "restore_rejected": 0,
     }
+
+
+def occupied_plane_fraction(prob, d):
+    """Fraction of the x-planes holding a CIC corner of some point at
+    distances d (planes ix and ix + 1 of every point's cell)."""
+    cell, _ = prob.cells(d, sort=False)
+    ix = cell.cpu().numpy().astype(np.int64) // (prob.N * prob.N)
+    occ = np.zeros(prob.N, dtype=bool)
+    occ[ix] = True
+    occ[(ix + 1) % prob.N] = True
+    return float(occ.mean())
 
 
 def model_bytes(N, n, rsz=4):
@@ -302,7 +316,9 @@ def run_batched(args, eps, L, use_graph):
     ess_tot = sum(ess(tr[:, c]["psi"]) for tr in traces for c in range(tr.shape[1]))
     acc = float(np.mean(np.concatenate([tr["accept"].ravel() for tr in traces])))
     n128 = states[0][1].C
-    ab = algorithmic_bytes(128, 30000, C=n128)
+    st128 = states[0][1]
+    fo = float(np.mean([occupied_plane_fraction(st128.problems[st128.chain_problem[c]], st128.get(c)["d"]) for c in range(n128)]))
+    ab = algorithmic_bytes(128, 30000, C=n128, fo=fo)
     total_k = sum(v[0] for v in prof.values())
     dname, (dms, dl) = max(prof.items(), key=lambda kv: kv[1][0])
     peaks, src = measured_peaks()
@@ -322,6 +338,7 @@ def run_batched(args, eps, L, use_graph):
                                       "at its own grid and catalogue size) x evaluations/s / measured HBM peak"},
            "roofline_128": {"kernel": dname, "achieved": ach, "peak": peaks.get("hbm_gbs"), "unit": "GB/s",
                             "frac": ach / peaks.get("hbm_gbs") if ach else None,
+                            "occupied_plane_fraction": fo,
                             "note": "16 chains of 128^3 in one launch; algorithmic bytes of the grid terms "
                                     "(point terms at 3e4 points per chain, an upper bound for these catalogues)"}}
     for _, s in states:
@@ -503,9 +520,10 @@ def main():
                "note": "per step: pinned H2D of (w, d), hm_state_set + hm_state_refresh (one extra gradient "
                        "evaluation, not counted), one trajectory, D2H of (w, d) and the trace record"}
 
-    # roofline of the dominant kernel (live CUDA-event times from the timed region)
+    # roofline of the dominant kernel (live CUDA-event times from the profiled pass)
     N, n = spec.N, spec.n_points
-    ab = algorithmic_bytes(N, n)
+    fo = occupied_plane_fraction(prob, state.get(0)["d"])
+    ab = algorithmic_bytes(N, n, fo=fo)
     total_k = sum(v[0] for v in prof.values())
     dom = max(prof.items(), key=lambda kv: kv[1][0])
     dname, (dms, dl) = dom
@@ -520,6 +538,7 @@ def main():
     roofline = {"bound": "hbm", "kernel": dname, "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak if achieved else None, "traffic": ncu_traffic(dname),
                 "algorithmic_bytes_per_launch": ab[dname], "peak_source": f"{src} hbm_gbs (copy bandwidth)",
+                "occupied_plane_fraction": fo,
                 "timing": "CUDA events around each launch of the kernel on its stream, averaged over the "
                           "profiled pass of the same K trajectories (L2 flushed before each)",
                 "clocks_profiled_pass": clk_p}

@@ -426,7 +426,7 @@ static int eval_run(const GradArgs& a, int n, int last_mode, cudaStream_t st) {
     // adjoint: residuals scattered plane by plane, forward transform, weights
     HM_PROF(pf, KK_R2C_SCATTER, st, launch_plane_r2c_scatter(a.prec, a.N, pts, a.S1, a.nspec, 3 * a.C, a.tw, st));
     HM_PROF(pf, KK_PENCIL_ADJ, st,
-            launch_pencil(a.prec, a.N, PM_ADJ, a.S1, a.nspec, a.S2, a.nspec, a.C, a.tw, a.amp, st));
+            launch_pencil(a.prec, a.N, PM_ADJ, a.S1, a.nspec, a.S2, a.nspec, a.C, a.tw, a.amp, st, pts.off));
     FieldEpi epi{};
     epi.w = a.w;
     epi.pw = a.pw;
@@ -1445,7 +1445,7 @@ extern "C" int hm_logpost_grad_noalloc(hm_problem* p, const void* w_dev, const d
   HM_CUDA(launch_plane_c2r_gather(p->prec, p->N, S2, p->nspec, pts, 3, p->tw.p, st));
   HM_CUDA(launch_points_lik(p->prec, 1, maxp, pp, pa, pts_part, pb, GM_GRAD, kin_part, cs, nullptr, st));
   HM_CUDA(launch_plane_r2c_scatter(p->prec, p->N, pts, S1, p->nspec, 3, p->tw.p, st));
-  HM_CUDA(launch_pencil(p->prec, p->N, PM_ADJ, S1, p->nspec, S2, p->nspec, 1, p->tw.p, p->amp.p, st));
+  HM_CUDA(launch_pencil(p->prec, p->N, PM_ADJ, S1, p->nspec, S2, p->nspec, 1, p->tw.p, p->amp.p, st, pts.off));
   FieldEpi epi{};
   epi.w = const_cast<void*>(w_dev);
   epi.pw = nullptr;

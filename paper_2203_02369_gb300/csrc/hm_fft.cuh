@@ -125,6 +125,45 @@ template <int N> struct Radix {
   static constexpr int M = N / R1;
 };
 
+// Stage 2 of fft_smem on its own (after a stage 1 done elsewhere): for each
+// k2 < R1 the M-point DFT of the contiguous block m + M k2, stored at its
+// natural position after a block barrier.  Ends with a barrier.
+template <typename T, int N, bool INV, int ROWS, int NT>
+__device__ __forceinline__ void fft_smem_stage2(cplx<T>* buf, int rs, int es) {
+  using C = cplx<T>;
+  constexpr int R1 = Radix<N>::R1;
+  constexpr int M = Radix<N>::M;
+  const int tid = threadIdx.x;
+  if constexpr (M > 1) {
+    constexpr int G2 = ROWS * R1;
+    constexpr int PER = (G2 + NT - 1) / NT;
+    C a[PER][M];
+#pragma unroll
+    for (int i = 0; i < PER; ++i) {
+      int g = tid + i * NT;
+      if (G2 % NT == 0 || g < G2) {
+        int r = g % ROWS, k2 = g / ROWS;
+        C* base = buf + r * rs + (M * k2) * es;
+#pragma unroll
+        for (int m = 0; m < M; ++m) a[i][m] = base[m * es];
+        dft_reg<M, INV>(a[i]);
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < PER; ++i) {
+      int g = tid + i * NT;
+      if (G2 % NT == 0 || g < G2) {
+        int r = g % ROWS, k2 = g / ROWS;
+        C* base = buf + r * rs + k2 * es;
+#pragma unroll
+        for (int k1 = 0; k1 < M; ++k1) base[(R1 * k1) * es] = a[i][k1];
+      }
+    }
+    __syncthreads();
+  }
+}
+
 // Batched in-place FFT of ROWS rows of length N held in shared memory.
 // Element k of row r lives at buf[r*rs + k*es].  NT threads take part; all of
 // them must call this function (it contains block barriers).  tw[e] holds
@@ -166,48 +205,25 @@ __device__ __forceinline__ void fft_smem(cplx<T>* buf, int rs, int es, const cpl
     for (int k2 = 0; k2 < R1; ++k2) base[(M * k2) * es] = a[k2];
   }
   __syncthreads();
-  if constexpr (M > 1) {
-    // ---- stage 2 (load all groups, barrier, store in natural order) ----
-    constexpr int G2 = ROWS * R1;
-    constexpr int PER = (G2 + NT - 1) / NT;
-    C a[PER][M];
-#pragma unroll
-    for (int i = 0; i < PER; ++i) {
-      int g = tid + i * NT;
-      if (G2 % NT == 0 || g < G2) {
-        int r = g % ROWS, k2 = g / ROWS;
-        C* base = buf + r * rs + (M * k2) * es;
-#pragma unroll
-        for (int m = 0; m < M; ++m) a[i][m] = base[m * es];
-        dft_reg<M, INV>(a[i]);
-      }
-    }
-    __syncthreads();
-#pragma unroll
-    for (int i = 0; i < PER; ++i) {
-      int g = tid + i * NT;
-      if (G2 % NT == 0 || g < G2) {
-        int r = g % ROWS, k2 = g / ROWS;
-        C* base = buf + r * rs + k2 * es;
-#pragma unroll
-        for (int k1 = 0; k1 < M; ++k1) base[(R1 * k1) * es] = a[i][k1];
-      }
-    }
-    __syncthreads();
-  }
+  fft_smem_stage2<T, N, INV, ROWS, NT>(buf, rs, es);
 }
 
-// Per-thread accumulator of 0.5 * sum x^2 for energy reductions.  For FP32
-// data it keeps an unevaluated pair (hi, lo) of floats: x*x is split exactly
-// into p + e with an FMA, p/2 is added with Knuth's TwoSum and every rounding
-// error goes to lo, so the per-thread sum carries about 48 significant bits
-// without using the (slow on this part) FP64 pipe; the pair is converted to
-// double once per thread for the FP64 block and grid reductions.  For FP64
+// Accumulator of 0.5 * sum x^2 for energy reductions.  For FP32 data it
+// keeps an unevaluated pair (hi, lo) of floats: x*x is split exactly into
+// p + e with an FMA, p/2 is added with Knuth's TwoSum and every rounding
+// error goes to lo, so the sum carries about 48 significant bits without
+// using the (slow on this part) FP64 pipe.  Partial sums of a warp are merged
+// the same way (warp_reduce, a fixed shuffle tree), and the pair is converted
+// to double once per warp for the FP64 block and grid reductions.  For FP64
 // data it is a plain double sum.
 template <typename T> struct HalfSqAcc;
 template <> struct HalfSqAcc<double> {
   double s = 0.0;
   __device__ __forceinline__ void add_half_sq(double x) { s += 0.5 * x * x; }
+  __device__ __forceinline__ void warp_reduce() {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  }
   __device__ __forceinline__ double value() const { return s; }
 };
 template <> struct HalfSqAcc<float> {
@@ -224,6 +240,15 @@ template <> struct HalfSqAcc<float> {
     const float e = __fmaf_rn(x, x, -p);
     add(__fmul_rn(0.5f, p));
     lo = __fmaf_rn(0.5f, e, lo);
+  }
+  __device__ __forceinline__ void warp_reduce() {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const float h = __shfl_down_sync(0xffffffffu, hi, o);
+      const float l = __shfl_down_sync(0xffffffffu, lo, o);
+      add(h);
+      lo = __fadd_rn(lo, l);
+    }
   }
   __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
 };

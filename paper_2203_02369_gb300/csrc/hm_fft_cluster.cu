@@ -185,6 +185,16 @@ __device__ __forceinline__ PlaneBucketsCl plane_buckets_cl(const int* __restrict
   return pb;
 }
 
+// True when no point of chain c has a CIC corner on plane ix (all K
+// sub-buckets of buckets ix and ix-1 empty).
+template <int N>
+__device__ __forceinline__ bool plane_empty_cl(const int* __restrict__ off, int c, int ix) {
+  constexpr int K = ClCfg<N>::K;
+  const int* o = off + (long long)c * (N * K + 1);
+  const int ixm = (ix + N - 1) & (N - 1);
+  return o[(ix + 1) * K] == o[ix * K] && o[(ixm + 1) * K] == o[ixm * K];
+}
+
 template <typename T> __device__ __forceinline__ T rcomp_cl(const PtRec<T>& p, int j) {
   return j == 0 ? p.rx : (j == 1 ? p.ry : p.rz);
 }
@@ -225,9 +235,13 @@ k_plane_r2c_cl(const T* __restrict__ in, long long in_stride, cplx<T>* __restric
     load_rows_packed_cl<T, N>(R, in + (long long)s * in_stride + ((long long)ix * N + row0) * N);
     __syncthreads();
   } else {
+    const int c = s / 3, j = s % 3;
+    // no point has a CIC corner on this plane (same answer in every CTA of
+    // the cluster): its spectrum is zero, which the adjoint pencil pass
+    // knows from the same bucket offsets, so nothing is written
+    if (plane_empty_cl<N>(pts.off, c, ix)) return;
     for (int e = threadIdx.x; e < P::ROWSLAB; e += NT) R[e] = C{(T)0, (T)0};
     cl.sync();   // every slab of the cluster is zero before any remote add
-    const int c = s / 3, j = s % 3;
     const PlaneBucketsCl pb = plane_buckets_cl<N>(pts.off, c, ix, q);
     const PtRec<T>* Rp = static_cast<const PtRec<T>*>(pts.rec);
     for (int t = threadIdx.x; t < pb.n0 + pb.n1; t += NT) {
@@ -299,6 +313,10 @@ k_plane_c2r_cl(const cplx<T>* __restrict__ in, long long in_stride, T* __restric
   const int s = blockIdx.y;
   const int row0 = q * RQ;
   auto rem = [&](int k) -> C* { return cl.map_shared_rank(R, k); };   // CTA k's row slab
+  // gather: only the values at the points' corners are used, so a plane
+  // that no point touches needs no transform (same answer in every CTA of
+  // the cluster, so the whole cluster leaves before any cluster barrier)
+  if (MODE == C2R_GATHER && plane_empty_cl<N>(pts.off, s / 3, ix)) return;
   int c0, c1;
   own_columns_cl<N>(q, c0, c1);
   const int nc = c1 - c0;
@@ -407,17 +425,14 @@ k_plane_c2r_cl(const cplx<T>* __restrict__ in, long long in_stride, T* __restric
         }
       }
     }
-    double acc_w = aw.value(), acc_p = ap.value();
-    // deterministic block reduction: warp shuffles, then thread 0 in order
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      acc_w += __shfl_down_sync(0xffffffffu, acc_w, o);
-      acc_p += __shfl_down_sync(0xffffffffu, acc_p, o);
-    }
+    // deterministic block reduction: a fixed shuffle tree per warp, then
+    // thread 0 over the warps in order
+    aw.warp_reduce();
+    ap.warp_reduce();
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     if (lane == 0) {
-      red[0][wid] = acc_w;
-      red[1][wid] = acc_p;
+      red[0][wid] = aw.value();
+      red[1][wid] = ap.value();
     }
     __syncthreads();
     if (threadIdx.x == 0) {

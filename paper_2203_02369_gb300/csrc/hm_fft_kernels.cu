@@ -80,96 +80,19 @@ template <int N> __device__ __forceinline__ constexpr int yo(int y) {
   return (y >> 1) * PlaneCfg<N>::ZP + (y & 1) * (N / 2);
 }
 
-// Z rows (after the forward z transform) -> spectrum view.  For a packed row
-// pair Z = X_a + i X_b (X_a, X_b the spectra of the real rows 2r, 2r+1):
-// X_a[k] = (Z[k] + conj Z[N-k]) / 2, X_b[k] = (Z[k] - conj Z[N-k]) / (2i);
-// column 0 receives (X[0], X[N/2]) of each row, both real.
-template <typename T, int N>
-__device__ __forceinline__ void unpack_rows(cplx<T>* B) {
-  using C = cplx<T>;
-  using P = PlaneCfg<N>;
-  constexpr int ZP = P::ZP, NT = P::NT, NC = P::NC;
-  constexpr int TOT = P::NR * NC;
-  constexpr int PER = (TOT + NT - 1) / NT;
-  C a[PER], b[PER];
-#pragma unroll
-  for (int i = 0; i < PER; ++i) {
-    const int e = threadIdx.x + i * NT;
-    if (TOT % NT == 0 || e < TOT) {
-      const int r = e / NC, k = e % NC;
-      const C* zr = B + r * ZP;
-      if (k == 0) {
-        const C z0 = zr[0], zn = zr[N / 2];
-        a[i] = C{z0.x, zn.x};
-        b[i] = C{z0.y, zn.y};
-      } else {
-        const C zk = zr[k], zm = cconj(zr[N - k]);
-        const C sp = cadd(zk, zm), df = csub(zk, zm);
-        a[i] = C{(T)0.5 * sp.x, (T)0.5 * sp.y};
-        b[i] = C{(T)0.5 * df.y, (T)-0.5 * df.x};
-      }
-    }
-  }
-  __syncthreads();
-#pragma unroll
-  for (int i = 0; i < PER; ++i) {
-    const int e = threadIdx.x + i * NT;
-    if (TOT % NT == 0 || e < TOT) {
-      const int r = e / NC, k = e % NC;
-      B[r * ZP + k] = a[i];
-      B[r * ZP + NC + k] = b[i];
-    }
-  }
-  __syncthreads();
-}
-
-// Spectrum view (inverse-transformed along y) -> Z rows for the inverse z
-// transform: Z[k] = X_a[k] + i X_b[k] with the Hermitian extension X[k] =
-// conj X[N-k] for k > N/2 and the real kz = 0, N/2 values from column 0.
-template <typename T, int N>
-__device__ __forceinline__ void pack_rows(cplx<T>* B) {
-  using C = cplx<T>;
-  using P = PlaneCfg<N>;
-  constexpr int ZP = P::ZP, NT = P::NT, NC = P::NC;
-  constexpr int TOT = P::NR * N;
-  constexpr int PER = (TOT + NT - 1) / NT;
-  C o[PER];
-#pragma unroll
-  for (int i = 0; i < PER; ++i) {
-    const int e = threadIdx.x + i * NT;
-    if (TOT % NT == 0 || e < TOT) {
-      const int r = e / N, k = e % N;
-      const C* zr = B + r * ZP;
-      if (k == 0 || k == N / 2) {
-        const C a = zr[0], b = zr[NC];
-        o[i] = (k == 0) ? C{a.x, b.x} : C{a.y, b.y};
-      } else {
-        C a, b;
-        if (k < N / 2) {
-          a = zr[k];
-          b = zr[NC + k];
-        } else {
-          a = cconj(zr[N - k]);
-          b = cconj(zr[NC + (N - k)]);
-        }
-        o[i] = C{a.x - b.y, a.y + b.x};
-      }
-    }
-  }
-  __syncthreads();
-#pragma unroll
-  for (int i = 0; i < PER; ++i) {
-    const int e = threadIdx.x + i * NT;
-    if (TOT % NT == 0 || e < TOT) B[(e / N) * ZP + (e % N)] = o[i];
-  }
-  __syncthreads();
-}
-
-// Forward y transform of the spectrum view; the result goes to the global
-// half-spectrum plane dst[ky][kz] (pitch N/2 + 1).  Stage 2 stores columns
-// c >= 1 straight to global memory; the packed column 0 is transformed in
-// shared memory and split afterwards: with Y = DFT(a + i b) for real a, b,
-// DFT(a)[k] = (Y[k] + conj Y[-k]) / 2 and DFT(b)[k] = (Y[k] - conj Y[-k]) / (2i).
+// Forward y transform of the plane held as Z rows (after the forward z
+// transform); the result goes to the global half-spectrum plane dst[ky][kz]
+// (pitch N/2 + 1).
+//
+// Stage 1 forms its operands from the Z rows as it loads them (the real ->
+// half-spectrum unpacking): for a packed row pair Z = X_a + i X_b (X_a, X_b
+// the spectra of the real rows 2r, 2r+1), X_a[k] = (Z[k] + conj Z[N-k]) / 2
+// and X_b[k] = (Z[k] - conj Z[N-k]) / (2i); column 0 takes (X[0], X[N/2]),
+// both real.  All loads finish before the in-place stores (they alias).
+// Stage 2 stores columns c >= 1 straight to global memory; the packed column
+// 0 is transformed in shared memory and split afterwards: with
+// Y = DFT(a + i b) for real a, b, DFT(a)[k] = (Y[k] + conj Y[-k]) / 2 and
+// DFT(b)[k] = (Y[k] - conj Y[-k]) / (2i).
 template <typename T, int N>
 __device__ __forceinline__ void yfft_fwd_store(cplx<T>* B, cplx<T>* __restrict__ dst,
                                                const cplx<T>* __restrict__ tw) {
@@ -178,15 +101,33 @@ __device__ __forceinline__ void yfft_fwd_store(cplx<T>* B, cplx<T>* __restrict__
   constexpr int R1 = Radix<N>::R1, M = Radix<N>::M;
   constexpr int NT = P::NT, NC = P::NC, NH = P::NH, ZP = P::ZP;
   constexpr int G1 = NC * M;
-  // ---- stage 1 (in place) ----
-#pragma unroll 1
-  for (int g = threadIdx.x; g < G1; g += NT) {
-    const int c = g % NC, m = (M == 1) ? 0 : g / NC;
-    C a[R1];
-    C* p = B + c + hoff<N>(m);
+  static_assert(G1 <= NT, "one stage-1 group per thread");
+  // ---- stage 1: unpack on load, DFT, twiddles; barrier; store ----
+  const int g = threadIdx.x;
+  const bool act = g < G1;
+  const int c = g % NC, m = (M == 1) ? 0 : g / NC;
+  C a[R1];
+  if (act) {
 #pragma unroll
-    for (int j = 0; j < R1; ++j) a[j] = p[(M == 1) ? yo<N>(j) : j * (M / 2) * ZP];
+    for (int j = 0; j < R1; ++j) {
+      const int y = m + M * j;
+      const C* zr = B + (y >> 1) * ZP;
+      C v;
+      if (c == 0) {
+        const C z0 = zr[0], zn = zr[N / 2];
+        v = (y & 1) ? C{z0.y, zn.y} : C{z0.x, zn.x};
+      } else {
+        const C zk = zr[c], zm = cconj(zr[N - c]);
+        const C sp = cadd(zk, zm), df = csub(zk, zm);
+        v = (y & 1) ? C{(T)0.5 * df.y, (T)-0.5 * df.x} : C{(T)0.5 * sp.x, (T)0.5 * sp.y};
+      }
+      a[j] = v;
+    }
     stage1_group<T, N, false>(a, m, tw);
+  }
+  __syncthreads();
+  if (act) {
+    C* p = B + c + hoff<N>(m);
     if constexpr (M == 1) {      // natural order already: this is the output
       if (c != 0) {
 #pragma unroll
@@ -205,42 +146,89 @@ __device__ __forceinline__ void yfft_fwd_store(cplx<T>* B, cplx<T>* __restrict__
     // ---- stage 2 (load all groups, barrier, store in natural order) ----
     constexpr int G2 = NC * R1;
     constexpr int PER = (G2 + NT - 1) / NT;
-    C a[PER][M];
+    C b[PER][M];
 #pragma unroll
     for (int i = 0; i < PER; ++i) {
-      const int g = threadIdx.x + i * NT;
-      if (G2 % NT == 0 || g < G2) {
-        const int c = g % NC, k2 = g / NC;
-        const C* q = B + c + (M * k2 / 2) * ZP;
+      const int g2 = threadIdx.x + i * NT;
+      if (G2 % NT == 0 || g2 < G2) {
+        const int c2 = g2 % NC, k2 = g2 / NC;
+        const C* q = B + c2 + (M * k2 / 2) * ZP;
 #pragma unroll
-        for (int m = 0; m < M; ++m) a[i][m] = q[yo<N>(m)];
-        dft_reg<M, false>(a[i]);
+        for (int mm = 0; mm < M; ++mm) b[i][mm] = q[yo<N>(mm)];
+        dft_reg<M, false>(b[i]);
       }
     }
     __syncthreads();
 #pragma unroll
     for (int i = 0; i < PER; ++i) {
-      const int g = threadIdx.x + i * NT;
-      if (G2 % NT == 0 || g < G2) {
-        const int c = g % NC, k2 = g / NC;
-        if (c != 0) {
+      const int g2 = threadIdx.x + i * NT;
+      if (G2 % NT == 0 || g2 < G2) {
+        const int c2 = g2 % NC, k2 = g2 / NC;
+        if (c2 != 0) {
 #pragma unroll
-          for (int k1 = 0; k1 < M; ++k1) dst[(k2 + R1 * k1) * NH + c] = a[i][k1];
+          for (int k1 = 0; k1 < M; ++k1) dst[(k2 + R1 * k1) * NH + c2] = b[i][k1];
         } else {
           C* q = B + hoff<N>(k2);
 #pragma unroll
-          for (int k1 = 0; k1 < M; ++k1) q[k1 * (R1 / 2) * ZP] = a[i][k1];
+          for (int k1 = 0; k1 < M; ++k1) q[k1 * (R1 / 2) * ZP] = b[i][k1];
         }
       }
     }
+    __syncthreads();
   }
-  __syncthreads();
   for (int k = threadIdx.x; k < N; k += NT) {
     const C y = B[hoff<N>(k)], ym = cconj(B[hoff<N>((N - k) & (N - 1))]);
     const C sp = cadd(y, ym), df = csub(y, ym);
     dst[k * NH] = C{(T)0.5 * sp.x, (T)0.5 * sp.y};
     dst[k * NH + N / 2] = C{(T)0.5 * df.y, (T)-0.5 * df.x};
   }
+}
+
+// Inverse z transform of the plane held in the spectrum view (after the
+// inverse y transform), to Z rows of real values.  Stage 1 forms the packed
+// rows as it loads them: Z[k] = X_a[k] + i X_b[k] with the Hermitian
+// extension X[k] = conj X[N-k] for k > N/2 and the real kz = 0, N/2 values
+// from column 0.  All loads finish before the in-place stores.
+template <typename T, int N>
+__device__ __forceinline__ void zfft_inv_packed(cplx<T>* B, const cplx<T>* __restrict__ tw) {
+  using C = cplx<T>;
+  using P = PlaneCfg<N>;
+  constexpr int R1 = Radix<N>::R1, M = Radix<N>::M;
+  constexpr int NT = P::NT, NC = P::NC, NR = P::NR, ZP = P::ZP;
+  constexpr int G1 = NR * M;
+  static_assert(G1 <= NT, "one stage-1 group per thread");
+  const int g = threadIdx.x;
+  const bool act = g < G1;
+  const int r = g % NR, m = (M == 1) ? 0 : g / NR;
+  C a[R1];
+  if (act) {
+    const C* zr = B + r * ZP;
+#pragma unroll
+    for (int j = 0; j < R1; ++j) {
+      const int k = m + M * j;
+      C v;
+      if ((j == 0 || j == R1 / 2) && m == 0) {     // k = 0 or N/2: real parts from column 0
+        const C x0 = zr[0], x1 = zr[NC];
+        v = (j == 0) ? C{x0.x, x1.x} : C{x0.y, x1.y};
+      } else if (j < R1 / 2) {                     // 0 < k < N/2
+        const C x0 = zr[k], x1 = zr[NC + k];
+        v = C{x0.x - x1.y, x0.y + x1.x};
+      } else {                                     // k > N/2: conjugate of N - k
+        const C x0 = cconj(zr[N - k]), x1 = cconj(zr[NC + N - k]);
+        v = C{x0.x - x1.y, x0.y + x1.x};
+      }
+      a[j] = v;
+    }
+    stage1_group<T, N, true>(a, m, tw);
+  }
+  __syncthreads();
+  if (act) {
+    C* p = B + r * ZP + m;
+#pragma unroll
+    for (int k2 = 0; k2 < R1; ++k2) p[M * k2] = a[k2];
+  }
+  __syncthreads();
+  fft_smem_stage2<T, N, true, NR, NT>(B, ZP, 1);
 }
 
 // Inverse y transform of the global half-spectrum plane src[ky][kz] into the
@@ -357,10 +345,14 @@ k_plane_r2c(const T* __restrict__ in, long long in_stride, cplx<T>* __restrict__
       B[r * ZP + z] = C{__ldg(&src[(2 * r) * N + z]), __ldg(&src[(2 * r + 1) * N + z])};
     }
   } else {
-    for (int e = threadIdx.x; e < P::SIZE; e += NT) B[e] = C{(T)0, (T)0};
-    __syncthreads();
     const int c = s / 3, j = s % 3;
     const PlaneBuckets pb = plane_buckets<N>(pts.off, c, ix);
+    // no point has a CIC corner on this plane: its spectrum is zero, which
+    // the adjoint pencil pass knows from the same bucket offsets, so nothing
+    // is written
+    if (pb.n0 + pb.n1 == 0) return;
+    for (int e = threadIdx.x; e < P::SIZE; e += NT) B[e] = C{(T)0, (T)0};
+    __syncthreads();
     const PtRec<T>* R = static_cast<const PtRec<T>*>(pts.rec);
     for (int t = threadIdx.x; t < pb.n0 + pb.n1; t += NT) {
       const bool lower = t < pb.n0;
@@ -378,7 +370,6 @@ k_plane_r2c(const T* __restrict__ in, long long in_stride, cplx<T>* __restrict__
   }
   __syncthreads();
   zfft<T, N, false>(B, tw);
-  unpack_rows<T, N>(B);
   yfft_fwd_store<T, N>(B, out + (long long)s * out_stride + (long long)ix * N * P::NH, tw);
 }
 
@@ -404,9 +395,14 @@ k_plane_c2r(const cplx<T>* __restrict__ in, long long in_stride, T* __restrict__
   __shared__ double red[2][NT / 32];
   const int ix = blockIdx.x;
   const int s = blockIdx.y;
+  if constexpr (MODE == C2R_GATHER) {
+    // only the values at the points' corners are used: a plane that no
+    // point touches needs no transform
+    const PlaneBuckets pb = plane_buckets<N>(pts.off, s / 3, ix);
+    if (pb.n0 + pb.n1 == 0) return;
+  }
   yfft_inv_load<T, N>(B, in + (long long)s * in_stride + (long long)ix * N * P::NH, tw);
-  pack_rows<T, N>(B);
-  zfft<T, N, true>(B, tw);
+  zfft_inv_packed<T, N>(B, tw);
   constexpr int ITEMS = P::NR * N;   // item (r, z): real rows 2r, 2r+1 at column z
   if constexpr (MODE == C2R_STORE) {
     T* dst = out + (long long)s * out_stride + (long long)ix * N * N;
@@ -500,17 +496,14 @@ k_plane_c2r(const cplx<T>* __restrict__ in, long long in_stride, T* __restrict__
         if (fuse_next) B[r * ZP + z] = C{nv[0], nv[1]};   // the drifted field replaces g in the buffer
       }
     }
-    double acc_w = aw.value(), acc_p = ap.value();
-    // deterministic block reduction: warp shuffles, then thread 0 in order
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      acc_w += __shfl_down_sync(0xffffffffu, acc_w, o);
-      acc_p += __shfl_down_sync(0xffffffffu, acc_p, o);
-    }
+    // deterministic block reduction: a fixed shuffle tree per warp, then
+    // thread 0 over the warps in order
+    aw.warp_reduce();
+    ap.warp_reduce();
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     if (lane == 0) {
-      red[0][wid] = acc_w;
-      red[1][wid] = acc_p;
+      red[0][wid] = aw.value();
+      red[1][wid] = ap.value();
     }
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -525,7 +518,6 @@ k_plane_c2r(const cplx<T>* __restrict__ in, long long in_stride, T* __restrict__
     if (fuse_next) {
       // forward plane transform of the drifted field for the next evaluation
       zfft<T, N, false>(B, tw);
-      unpack_rows<T, N>(B);
       yfft_fwd_store<T, N>(B, next + (long long)s * next_stride + (long long)ix * N * P::NH, tw);
     }
   }
@@ -551,14 +543,17 @@ template <typename T> struct PencilMinB { static constexpr int v = sizeof(T) == 
 
 // Stage 1 of the x transform for group (t, m), operands read from global
 // memory (zero for a column past the end), result to the component buffer.
+// rows: bit j set when row m + M j is to be read (else it is zero).
 template <typename T, int N, bool INV, int W>
 __device__ __forceinline__ void px_s1_global(cplx<T>* buf, const cplx<T>* __restrict__ src, long long col,
-                                             bool ok, int t, int m, const cplx<T>* __restrict__ tw) {
+                                             bool ok, int t, int m, const cplx<T>* __restrict__ tw,
+                                             unsigned rows) {
   using C = cplx<T>;
   constexpr int R1 = Radix<N>::R1, M = Radix<N>::M, NCOL = N * (N / 2 + 1);
   C a[R1];
 #pragma unroll
-  for (int j = 0; j < R1; ++j) a[j] = ok ? __ldg(&src[(long long)(m + M * j) * NCOL + col]) : C{(T)0, (T)0};
+  for (int j = 0; j < R1; ++j)
+    a[j] = (ok && ((rows >> j) & 1u)) ? __ldg(&src[(long long)(m + M * j) * NCOL + col]) : C{(T)0, (T)0};
   stage1_group<T, N, INV>(a, m, tw);
 #pragma unroll
   for (int k2 = 0; k2 < R1; ++k2) buf[(m + M * k2) * W + t] = a[k2];
@@ -636,12 +631,39 @@ template <int N> __device__ __forceinline__ ColGeom<N> col_geom(long long col) {
   return g;
 }
 
+// PM_ADJ reads the x-planes of the three scatter spectra whose planes carry
+// points; plane_off (the per-chain bucket offsets of the points, ksplit
+// sub-buckets per plane, as the scatter plane pass used them) says which:
+// plane x is nonzero when bucket x or x-1 is non-empty.  plane_off ==
+// nullptr reads every plane.
 template <typename T, int N, int MODE>
 __global__ void __launch_bounds__(kPencilNT, PencilMinB<T>::v)
 k_pencil(const cplx<T>* __restrict__ in, long long in_stride, cplx<T>* __restrict__ out,
-         long long out_stride, const cplx<T>* __restrict__ tw, const T* __restrict__ amp) {
+         long long out_stride, const cplx<T>* __restrict__ tw, const T* __restrict__ amp,
+         const int* __restrict__ plane_off, int ksplit) {
   pdl_wait();
   pdl_trigger();
+  // x-planes to read, one bit per plane, kept in registers (PM_ADJ only)
+  constexpr int NW = N >= 32 ? N / 32 : 1;
+  unsigned occw[NW];
+#pragma unroll
+  for (int k = 0; k < NW; ++k) occw[k] = 0xffffffffu;
+  if constexpr (MODE == PM_ADJ) {
+    __shared__ unsigned occ_s[NW];
+    if (plane_off != nullptr) {
+      const int* o = plane_off + (long long)blockIdx.y * (N * ksplit + 1);
+      const int lane = threadIdx.x & 31;
+      for (int x0 = (threadIdx.x >> 5) * 32; x0 < N; x0 += kPencilNT) {
+        const int x = x0 + lane, xm = (x + N - 1) & (N - 1);
+        const bool on = x < N && ((o[(x + 1) * ksplit] != o[x * ksplit]) || (o[(xm + 1) * ksplit] != o[xm * ksplit]));
+        const unsigned word = __ballot_sync(0xffffffffu, on);
+        if (lane == 0) occ_s[x0 >> 5] = word;
+      }
+      __syncthreads();
+#pragma unroll
+      for (int k = 0; k < NW; ++k) occw[k] = occ_s[k];
+    }
+  }
   using C = cplx<T>;
   constexpr int R1 = Radix<N>::R1, M = Radix<N>::M;
   constexpr int NCOL = N * (N / 2 + 1);
@@ -658,8 +680,16 @@ k_pencil(const cplx<T>* __restrict__ in, long long in_stride, cplx<T>* __restric
   for (int g = threadIdx.x; g < NIN * kTC * M; g += kPencilNT) {
     const int t = g % kTC, m = (g / kTC) % M, j = g / (kTC * M);
     const long long col = c0 + t;
+    // rows m + M jj of this group: word (M jj) / 32, bit m + (M jj) % 32
+    // (M divides 32 and m < M)
+    unsigned rows = 0xffffffffu;
+    if constexpr (MODE == PM_ADJ) {
+      rows = 0;
+#pragma unroll
+      for (int jj = 0; jj < R1; ++jj) rows |= ((occw[(M * jj) >> 5] >> (m + ((M * jj) & 31))) & 1u) << jj;
+    }
     px_s1_global<T, N, INV1, W>(buf + j * kTC, in + (long long)(s * NIN + j) * in_stride, col, col < NCOL, t, m,
-                                tw);
+                                tw, rows);
   }
   __syncthreads();
   if constexpr (MODE == PM_FWD || MODE == PM_INV) {
@@ -754,14 +784,15 @@ static cudaError_t plane_c2r_t(const void* in, long long in_stride, void* out, l
 
 template <typename T, int N, int MODE>
 static cudaError_t pencil_t(const void* in, long long in_stride, void* out, long long out_stride,
-                            int count, const void* tw, const void* amp, cudaStream_t st) {
+                            int count, const void* tw, const void* amp, cudaStream_t st,
+                            const int* plane_off = nullptr, int ksplit = 1) {
   constexpr int NH = N / 2 + 1;
   constexpr int NCOMP = (MODE == PM_VEL || MODE == PM_ADJ) ? 3 : 1;
   constexpr size_t sm = sizeof(cplx<T>) * N * NCOMP * kTC;
   dim3 grid((N * NH + kTC - 1) / kTC, count);
   return launch_k(k_pencil<T, N, MODE>, grid, dim3(kPencilNT), sm, st, static_cast<const cplx<T>*>(in), in_stride,
                   static_cast<cplx<T>*>(out), out_stride, static_cast<const cplx<T>*>(tw),
-                  static_cast<const T*>(amp));
+                  static_cast<const T*>(amp), plane_off, ksplit);
 }
 
 // Supported grids: N in {8, 16, 32, 64, 128} at both precisions (one x-plane
@@ -883,20 +914,22 @@ cudaError_t launch_plane_c2r_gather(int prec, int N, const void* in, long long i
 template <typename T, int N>
 static cudaError_t pencil_mode(int mode, const void* in, long long in_stride, void* out,
                                long long out_stride, int count, const void* tw, const void* amp,
-                               cudaStream_t st) {
+                               cudaStream_t st, const int* plane_off) {
   switch (mode) {
     case PM_FWD: return pencil_t<T, N, PM_FWD>(in, in_stride, out, out_stride, count, tw, amp, st);
     case PM_INV: return pencil_t<T, N, PM_INV>(in, in_stride, out, out_stride, count, tw, amp, st);
     case PM_VEL: return pencil_t<T, N, PM_VEL>(in, in_stride, out, out_stride, count, tw, amp, st);
-    case PM_ADJ: return pencil_t<T, N, PM_ADJ>(in, in_stride, out, out_stride, count, tw, amp, st);
+    case PM_ADJ:
+      return pencil_t<T, N, PM_ADJ>(in, in_stride, out, out_stride, count, tw, amp, st, plane_off, plane_split(N));
   }
   return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_pencil(int prec, int N, int mode, const void* in, long long in_stride, void* out,
                           long long out_stride, int count, const void* tw, const void* amp,
-                          cudaStream_t st) {
-  HM_DISPATCH_PENCIL(prec, N, (pencil_mode<T, NN>(mode, in, in_stride, out, out_stride, count, tw, amp, st)));
+                          cudaStream_t st, const int* plane_off) {
+  HM_DISPATCH_PENCIL(prec, N, (pencil_mode<T, NN>(mode, in, in_stride, out, out_stride, count, tw, amp, st,
+                                                  plane_off)));
 }
 
 }  // namespace hm

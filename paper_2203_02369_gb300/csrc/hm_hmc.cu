@@ -130,8 +130,15 @@ k_traj_begin_field(long long n3, T* __restrict__ w, T* __restrict__ pw, const T*
       w[e + h] = wi + eps * ph;
     }
   }
-  const double s = block_sum2<T>(kin.value(), red);
-  if (threadIdx.x == 0) kin_part[(long long)c * gridDim.x + blockIdx.x] = s;
+  kin.warp_reduce();
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) red[wid] = kin.value();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int i = 0; i < kEwNT / 32; ++i) s += red[i];
+    kin_part[(long long)c * gridDim.x + blockIdx.x] = s;
+  }
 }
 
 // Trajectory start, distance part: p_d ~ N(0, (H0/sigma_v)^2).

@@ -165,9 +165,12 @@ cudaError_t launch_plane_c2r(int prec, int N, const void* in, long long in_strid
 cudaError_t launch_plane_c2r_gather(int prec, int N, const void* in, long long in_stride,
                                     const PlanePoints& pts, int count, const void* tw, cudaStream_t st);
 // x-axis pass over count chains.  PM_VEL: 1 spectrum -> 3; PM_ADJ: 3 -> 1.
+// For PM_ADJ, plane_off (the chains' point-bucket offsets, [count][N*K+1])
+// marks the x-planes that the scatter plane pass left unwritten because no
+// point touches them; they are read as zero.  nullptr reads every plane.
 cudaError_t launch_pencil(int prec, int N, int mode, const void* in, long long in_stride, void* out,
                           long long out_stride, int count, const void* tw, const void* amp,
-                          cudaStream_t st);
+                          cudaStream_t st, const int* plane_off = nullptr);
 bool fft_supported(int prec, int N);
 // N = 256 plane passes (thread-block clusters, FP32): pts == nullptr loads
 // real grids, else scatters the bucketed residuals; mode is C2R_STORE (0),
