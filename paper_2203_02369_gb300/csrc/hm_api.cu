@@ -317,7 +317,7 @@ static PointArrays point_arrays(hm_state* s) {
   pa.ry = s->ry.as<double>();
   pa.rz = s->rz.as<double>();
   pa.mu = s->mu.as<double>();
-  pa.smu = s->smu.as<double>();
+  pa.ismu2 = s->smu.as<double>();
   pa.zobs = s->zobs.as<double>();
   pa.scz = s->scz.as<double>();
   pa.d = s->d.as<double>();
@@ -331,9 +331,12 @@ static PointParams point_params(const hm_problem* p, long long off) {
   PointParams P{};
   for (int j = 0; j < 3; ++j) P.obs[j] = p->obs[j];
   P.delta = p->delta;
+  P.inv_delta = 1.0 / p->delta;
   P.omega_m = p->desc.omega_m;
   P.h = p->desc.h;
   P.sigma_nl2 = p->desc.sigma_nl * p->desc.sigma_nl;
+  P.ik2_nl = 1.0 / P.sigma_nl2;
+  P.logk2_nl = std::log(P.sigma_nl2);
   P.minv_d = p->minv_d;
   P.N = p->N;
   P.ksplit = plane_split(p->N);
@@ -607,7 +610,9 @@ int hm_set_catalog(hm_problem* p, int64_t n, const double* rhat, const double* m
   HM_TRY(upload(p->ry, ry.data(), n));
   HM_TRY(upload(p->rz, rz.data(), n));
   HM_TRY(upload(p->mu, mu, n));
-  HM_TRY(upload(p->smu, smu, n));
+  std::vector<double> ismu2(n);
+  for (long long i = 0; i < n; ++i) ismu2[i] = 1.0 / (smu[i] * smu[i]);
+  HM_TRY(upload(p->smu, ismu2.data(), n));   // the device keeps 1/sigma_mu^2
   HM_TRY(upload(p->zobs, z.data(), n));
   HM_TRY(upload(p->scz, sc.data(), n));
   p->n = n;
@@ -651,7 +656,7 @@ int hm_logpost_grad(hm_problem* p, const void* w_dev, const double* d_dev, doubl
   pa.ry = p->ry.as<double>();
   pa.rz = p->rz.as<double>();
   pa.mu = p->mu.as<double>();
-  pa.smu = p->smu.as<double>();
+  pa.ismu2 = p->smu.as<double>();
   pa.zobs = p->zobs.as<double>();
   pa.scz = p->scz.as<double>();
   pa.d = const_cast<double*>(d_dev);
@@ -1407,7 +1412,7 @@ extern "C" int hm_logpost_grad_noalloc(hm_problem* p, const void* w_dev, const d
   pa.ry = p->ry.as<double>();
   pa.rz = p->rz.as<double>();
   pa.mu = p->mu.as<double>();
-  pa.smu = p->smu.as<double>();
+  pa.ismu2 = p->smu.as<double>();
   pa.zobs = p->zobs.as<double>();
   pa.scz = p->scz.as<double>();
   pa.d = const_cast<double*>(d_dev);

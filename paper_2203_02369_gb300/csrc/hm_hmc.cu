@@ -38,6 +38,30 @@ __device__ __forceinline__ uint2 key_of(unsigned long long seed) {
   return make_uint2((unsigned)(seed & 0xffffffffull), (unsigned)(seed >> 32));
 }
 
+// k * 2^-53 rounded to the nearest float (ties to even) for 0 <= k <= 2^53,
+// with integer operations only: the same value as (float)(k * 2^-53) formed
+// in double, without using the FP64 units.
+__device__ __forceinline__ float u53_float(unsigned long long k) {
+  if (k == 0) return 0.f;
+  const int nb = 64 - __clzll((long long)k);   // bit length, 1..54
+  unsigned long long m = k;
+  int sh = 0;
+  if (nb > 24) {
+    sh = nb - 24;
+    m = k >> sh;
+    const unsigned long long rem = k & ((1ull << sh) - 1), half = 1ull << (sh - 1);
+    if (rem > half || (rem == half && (m & 1ull))) {
+      ++m;
+      if (m == (1ull << 24)) {
+        m >>= 1;
+        ++sh;
+      }
+    }
+  }
+  // m < 2^24 converts exactly; 2^(sh - 53) is a normal float for sh <= 30
+  return (float)(unsigned)m * __int_as_float((sh - 53 + 127) << 23);
+}
+
 // Two standard normals from counter (pair, traj, chain, tag): Box-Muller on
 // u1 = words (0,1), u2 = words (2,3); radius sqrt(-2 ln(1-u1)), angle 2 pi u2.
 __device__ __forceinline__ void normal_pair(unsigned long long seed, unsigned pair, unsigned traj,
@@ -64,8 +88,10 @@ __device__ __forceinline__ void normal_pair_t(unsigned long long seed, unsigned 
     n1 = b;
   } else {
     const uint4 x = philox4x32_10(make_uint4(pair, traj, chain, tag), key_of(seed));
-    const float om = (float)(1.0 - u53(x.x, x.y));
-    const float u2 = (float)u53(x.z, x.w);
+    const unsigned long long k1 = ((unsigned long long)(x.x >> 5) << 26) + (x.y >> 6);
+    const unsigned long long k2 = ((unsigned long long)(x.z >> 5) << 26) + (x.w >> 6);
+    const float om = u53_float((1ull << 53) - k1);   // (float)(1 - u53), exactly
+    const float u2 = u53_float(k2);                  // (float)u53, exactly
     const float r = sqrtf(-2.0f * logf(om));
     float s, c;
     sincospif(2.0f * u2, &s, &c);

@@ -45,8 +45,10 @@ int plane_split(int N);
 struct PointParams {
   double obs[3];
   double delta;          // grid spacing L/N
+  double inv_delta;      // 1/delta (rounded once, on the host)
   double omega_m, h;
   double sigma_nl2;      // sigma_NL^2
+  double ik2_nl, logk2_nl;  // 1/sigma_NL^2 and ln sigma_NL^2 (kappa^2 of a point with sigma_cz = 0)
   double minv_d;         // (sigma_v/H0)^2, inverse mass of a distance
   int N;
   int prior_kind;
@@ -118,7 +120,7 @@ struct PointArrays {
   const double* ry;
   const double* rz;
   const double* mu;
-  const double* smu;
+  const double* ismu2;   // 1 / sigma_mu^2 per point
   const double* zobs;
   const double* scz;
   double* d;

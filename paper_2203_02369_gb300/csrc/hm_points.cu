@@ -13,9 +13,9 @@ constexpr int kPtsNT = 128;
 
 __device__ __forceinline__ CellPos cell_of(const PointParams& P, double d, double rx, double ry, double rz) {
   CellPos c;
-  cell_axis(P.obs[0], d, rx, P.delta, P.N, c.ix, c.fx);
-  cell_axis(P.obs[1], d, ry, P.delta, P.N, c.iy, c.fy);
-  cell_axis(P.obs[2], d, rz, P.delta, P.N, c.iz, c.fz);
+  cell_axis(P.obs[0], d, rx, P.delta, P.inv_delta, P.N, c.ix, c.fx);
+  cell_axis(P.obs[1], d, ry, P.delta, P.inv_delta, P.N, c.iy, c.fy);
+  cell_axis(P.obs[2], d, rz, P.delta, P.inv_delta, P.N, c.iz, c.fz);
   return c;
 }
 
@@ -180,15 +180,24 @@ k_points_place(const PointParams* __restrict__ pp, PointArrays pa, ChainScal* __
   const double mup = (5.0 / 2.302585092994045684) * (1.0 / d + zbp * iopz);
   const double z = pa.zobs[i];
   const double scz = pa.scz[i];
-  const double scz2 = scz * scz;
-  const double snl2 = cs[c].sample_sig ? cs[c].sig * cs[c].sig : P.sigma_nl2;
-  const double k2 = snl2 + scz2 * iopz * iopz;
-  const double ik2 = 1.0 / k2;
-  const double k2p = -2.0 * scz2 * zbp * iopz * iopz * iopz;
-  const double smu = pa.smu[i];
-  const double ismu2 = 1.0 / (smu * smu);
+  // kappa^2 = sigma_NL^2 + sigma_cz^2 / (1 + zbar)^2 (eq. kappa); with
+  // sigma_cz = 0 and a fixed sigma_NL it is a per-chain constant
+  double ik2, lk2, k2p;
+  if (scz == 0.0 && !cs[c].sample_sig) {
+    ik2 = P.ik2_nl;
+    lk2 = P.logk2_nl;
+    k2p = 0.0;
+  } else {
+    const double scz2 = scz * scz;
+    const double snl2 = cs[c].sample_sig ? cs[c].sig * cs[c].sig : P.sigma_nl2;
+    const double k2 = snl2 + scz2 * iopz * iopz;
+    ik2 = 1.0 / k2;
+    lk2 = log(k2);
+    k2p = -2.0 * scz2 * zbp * iopz * iopz * iopz;
+  }
+  const double ismu2 = pa.ismu2[i];
   const double res_mu = pa.mu[i] - mu_d;
-  pa.lk[i] = 0.5 * res_mu * res_mu * ismu2 + 0.5 * log(k2) - lp;
+  pa.lk[i] = 0.5 * res_mu * res_mu * ismu2 + 0.5 * lk2 - lp;
   pa.lk[nt + i] = -res_mu * mup * ismu2 + 0.5 * k2p * ik2 - dlp;
   pa.lk[2 * nt + i] = kC * (z - zb) * iopz;
   pa.lk[3 * nt + i] = -kC * zbp * (1.0 + z) * iopz * iopz;
@@ -227,11 +236,26 @@ k_points_lik(const PointParams* __restrict__ pp, PointArrays pa, double* __restr
       gd = 0.0;
     } else {
       const T* part = static_cast<const T*>(pa.part);
-      double u = 0.0, du = 0.0;
+      double u, du;
+      if constexpr (sizeof(T) == 4) {
+        // the six FP32 partials summed with TwoSum (error-free FP32 pairs), so
+        // the FP64 result equals their exact sum to ~1e-14 without FP64 adds
+        HalfSqAcc<float> su, sdu;
 #pragma unroll
-      for (int k = 0; k < 6; ++k) {
-        u += (double)part[(long long)k * nt + pos];
-        du += (double)part[(long long)(6 + k) * nt + pos];
+        for (int k = 0; k < 6; ++k) {
+          su.add((float)part[(long long)k * nt + pos]);
+          sdu.add((float)part[(long long)(6 + k) * nt + pos]);
+        }
+        u = su.value();
+        du = sdu.value();
+      } else {
+        u = 0.0;
+        du = 0.0;
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+          u += (double)part[(long long)k * nt + pos];
+          du += (double)part[(long long)(6 + k) * nt + pos];
+        }
       }
       const double vo = pa.lk[2 * nt + i], vop = pa.lk[3 * nt + i];
       const double ik2 = pa.lk[4 * nt + i], k2p = pa.lk[5 * nt + i];
