@@ -54,6 +54,8 @@ def parse():
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--batched-only", action="store_true", help="run only the 32-chain batched measurement")
     ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--accept-target", type=float, default=0.70,
+                    help="acceptance the batched and served chains' step sizes are tuned to (dual averaging)")
     ap.add_argument("--tune-eps", action="store_true", help="print acceptance for a sweep of eps and exit")
     return ap.parse_args()
 
@@ -283,12 +285,18 @@ def run_batched(args, eps, L, use_graph):
     stream = torch.cuda.current_stream()
     for _, s in states:
         s.run_chain(max(args.warmup, 3), L, eps, use_graph=use_graph, trace=False)
+    # each chain's step tuned to the plain chain's acceptance (dual averaging),
+    # so that both forms are compared at equal acceptance
+    eps_c = {}
+    for N, s in states:
+        e, _ = s.adapt_step_size(40, L, eps, target=args.accept_target)
+        eps_c[N] = e
     torch.cuda.synchronize()
     K = max(4, args.steps // 5)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    for _, s in states:
-        s.run_chain(K, L, eps, use_graph=use_graph, trace=False)
+    for N, s in states:
+        s.run_chain(K, L, eps_c[N], use_graph=use_graph, trace=False)
     e1.record(stream)
     torch.cuda.synchronize()
     secs = e0.elapsed_time(e1) / 1e3
@@ -296,11 +304,11 @@ def run_batched(args, eps, L, use_graph):
     # per-kernel times of the 128^3 state alone (events inside its graph)
     s128 = states[0][1]
     s128.profile(True)
-    s128.run_chain(1, L, eps, use_graph=use_graph, trace=False)
+    s128.run_chain(1, L, eps_c[128], use_graph=use_graph, trace=False)
     torch.cuda.synchronize()
     s128.profile(True)
     for _ in range(5):
-        s128.run_chain(1, L, eps, use_graph=use_graph, trace=False)
+        s128.run_chain(1, L, eps_c[128], use_graph=use_graph, trace=False)
         torch.cuda.synchronize()
         s128.profile_collect()
     prof = s128.profile_read()
@@ -309,7 +317,7 @@ def run_batched(args, eps, L, use_graph):
     M = 60
     e2, e3 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e2.record(stream)
-    traces = [s.run_chain(M, L, eps, use_graph=use_graph, trace=True) for _, s in states]
+    traces = [s.run_chain(M, L, eps_c[N], use_graph=use_graph, trace=True) for N, s in states]
     e3.record(stream)
     torch.cuda.synchronize()
     msecs = e2.elapsed_time(e3) / 1e3
@@ -328,6 +336,8 @@ def run_batched(args, eps, L, use_graph):
     # points per chain differ: the 128^3 roofline uses the bytes of the grid terms only
     ach = ab[dname] / (dms / dl / 1e3) / 1e9 if dl else None
     out = {"chains": nch, "chains_128": n128, "chains_64": nch - n128, "trajectories_timed": K,
+           "eps_tuning": {"method": "dual averaging, 40 trajectories per chain", "target_accept": args.accept_target,
+                          "eps_128_median": float(np.median(eps_c[128])), "eps_64_median": float(np.median(eps_c[64]))},
            "grad_evals_per_s": evals_per_s, "ms_per_trajectory_all_chains": 1e3 * secs / K,
            "ess_psi_sum": ess_tot, "ess_per_s": ess_tot / msecs, "ess_trajectories": M, "accept_rate": acc,
            "kernels_128": kern,
@@ -348,20 +358,23 @@ def run_batched(args, eps, L, use_graph):
     return out
 
 
-def run_serving(eps, L):
+def run_serving(eps, L, target):
     """Poisson stream of reconstruction jobs (64^3 / 128^3 at 500 Mpc/h,
     256^3 at 1000 Mpc/h; 1e3-1e5 points), all arriving within a fraction of
     a second so that the GPU is saturated; served with 4 slots (continuous
     batching) and, for reference, the same jobs one at a time."""
     from paper_2203_02369_gb300.serve import ServingLoop, poisson_jobs
     def jobs():
-        return poisson_jobs(12, rate_per_s=40.0, seed=7, n_traj=12, grids=(64, 128, 256), eps=eps)
+        return poisson_jobs(12, rate_per_s=40.0, seed=7, n_traj=12, grids=(64, 128, 256), eps=eps,
+                            adapt_warmup=8, accept_target=target)
     served = ServingLoop(max_slots=4).run(jobs())
     plain = ServingLoop(max_slots=1).run(jobs())
     served["plain_one_at_a_time"] = {k: plain[k] for k in ("makespan_s", "grad_evals_per_s", "ess_per_s",
                                                            "trajectory_latency_ms", "job_latency_s")}
     served["speedup_vs_plain_evals"] = served["grad_evals_per_s"] / plain["grad_evals_per_s"]
-    served["workload"] = "12 jobs, Poisson arrivals at 40/s, grids 64/128/256, 1e3-1e5 points, 12 trajectories x 20 steps each"
+    served["workload"] = ("12 jobs, Poisson arrivals at 40/s, grids 64/128/256, 1e3-1e5 points; each job tunes "
+                          f"its step by dual averaging (8 trajectories, target acceptance {target}) and then runs "
+                          "12 trajectories x 20 steps (the timed ones)")
     return served
 
 
@@ -565,7 +578,7 @@ def main():
 
     serving = None
     if not args.no_serve and ws == 1:
-        serving = run_serving(args.eps, L)
+        serving = run_serving(args.eps, L, args.accept_target)
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,

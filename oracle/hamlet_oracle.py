@@ -818,3 +818,83 @@ def problem_from_catalog(spec_N, spec_L, cosmo, sigma_nl, cat, prior=None):
         prior = ("table", cat["prior_d0"], cat["prior_bin"], cat["prior_logdens"])
     return Problem(spec_N, spec_L, cosmo, sigma_nl, cat["rhat"], cat["mu"], cat["sigma_mu"],
                    cat["cz"], cat["sigma_cz"], prior)
+
+
+# ----------------------------------------------------------------------------
+# Chain analytics: Monte-Carlo means over chain states (eq. int_mc), the
+# convergence monitor (section "Convergence") and the monopole and dipole of
+# the velocity field in spheres about the observer (section "Monopole and
+# dipole").
+# ----------------------------------------------------------------------------
+def density_field(prob, w):
+    """delta(x) = IDFT(sqrt(P/Delta^3) DFT(w)): the coloured field."""
+    return np.fft.ifftn(delta_k(prob, w)).real
+
+
+def node_offsets(prob):
+    """Offsets x - o of the grid nodes (positions i*Delta) from the observer,
+    shape (3, N, N, N), and their lengths (no periodic wrap)."""
+    i = np.arange(prob.N) * prob.delta
+    gx, gy, gz = np.meshgrid(i, i, i, indexing="ij")
+    off = np.stack([gx - prob.observer[0], gy - prob.observer[1], gz - prob.observer[2]])
+    r = np.sqrt(off[0] * off[0] + off[1] * off[1] + off[2] * off[2])
+    return off, r
+
+
+def radial_velocity(prob, v):
+    """v_r = rhat . v at every node, rhat the unit vector from the observer
+    (v_r = 0 at a node on the observer)."""
+    off, r = node_offsets(prob)
+    safe = np.where(r > 0, r, 1.0)
+    return np.where(r > 0, (off[0] * v[0] + off[1] * v[1] + off[2] * v[2]) / safe, 0.0)
+
+
+def sample_moments(samples):
+    """eq. int_mc: mean of a functional over the n chain states, and the
+    sample variance (divisor n - 1; zero for one state)."""
+    a = np.stack([np.asarray(x, float) for x in samples])
+    n = a.shape[0]
+    mean = a.sum(axis=0) / n
+    var = ((a - mean) ** 2).sum(axis=0) / (n - 1) if n > 1 else np.zeros_like(mean)
+    return mean, var
+
+
+def convergence_metric(delta_samples):
+    """Section "Convergence": the change of <delta>/Sigma_delta between
+    successive steps.  m_s = mean of the first s density fields (eq. int_mc),
+    Sigma_s^2 = variance over the grid of the s-th field; the field
+    m_s/Sigma_s - m_{s-1}/Sigma_{s-1} is summarised by its root mean square
+    over the nodes.  Returns the values for s = 2..n (n - 1 of them)."""
+    out = []
+    m_prev = None
+    s_prev = None
+    acc = None
+    for s, x in enumerate(delta_samples, start=1):
+        x = np.asarray(x, float)
+        acc = x.copy() if acc is None else acc + x
+        m = acc / s
+        sig = math.sqrt(float(np.mean(x * x)) - float(np.mean(x)) ** 2)
+        if m_prev is not None:
+            out.append(math.sqrt(float(np.mean((m / sig - m_prev / s_prev) ** 2))))
+        m_prev, s_prev = m, sig
+    return np.array(out)
+
+
+def sphere_moments(prob, delta, v, radii):
+    """Section "Monopole and dipole" in spheres |x - o| <= R about the
+    observer, over the grid nodes inside: the monopole is the mean of
+    -div v / H0, which by linear continuity (div v = -aHf delta, exact per mode
+    away from the Nyquist planes) is a f <delta>; the dipole is the mean
+    velocity (bulk flow) V.  Returns (R, 5): monopole, V_x, V_y, V_z, |V|."""
+    _, r = node_offsets(prob)
+    out = np.zeros((len(radii), 5))
+    for k, R in enumerate(radii):
+        m = r <= R
+        cnt = int(m.sum())
+        if cnt == 0:
+            continue
+        V = np.array([v[j][m].sum() / cnt for j in range(3)])
+        out[k, 0] = 1.0 * prob.f * delta[m].sum() / cnt
+        out[k, 1:4] = V
+        out[k, 4] = math.sqrt(float(V @ V))
+    return out

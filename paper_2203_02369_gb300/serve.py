@@ -33,12 +33,15 @@ class Job:
     eps: float = 0.025
     seed: int = 0
     arrival: float = 0.0            # seconds after the start of the run
+    adapt_warmup: int = 0           # dual-averaging warm-up trajectories before the timed ones
+    accept_target: float = 0.70
     # filled in by the loop
     admitted: float = float("nan")
     finished: float = float("nan")
     traj_latency: list = field(default_factory=list)
     psi: list = field(default_factory=list)
     accept: list = field(default_factory=list)
+    eps_used: float = float("nan")
     final_w: object = None
     final_d: object = None
     error: str = ""
@@ -89,9 +92,15 @@ class ServingLoop:
             cat = mock.make_catalog(job.spec)
             prob = Problem.from_mock(job.spec, cat, device=self.device)
             st = State(prob, [cat["d_init"]], seed=job.seed, chain_ids=[job.job_id])
+            eps = job.eps
+            if job.adapt_warmup > 0:
+                # the job's own step size, tuned to the target acceptance
+                e, _ = st.adapt_step_size(job.adapt_warmup, job.n_leapfrog, job.eps, target=job.accept_target)
+                eps = float(e[0])
+            job.eps_used = eps
             for _ in range(job.n_traj):
                 a = time.perf_counter()
-                tr = st.run_chain(1, job.n_leapfrog, job.eps, use_graph=self.use_graph, trace=True)
+                tr = st.run_chain(1, job.n_leapfrog, eps, use_graph=self.use_graph, trace=True)
                 job.traj_latency.append(time.perf_counter() - a)
                 job.psi.append(float(tr[0, 0]["psi"]))
                 job.accept.append(int(tr[0, 0]["accept"]))
@@ -169,7 +178,8 @@ def summarize(jobs, makespan):
     }
 
 
-def poisson_jobs(n_jobs, rate_per_s, seed=7, n_traj=30, grids=(64, 128), n_range=(1e3, 1e5), eps=0.025):
+def poisson_jobs(n_jobs, rate_per_s, seed=7, n_traj=30, grids=(64, 128), n_range=(1e3, 1e5), eps=0.025,
+                 adapt_warmup=0, accept_target=0.70):
     """Synthetic arrival stream: Poisson arrivals, grid 64^3 or 128^3 (box
     500 Mpc/h) or 256^3 (box 1000 Mpc/h), catalogue sizes log-uniform in
     n_range."""
@@ -182,5 +192,6 @@ def poisson_jobs(n_jobs, rate_per_s, seed=7, n_traj=30, grids=(64, 128), n_range
         n = int(round(np.exp(rng.uniform(np.log(n_range[0]), np.log(n_range[1])))))
         spec = mock.MockSpec(N=N, L=1000.0 if N == 256 else 500.0, n_points=n, r_max=160.0, mask_deg=10.0,
                              sigma_mu=(0.2, 0.45), sigma_nl=250.0, seed=1000 + k)
-        jobs.append(Job(job_id=k, spec=spec, n_traj=n_traj, seed=seed, arrival=t, eps=eps))
+        jobs.append(Job(job_id=k, spec=spec, n_traj=n_traj, seed=seed, arrival=t, eps=eps,
+                        adapt_warmup=adapt_warmup, accept_target=accept_target))
     return jobs
