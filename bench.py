@@ -283,13 +283,14 @@ def run_batched(args, eps, L, use_graph):
     nch = sum(s.C for _, s in states)
     mbytes = sum(4 * model_bytes(specs[i].N, specs[i].n_points) for i in range(len(specs)))  # 4 chains each
     stream = torch.cuda.current_stream()
+    # burn-in at a small step (the chains start at w = 0), then each chain's
+    # step tuned to the plain chain's acceptance by dual averaging, so that
+    # both forms are compared at equal acceptance
     for _, s in states:
-        s.run_chain(max(args.warmup, 3), L, eps, use_graph=use_graph, trace=False)
-    # each chain's step tuned to the plain chain's acceptance (dual averaging),
-    # so that both forms are compared at equal acceptance
+        s.run_chain(60, L, 0.4 * eps, use_graph=use_graph, trace=False)
     eps_c = {}
     for N, s in states:
-        e, _ = s.adapt_step_size(40, L, eps, target=args.accept_target)
+        e, _ = s.adapt_step_size(150, L, eps, target=args.accept_target)
         eps_c[N] = e
     torch.cuda.synchronize()
     K = max(4, args.steps // 5)
@@ -336,7 +337,8 @@ def run_batched(args, eps, L, use_graph):
     # points per chain differ: the 128^3 roofline uses the bytes of the grid terms only
     ach = ab[dname] / (dms / dl / 1e3) / 1e9 if dl else None
     out = {"chains": nch, "chains_128": n128, "chains_64": nch - n128, "trajectories_timed": K,
-           "eps_tuning": {"method": "dual averaging, 40 trajectories per chain", "target_accept": args.accept_target,
+           "eps_tuning": {"method": "60 burn-in trajectories at 0.4 eps, then dual averaging over 150 trajectories per chain",
+                          "target_accept": args.accept_target,
                           "eps_128_median": float(np.median(eps_c[128])), "eps_64_median": float(np.median(eps_c[64]))},
            "grad_evals_per_s": evals_per_s, "ms_per_trajectory_all_chains": 1e3 * secs / K,
            "ess_psi_sum": ess_tot, "ess_per_s": ess_tot / msecs, "ess_trajectories": M, "accept_rate": acc,

@@ -235,6 +235,39 @@ int hm_adapt_step_size(hm_state* s, int32_t n_warmup, int32_t n_leapfrog, double
                        const double* eps0_host, int32_t sample_distances, double* eps_out_host,
                        hm_trace* trace_host, void* stream);
 
+/* Chain analytics on the device (eq. int_mc: Monte-Carlo means over chain
+ * states; section "Convergence": the convergence monitor; section "Monopole
+ * and dipole": velocity moments in spheres about the observer).  With
+ * enable != 0, every trajectory of hm_run_chain (not of hm_adapt_step_size)
+ * adds one sample per chain, the chain state after its Metropolis test:
+ *   - running mean and variance (divisor n - 1) at every grid node of the
+ *     density field delta = IDFT(sqrt(P/Delta^3) DFT(w)) and of the radial
+ *     velocity v_r = rhat . v (rhat from the observer to the node; 0 on it);
+ *   - for samples s >= 2, the root mean square over the nodes of
+ *     m_s/Sigma_s - m_{s-1}/Sigma_{s-1} (m_s the running mean of delta after s
+ *     samples, Sigma_s^2 the variance over the grid of sample s's delta), the
+ *     first max_samples values kept;
+ *   - in each sphere |x - o| <= radii_host[k] (n_radii <= 32, increasing,
+ *     nodes at x = i*Delta, no periodic wrap): the monopole a f <delta>
+ *     (= the mean of -div v/H0 by linear continuity, a = 1), the mean velocity
+ *     V (dipole) and |V|, with their mean and variance over samples.
+ * enable != 0 allocates and zeroes the accumulators (about 8 field-sized
+ * arrays per chain; HM_ENOMEM when they do not fit), enable = 0 frees them.
+ * Both synchronise the stream.  Errors: HM_EINVAL for bad radii or sizes. */
+int hm_state_analytics(hm_state* s, int32_t enable, int32_t n_radii, const double* radii_host,
+                       int32_t max_samples, void* stream);
+
+/* Read the analytics of one chain.  Device outputs (field precision, layout
+ * [x][y][z], may be NULL): mean and variance of delta and of v_r.  Host
+ * outputs (may be NULL): metric_host[0 .. min(n-1, max_samples, max_metric))
+ * the convergence values of samples 2, 3, ...; sphere_host[k][q][2] for the
+ * n_radii spheres and q = monopole, V_x, V_y, V_z, |V|: mean and variance over
+ * samples; *n_samples_out the sample count n.  Synchronises the stream.
+ * Errors: HM_ESTATE when analytics are off, HM_EINVAL for a bad chain. */
+int hm_state_analytics_read(hm_state* s, int32_t chain, void* mean_delta_dev, void* var_delta_dev,
+                            void* mean_vr_dev, void* var_vr_dev, double* metric_host, int32_t max_metric,
+                            double* sphere_host, int64_t* n_samples_out, void* stream);
+
 /* Per-kernel timing of hm_run_chain: with profiling enabled, every kernel
  * launch of a trajectory is bracketed by a pair of CUDA events on the
  * launching stream (recorded as graph nodes when the trajectory is

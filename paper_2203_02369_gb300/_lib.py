@@ -83,6 +83,9 @@ SIGNATURES = [
     ("hm_state_get_sigma_nl", ct.c_int, [_P, c_double_p, c_double_p, _P]),
     ("hm_adapt_step_size", ct.c_int, [_P, ct.c_int32, ct.c_int32, ct.c_double, c_double_p, ct.c_int32,
                                       c_double_p, ct.POINTER(hm_trace), _P]),
+    ("hm_state_analytics", ct.c_int, [_P, ct.c_int32, ct.c_int32, c_double_p, ct.c_int32, _P]),
+    ("hm_state_analytics_read", ct.c_int, [_P, ct.c_int32, _P, _P, _P, _P, c_double_p, ct.c_int32, c_double_p,
+                                           ct.POINTER(ct.c_int64), _P]),
     ("hm_state_profile", ct.c_int, [_P, ct.c_int32]),
     ("hm_state_profile_collect", ct.c_int, [_P]),
     ("hm_state_profile_read", ct.c_int, [_P, ct.c_int32, c_double_p, ct.POINTER(ct.c_int64),

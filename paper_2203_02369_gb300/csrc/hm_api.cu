@@ -18,12 +18,14 @@
 using namespace hm;
 
 namespace hm {
-bool pdl_enabled() {
-  static const bool on = [] {
+bool pdl_enabled(int cat) {
+  static const int mask = [] {
+    // default: the x pencils only (measured on the 128^3 trajectory: pencils
+    // 1.725 ms, none 1.750, plane passes 1.887, point kernels 2.047, all 2.312)
     const char* e = std::getenv("HM_PDL");
-    return e && e[0] == '1';
+    return e ? std::atoi(e) : (int)PDL_PENCIL;
   }();
-  return on;
+  return (mask & cat) != 0;
 }
 }  // namespace hm
 
@@ -267,7 +269,7 @@ struct hm_problem {
   double f = 0, aHf = 0, sigma_v = 0, minv_d = 0, pkA = 0;
   size_t rsz = 4;            // bytes of one real
   long long n3 = 0, nspec = 0;
-  DevBuf tw, amp, prior_logdens;
+  DevBuf tw, amp, ampd, prior_logdens;   // ampd: colouring sqrt(P/Delta^3)/N^3 per n^2
   std::vector<double> prior_host;
   // catalogue
   long long n = 0;
@@ -301,6 +303,14 @@ struct hm_state {
   int prof_pairs = 0;      // event pairs recorded by one trajectory
   int prof_pending = 0;    // pairs recorded by the last single-trajectory run, not yet read
   cudaStream_t prof_stream = nullptr;
+  // chain analytics (one sample per trajectory when on)
+  struct Analytics {
+    bool on = false;
+    int nsh = 0, max_samples = 0, nblk = 1;
+    std::vector<double> radii;
+    DevBuf delta_g, vel_g, mean_d, m2_d, mean_vr, m2_vr, shell, sph_cnt, sig_part, met_part, shell_part;
+    DevBuf sig_prev, sig_cur, count, hist, sph_acc, obs;
+  } an;
   // captured trajectory graph
   cudaStream_t gstream = nullptr;
   cudaGraphExec_t gexec = nullptr;
@@ -518,13 +528,14 @@ int hm_init_problem(const hm_problem_desc* desc, hm_problem** out) {
   // the 1/N^3 of the inverse DFT folded in
   const int N = d.N;
   const int nmax = 3 * (N / 2) * (N / 2);
-  std::vector<double> ampd(nmax + 1, 0.0);
+  std::vector<double> ampd(nmax + 1, 0.0), colour(nmax + 1, 0.0);
   const double kf = 2.0 * kPi / d.L;
   const double d3 = p->delta * p->delta * p->delta;
   const double n3d = (double)N * N * N;
   for (int n2 = 1; n2 <= nmax; ++n2) {
     const double k = kf * std::sqrt((double)n2);
     ampd[n2] = kf * p->aHf * std::sqrt(eh.pk(k) / d3) / (k * k * n3d);
+    colour[n2] = std::sqrt(eh.pk(k) / d3) / n3d;   // density field: delta = IDFT(sqrt(P/Delta^3) DFT(w))
   }
   std::vector<double> twd(2 * N);
   for (int e = 0; e < N; ++e) {
@@ -533,13 +544,18 @@ int hm_init_problem(const hm_problem_desc* desc, hm_problem** out) {
   }
   if (p->prec == HM_FP32) {
     std::vector<float> af(ampd.begin(), ampd.end()), tf(twd.begin(), twd.end());
+    std::vector<float> cf(colour.begin(), colour.end());
     HM_TRY(p->amp.alloc(af.size() * 4));
     HM_CUDA(cudaMemcpy(p->amp.p, af.data(), af.size() * 4, cudaMemcpyHostToDevice));
+    HM_TRY(p->ampd.alloc(cf.size() * 4));
+    HM_CUDA(cudaMemcpy(p->ampd.p, cf.data(), cf.size() * 4, cudaMemcpyHostToDevice));
     HM_TRY(p->tw.alloc(tf.size() * 4));
     HM_CUDA(cudaMemcpy(p->tw.p, tf.data(), tf.size() * 4, cudaMemcpyHostToDevice));
   } else {
     HM_TRY(p->amp.alloc(ampd.size() * 8));
     HM_CUDA(cudaMemcpy(p->amp.p, ampd.data(), ampd.size() * 8, cudaMemcpyHostToDevice));
+    HM_TRY(p->ampd.alloc(colour.size() * 8));
+    HM_CUDA(cudaMemcpy(p->ampd.p, colour.data(), colour.size() * 8, cudaMemcpyHostToDevice));
     HM_TRY(p->tw.alloc(twd.size() * 8));
     HM_CUDA(cudaMemcpy(p->tw.p, twd.data(), twd.size() * 8, cudaMemcpyHostToDevice));
   }
@@ -1113,8 +1129,12 @@ static int trajectory(hm_state* s, int n_leapfrog, cudaStream_t st, Prof* pf) {
   return HM_OK;
 }
 
+static int analytics_sample(hm_state* s, cudaStream_t st);
+
+// sample != 0: one chain-analytics sample after every trajectory (when on).
 static int run_traj_loop(hm_state* s, int32_t n_traj, int32_t n_leapfrog, int32_t sample_distances,
-                         int32_t use_graph, cudaStream_t st) {
+                         int32_t use_graph, cudaStream_t st, int sample = 0) {
+  const bool an = sample && s->an.on;
   Prof* pf = s->prof.get();
   if (pf) {
     HM_TRY(profile_collect(s));
@@ -1128,6 +1148,7 @@ static int run_traj_loop(hm_state* s, int32_t n_traj, int32_t n_leapfrog, int32_
     for (int t = 0; t < n_traj; ++t) {
       if (pf) pf->idx = 0;
       HM_TRY(trajectory(s, n_leapfrog, st, pf));
+      if (an) HM_TRY(analytics_sample(s, st));
       if (pf) {
         if (n_traj == 1) {
           s->prof_pending = pf->idx;
@@ -1170,6 +1191,7 @@ static int run_traj_loop(hm_state* s, int32_t n_traj, int32_t n_leapfrog, int32_
     HM_CUDA(cudaStreamWaitEvent(s->gstream, ev, 0));
     for (int t = 0; t < n_traj; ++t) {
       HM_CUDA(cudaGraphLaunch(s->gexec, s->gstream));
+      if (an) HM_TRY(analytics_sample(s, s->gstream));
       if (pf) {
         if (n_traj == 1) {
           s->prof_pending = s->prof_pairs;
@@ -1203,7 +1225,7 @@ int hm_run_chain(hm_state* s, int32_t n_traj, int32_t n_leapfrog, const double* 
     }
   }
   HM_TRY(set_run(s, eps_host, sample_distances, st));
-  HM_TRY(run_traj_loop(s, n_traj, n_leapfrog, sample_distances, use_graph, st));
+  HM_TRY(run_traj_loop(s, n_traj, n_leapfrog, sample_distances, use_graph, st, 1));
   if (trace_host && n_traj > 0) {
     HM_CUDA(cudaMemcpyAsync(trace_host, s->trace_dev.p, sizeof(hm_trace) * (size_t)n_traj * s->C,
                             cudaMemcpyDeviceToHost, st));
@@ -1272,6 +1294,199 @@ int hm_state_get_sigma_nl(hm_state* s, double* sigma_out_host, double* grad_out_
     sigma_out_host[c] = s->sample_sig ? cs[c].sig : s->chain_prob[c]->desc.sigma_nl;
     if (grad_out_host) grad_out_host[c] = s->sample_sig ? cs[c].g_sig : 0.0;
   }
+  return HM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Chain analytics (eq. int_mc; sections "Convergence", "Monopole and dipole")
+// ---------------------------------------------------------------------------
+static void analytics_release(hm_state::Analytics& A) {
+  DevBuf* bufs[] = {&A.delta_g, &A.vel_g, &A.mean_d, &A.m2_d, &A.mean_vr, &A.m2_vr, &A.shell, &A.sph_cnt,
+                    &A.sig_part, &A.met_part, &A.shell_part, &A.sig_prev, &A.sig_cur, &A.count, &A.hist,
+                    &A.sph_acc, &A.obs};
+  for (DevBuf* b : bufs) b->release();
+  A.on = false;
+  A.nsh = 0;
+  A.max_samples = 0;
+  A.radii.clear();
+}
+
+static AnArgs an_args(hm_state* s) {
+  hm_state::Analytics& A = s->an;
+  AnArgs a{};
+  a.C = s->C;
+  a.N = s->N;
+  a.nsh = A.nsh;
+  a.max_samples = A.max_samples;
+  a.nblk = A.nblk;
+  a.n3 = s->n3;
+  a.delta = s->p0->delta;
+  a.f = s->p0->f;
+  a.obs = A.obs.as<double>();
+  a.delta_g = A.delta_g.p;
+  a.vel_g = A.vel_g.p;
+  a.mean_d = A.mean_d.p;
+  a.m2_d = A.m2_d.p;
+  a.mean_vr = A.mean_vr.p;
+  a.m2_vr = A.m2_vr.p;
+  a.shell = A.shell.as<unsigned char>();
+  a.sph_cnt = A.sph_cnt.as<double>();
+  a.sig_part = A.sig_part.as<double>();
+  a.met_part = A.met_part.as<double>();
+  a.shell_part = A.shell_part.as<double>();
+  a.sig_prev = A.sig_prev.as<double>();
+  a.sig_cur = A.sig_cur.as<double>();
+  a.count = A.count.as<long long>();
+  a.hist = A.hist.as<double>();
+  a.sph_acc = A.sph_acc.as<double>();
+  return a;
+}
+
+// One sample of every chain from its current field w: forward plane pass,
+// x pass with the velocity weights (3 spectra per chain in S2) and with the
+// colouring (1 spectrum per chain after the first C spectra of S1), c2r to
+// the real grids, then the analytics kernels.  S1 and S2 are free between
+// trajectories (each trajectory starts from the plane pass of w).
+static int analytics_sample(hm_state* s, cudaStream_t st) {
+  hm_problem* p = s->p0;
+  hm_state::Analytics& A = s->an;
+  const size_t csz = 2 * s->rsz;
+  void* dspec = static_cast<char*>(s->S1.p) + (size_t)s->C * s->nspec * csz;
+  HM_CUDA(launch_plane_r2c(s->prec, s->N, s->w.p, s->n3, s->S1.p, s->nspec, s->C, p->tw.p, st));
+  HM_CUDA(launch_pencil(s->prec, s->N, PM_VEL, s->S1.p, s->nspec, s->S2.p, s->nspec, s->C, p->tw.p, p->amp.p, st));
+  HM_CUDA(launch_pencil(s->prec, s->N, PM_SCALE, s->S1.p, s->nspec, dspec, s->nspec, s->C, p->tw.p, p->ampd.p, st));
+  HM_CUDA(launch_plane_c2r(s->prec, s->N, s->S2.p, s->nspec, A.vel_g.p, s->n3, 3 * s->C, p->tw.p, nullptr, st));
+  HM_CUDA(launch_plane_c2r(s->prec, s->N, dspec, s->nspec, A.delta_g.p, s->n3, s->C, p->tw.p, nullptr, st));
+  HM_CUDA(launch_analytics(s->prec, an_args(s), st));
+  return HM_OK;
+}
+
+int hm_state_analytics(hm_state* s, int32_t enable, int32_t n_radii, const double* radii_host, int32_t max_samples,
+                       void* stream) {
+  if (!s) return fail(HM_EINVAL, "null state");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  HM_CUDA(cudaSetDevice(s->device));
+  HM_CUDA(cudaStreamSynchronize(st));   // no sample in flight still uses the buffers
+  if (s->gstream) HM_CUDA(cudaStreamSynchronize(s->gstream));
+  hm_state::Analytics& A = s->an;
+  analytics_release(A);
+  if (!enable) return HM_OK;
+  if (n_radii < 0 || n_radii > kMaxShells) return fail(HM_EINVAL, "n_radii must be in [0, 32]");
+  if (n_radii > 0 && !radii_host) return fail(HM_EINVAL, "null radii");
+  if (max_samples < 0) return fail(HM_EINVAL, "max_samples must be >= 0");
+  for (int k = 0; k < n_radii; ++k) {
+    if (!std::isfinite(radii_host[k]) || radii_host[k] < 0) return fail(HM_EINVAL, "radii must be finite and >= 0");
+    if (k > 0 && !(radii_host[k] > radii_host[k - 1])) return fail(HM_EINVAL, "radii must increase");
+  }
+  const int C = s->C, N = s->N;
+  const long long n3 = s->n3;
+  A.nsh = n_radii;
+  A.radii.assign(radii_host, radii_host + n_radii);
+  A.max_samples = max_samples;
+  A.nblk = (int)std::min<long long>(512, std::max<long long>(1, n3 / (256 * 8)));
+  const size_t fb = (size_t)n3 * s->rsz;
+  HM_TRY(A.delta_g.alloc(fb * C));
+  HM_TRY(A.vel_g.alloc(fb * 3 * C));
+  DevBuf* acc[] = {&A.mean_d, &A.m2_d, &A.mean_vr, &A.m2_vr};
+  for (DevBuf* b : acc) {
+    HM_TRY(b->alloc(fb * C));
+    HM_CUDA(cudaMemsetAsync(b->p, 0, fb * C, st));
+  }
+  // sphere membership of every node (host, FP64): the innermost sphere
+  // |x - o| <= R_k holding node x = i*Delta, 255 for none; chains with the
+  // same observer share the computation
+  std::vector<unsigned char> shell((size_t)n3 * C, 255);
+  std::vector<double> cnt((size_t)C * std::max(1, n_radii), 0.0), obs(3 * C);
+  const double dl = s->p0->delta;
+  for (int c = 0; c < C; ++c) {
+    const double* o = s->chain_prob[c]->obs;
+    for (int j = 0; j < 3; ++j) obs[3 * c + j] = o[j];
+    int same = -1;
+    for (int c2 = 0; c2 < c && same < 0; ++c2)
+      if (obs[3 * c2] == o[0] && obs[3 * c2 + 1] == o[1] && obs[3 * c2 + 2] == o[2]) same = c2;
+    unsigned char* sc = shell.data() + (size_t)c * n3;
+    if (same >= 0) {
+      std::memcpy(sc, shell.data() + (size_t)same * n3, (size_t)n3);
+      for (int k = 0; k < n_radii; ++k) cnt[(size_t)c * n_radii + k] = cnt[(size_t)same * n_radii + k];
+      continue;
+    }
+    if (n_radii == 0) continue;
+    for (int ix = 0; ix < N; ++ix)
+      for (int iy = 0; iy < N; ++iy)
+        for (int iz = 0; iz < N; ++iz) {
+          const double dx = ix * dl - o[0], dy = iy * dl - o[1], dz = iz * dl - o[2];
+          const double r = std::sqrt(dx * dx + dy * dy + dz * dz);
+          int k = 0;
+          while (k < n_radii && r > radii_host[k]) ++k;
+          if (k < n_radii) {
+            sc[((size_t)ix * N + iy) * N + iz] = (unsigned char)k;
+            for (int q = k; q < n_radii; ++q) cnt[(size_t)c * n_radii + q] += 1.0;
+          }
+        }
+  }
+  HM_TRY(A.shell.alloc((size_t)n3 * C));
+  HM_CUDA(cudaMemcpyAsync(A.shell.p, shell.data(), (size_t)n3 * C, cudaMemcpyHostToDevice, st));
+  HM_TRY(A.sph_cnt.alloc(8 * cnt.size()));
+  HM_CUDA(cudaMemcpyAsync(A.sph_cnt.p, cnt.data(), 8 * cnt.size(), cudaMemcpyHostToDevice, st));
+  HM_TRY(A.obs.alloc(8 * obs.size()));
+  HM_CUDA(cudaMemcpyAsync(A.obs.p, obs.data(), 8 * obs.size(), cudaMemcpyHostToDevice, st));
+  const size_t nsh1 = (size_t)std::max(1, n_radii);
+  HM_TRY(A.sig_part.alloc(8 * 2 * (size_t)C * A.nblk));
+  HM_TRY(A.met_part.alloc(8 * (size_t)C * A.nblk));
+  HM_TRY(A.shell_part.alloc(8 * 4 * nsh1 * C * A.nblk));
+  DevBuf* zero[] = {&A.sig_prev, &A.sig_cur, &A.count};
+  for (DevBuf* b : zero) {
+    HM_TRY(b->alloc(8 * (size_t)C));
+    HM_CUDA(cudaMemsetAsync(b->p, 0, 8 * (size_t)C, st));
+  }
+  HM_TRY(A.hist.alloc(8 * (size_t)C * std::max(1, max_samples)));
+  HM_CUDA(cudaMemsetAsync(A.hist.p, 0, 8 * (size_t)C * std::max(1, max_samples), st));
+  HM_TRY(A.sph_acc.alloc(8 * 10 * nsh1 * C));
+  HM_CUDA(cudaMemsetAsync(A.sph_acc.p, 0, 8 * 10 * nsh1 * C, st));
+  HM_CUDA(cudaStreamSynchronize(st));   // the host staging vectors go out of scope
+  A.on = true;
+  return HM_OK;
+}
+
+int hm_state_analytics_read(hm_state* s, int32_t chain, void* mean_delta_dev, void* var_delta_dev,
+                            void* mean_vr_dev, void* var_vr_dev, double* metric_host, int32_t max_metric,
+                            double* sphere_host, int64_t* n_samples_out, void* stream) {
+  if (!s) return fail(HM_EINVAL, "null state");
+  hm_state::Analytics& A = s->an;
+  if (!A.on) return fail(HM_ESTATE, "chain analytics are off (hm_state_analytics)");
+  if (chain < 0 || chain >= s->C) return fail(HM_EINVAL, "chain out of range");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  HM_CUDA(cudaSetDevice(s->device));
+  if (s->gstream) HM_CUDA(cudaStreamSynchronize(s->gstream));
+  long long n = 0;
+  HM_CUDA(cudaMemcpyAsync(&n, A.count.as<long long>() + chain, 8, cudaMemcpyDeviceToHost, st));
+  HM_CUDA(cudaStreamSynchronize(st));
+  const double scale = n > 1 ? 1.0 / (double)(n - 1) : 0.0;
+  const size_t fb = (size_t)s->n3 * s->rsz;
+  const size_t off = fb * chain;
+  if (mean_delta_dev)
+    HM_CUDA(cudaMemcpyAsync(mean_delta_dev, A.mean_d.as<char>() + off, fb, cudaMemcpyDeviceToDevice, st));
+  if (mean_vr_dev) HM_CUDA(cudaMemcpyAsync(mean_vr_dev, A.mean_vr.as<char>() + off, fb, cudaMemcpyDeviceToDevice, st));
+  if (var_delta_dev) HM_CUDA(launch_an_scale(s->prec, s->n3, A.m2_d.as<char>() + off, var_delta_dev, scale, st));
+  if (var_vr_dev) HM_CUDA(launch_an_scale(s->prec, s->n3, A.m2_vr.as<char>() + off, var_vr_dev, scale, st));
+  if (metric_host && max_metric > 0 && n >= 2) {
+    const long long m = std::min<long long>({n - 1, (long long)A.max_samples, (long long)max_metric});
+    if (m > 0)
+      HM_CUDA(cudaMemcpyAsync(metric_host, A.hist.as<double>() + (size_t)chain * std::max(1, A.max_samples),
+                              8 * (size_t)m, cudaMemcpyDeviceToHost, st));
+  }
+  std::vector<double> sph((size_t)10 * std::max(1, A.nsh));
+  if (sphere_host && A.nsh > 0)
+    HM_CUDA(cudaMemcpyAsync(sph.data(), A.sph_acc.as<double>() + (size_t)chain * 10 * A.nsh, 8 * 10 * (size_t)A.nsh,
+                            cudaMemcpyDeviceToHost, st));
+  HM_CUDA(cudaStreamSynchronize(st));
+  if (sphere_host)
+    for (int k = 0; k < A.nsh; ++k)
+      for (int q = 0; q < 5; ++q) {
+        sphere_host[(k * 5 + q) * 2] = sph[(k * 5 + q) * 2];
+        sphere_host[(k * 5 + q) * 2 + 1] = sph[(k * 5 + q) * 2 + 1] * scale;
+      }
+  if (n_samples_out) *n_samples_out = n;
   return HM_OK;
 }
 

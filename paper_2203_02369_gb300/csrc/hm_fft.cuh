@@ -219,6 +219,7 @@ __device__ __forceinline__ void fft_smem(cplx<T>* buf, int rs, int es, const cpl
 template <typename T> struct HalfSqAcc;
 template <> struct HalfSqAcc<double> {
   double s = 0.0;
+  __device__ __forceinline__ void add(double x) { s += x; }
   __device__ __forceinline__ void add_half_sq(double x) { s += 0.5 * x * x; }
   __device__ __forceinline__ void warp_reduce() {
 #pragma unroll

@@ -496,9 +496,9 @@ cudaError_t launch_plane_r2c_cl(const void* in, long long in_stride, void* out, 
   const dim3 grid(N * ClCfg<N>::K, count);
   PlanePoints none{};
   if (pts)
-    return launch_k(k_plane_r2c_cl<T, N, true>, grid, dim3(ClCfg<N>::NT), sm, st, static_cast<const T*>(nullptr),
+    return launch_k<PDL_PLANE>(k_plane_r2c_cl<T, N, true>, grid, dim3(ClCfg<N>::NT), sm, st, static_cast<const T*>(nullptr),
                     0ll, static_cast<cplx<T>*>(out), out_stride, static_cast<const cplx<T>*>(tw), *pts);
-  return launch_k(k_plane_r2c_cl<T, N, false>, grid, dim3(ClCfg<N>::NT), sm, st, static_cast<const T*>(in), in_stride,
+  return launch_k<PDL_PLANE>(k_plane_r2c_cl<T, N, false>, grid, dim3(ClCfg<N>::NT), sm, st, static_cast<const T*>(in), in_stride,
                   static_cast<cplx<T>*>(out), out_stride, static_cast<const cplx<T>*>(tw), none);
 }
 
@@ -514,7 +514,7 @@ cudaError_t launch_plane_c2r_cl(int mode, const void* in, long long in_stride, v
   PlanePoints p{};
   if (pts) p = *pts;
   auto args = [&](auto kern) {
-    return launch_k(kern, grid, dim3(ClCfg<N>::NT), sm, st, static_cast<const cplx<T>*>(in), in_stride,
+    return launch_k<PDL_PLANE>(kern, grid, dim3(ClCfg<N>::NT), sm, st, static_cast<const cplx<T>*>(in), in_stride,
                     static_cast<T*>(out), out_stride, static_cast<const cplx<T>*>(tw), e, p,
                     static_cast<cplx<T>*>(next), in_stride);
   };

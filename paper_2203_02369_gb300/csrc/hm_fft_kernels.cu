@@ -699,7 +699,29 @@ k_pencil(const cplx<T>* __restrict__ in, long long in_stride, cplx<T>* __restric
     for (int j = 0; j < NIN; ++j) px_s2_smem<T, N, false, W>(buf + j * kTC);
     // inverse transform(s): stage 1 loads the natural-order spectra and
     // applies the k-space operator on the way in
-    if constexpr (MODE == PM_VEL) {
+    if constexpr (MODE == PM_SCALE) {
+      // real weight amp[n^2] applied as the inverse's first stage loads
+#pragma unroll 1
+      for (int g = threadIdx.x; g < kTC * M; g += kPencilNT) {
+        const int t = g % kTC, m = g / kTC;
+        const long long col = c0 + t;
+        const ColGeom<N> cg = col_geom<N>(col < NCOL ? col : 0);
+        C a[R1];
+#pragma unroll
+        for (int jj = 0; jj < R1; ++jj) {
+          const int kx = m + M * jj;
+          const int nx = kx < N / 2 ? kx : kx - N;
+          const T am = __ldg(&amp[nx * nx + cg.ny2nz2]);
+          const C wk = buf[kx * W + t];
+          a[jj] = C{am * wk.x, am * wk.y};
+        }
+        stage1_group<T, N, true>(a, m, tw);
+#pragma unroll
+        for (int k2 = 0; k2 < R1; ++k2) buf[(m + M * k2) * W + t] = a[k2];
+      }
+      __syncthreads();
+      px_s2_global<T, N, true, W>(buf, out + (long long)s * out_stride, c0);
+    } else if constexpr (MODE == PM_VEL) {
       // component order y, z, x: x is written over the input spectrum, and
       // each group reads and writes only its own elements
 #pragma unroll 1
@@ -765,7 +787,7 @@ static cudaError_t plane_r2c_t(const void* in, long long in_stride, void* out, l
                                int count, const void* tw, const PlanePoints& pts, cudaStream_t st) {
   constexpr size_t sm = plane_smem_bytes<T, N>();
   dim3 grid(N, count);
-  return launch_k(k_plane_r2c<T, N, SC>, grid, dim3(PlaneCfg<N>::NT), sm, st, static_cast<const T*>(in), in_stride,
+  return launch_k<PDL_PLANE>(k_plane_r2c<T, N, SC>, grid, dim3(PlaneCfg<N>::NT), sm, st, static_cast<const T*>(in), in_stride,
                   static_cast<cplx<T>*>(out), out_stride, static_cast<const cplx<T>*>(tw), pts);
 }
 
@@ -777,7 +799,7 @@ static cudaError_t plane_c2r_t(const void* in, long long in_stride, void* out, l
   dim3 grid(N, count);
   FieldEpi e{};
   if (epi) e = *epi;
-  return launch_k(k_plane_c2r<T, N, MODE>, grid, dim3(PlaneCfg<N>::NT), sm, st, static_cast<const cplx<T>*>(in),
+  return launch_k<PDL_PLANE>(k_plane_c2r<T, N, MODE>, grid, dim3(PlaneCfg<N>::NT), sm, st, static_cast<const cplx<T>*>(in),
                   in_stride, static_cast<T*>(out), out_stride, static_cast<const cplx<T>*>(tw), e, pts,
                   static_cast<cplx<T>*>(next), in_stride);
 }
@@ -790,7 +812,7 @@ static cudaError_t pencil_t(const void* in, long long in_stride, void* out, long
   constexpr int NCOMP = (MODE == PM_VEL || MODE == PM_ADJ) ? 3 : 1;
   constexpr size_t sm = sizeof(cplx<T>) * N * NCOMP * kTC;
   dim3 grid((N * NH + kTC - 1) / kTC, count);
-  return launch_k(k_pencil<T, N, MODE>, grid, dim3(kPencilNT), sm, st, static_cast<const cplx<T>*>(in), in_stride,
+  return launch_k<PDL_PENCIL>(k_pencil<T, N, MODE>, grid, dim3(kPencilNT), sm, st, static_cast<const cplx<T>*>(in), in_stride,
                   static_cast<cplx<T>*>(out), out_stride, static_cast<const cplx<T>*>(tw),
                   static_cast<const T*>(amp), plane_off, ksplit);
 }
@@ -839,6 +861,7 @@ static cudaError_t prepare_pencil_t() {
   constexpr int s1 = (int)(sizeof(cplx<T>) * N * kTC), s3 = (int)(sizeof(cplx<T>) * N * 3 * kTC);
   if ((e = cudaFuncSetAttribute(k_pencil<T, N, PM_FWD>, A, s1)) != cudaSuccess) return e;
   if ((e = cudaFuncSetAttribute(k_pencil<T, N, PM_INV>, A, s1)) != cudaSuccess) return e;
+  if ((e = cudaFuncSetAttribute(k_pencil<T, N, PM_SCALE>, A, s1)) != cudaSuccess) return e;
   if ((e = cudaFuncSetAttribute(k_pencil<T, N, PM_VEL>, A, s3)) != cudaSuccess) return e;
   return cudaFuncSetAttribute(k_pencil<T, N, PM_ADJ>, A, s3);
 }
@@ -856,6 +879,7 @@ static cudaError_t prepare_t() {
   constexpr int s1 = (int)(sizeof(cplx<T>) * N * kTC), s3 = (int)(sizeof(cplx<T>) * N * 3 * kTC);
   if ((e = cudaFuncSetAttribute(k_pencil<T, N, PM_FWD>, A, s1)) != cudaSuccess) return e;
   if ((e = cudaFuncSetAttribute(k_pencil<T, N, PM_INV>, A, s1)) != cudaSuccess) return e;
+  if ((e = cudaFuncSetAttribute(k_pencil<T, N, PM_SCALE>, A, s1)) != cudaSuccess) return e;
   if ((e = cudaFuncSetAttribute(k_pencil<T, N, PM_VEL>, A, s3)) != cudaSuccess) return e;
   return cudaFuncSetAttribute(k_pencil<T, N, PM_ADJ>, A, s3);
 }
@@ -921,6 +945,7 @@ static cudaError_t pencil_mode(int mode, const void* in, long long in_stride, vo
     case PM_VEL: return pencil_t<T, N, PM_VEL>(in, in_stride, out, out_stride, count, tw, amp, st);
     case PM_ADJ:
       return pencil_t<T, N, PM_ADJ>(in, in_stride, out, out_stride, count, tw, amp, st, plane_off, plane_split(N));
+    case PM_SCALE: return pencil_t<T, N, PM_SCALE>(in, in_stride, out, out_stride, count, tw, amp, st);
   }
   return cudaErrorInvalidValue;
 }

@@ -8,12 +8,17 @@ namespace hm {
 
 // Kernel launch, optionally with programmatic stream serialisation (the
 // kernel may start while its predecessor in the stream finishes; it calls
-// pdl_wait before reading the predecessor's output).  Off unless the
-// environment sets HM_PDL=1: measured on the 128^3 trajectory it was slower
-// (dependents launched early hold shared memory on SMs that the draining
-// plane pass still needs).
-bool pdl_enabled();
-template <typename... KArgs, typename... Args>
+// pdl_wait before reading the predecessor's output), for the categories
+// that HM_PDL selects (default: the x pencils).  Launching the plane passes
+// or the point kernels early made the 128^3 trajectory slower: the early
+// CTAs wait on SMs that the predecessor's last CTAs or the side stream need.
+// Launch categories for the programmatic-dependent-launch switch: the
+// environment variable HM_PDL is a bit mask of the categories whose kernels
+// may start early (the kernel launched with the attribute is the one that
+// waits for its predecessor).
+enum PdlCat : int { PDL_PLANE = 1, PDL_PENCIL = 2, PDL_POINTS = 4, PDL_OTHER = 8 };
+bool pdl_enabled(int cat);
+template <int CAT = PDL_OTHER, typename... KArgs, typename... Args>
 inline cudaError_t launch_k(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
                             Args... args) {
   cudaLaunchAttribute attr[1];
@@ -25,7 +30,7 @@ inline cudaError_t launch_k(void (*kern)(KArgs...), dim3 grid, dim3 block, size_
   cfg.dynamicSmemBytes = smem;
   cfg.stream = st;
   cfg.attrs = attr;
-  cfg.numAttrs = pdl_enabled() ? 1 : 0;
+  cfg.numAttrs = pdl_enabled(CAT) ? 1 : 0;
   return cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...);
 }
 
@@ -140,7 +145,7 @@ struct PointArrays {
 
 // ---- FFT passes (hm_fft_kernels.cu) ----
 // Spectrum layout: [x][y][z], z in 0..N/2 (NH = N/2+1 entries), complex.
-enum PencilMode : int { PM_FWD = 0, PM_INV = 1, PM_VEL = 2, PM_ADJ = 3 };
+enum PencilMode : int { PM_FWD = 0, PM_INV = 1, PM_VEL = 2, PM_ADJ = 3, PM_SCALE = 4 };
 
 // Plane-pass inputs/outputs beyond plain arrays.
 struct PlanePoints {
@@ -166,7 +171,9 @@ cudaError_t launch_plane_c2r(int prec, int N, const void* in, long long in_strid
 // 3C velocity spectra -> CIC partials of u and du at the bucketed points.
 cudaError_t launch_plane_c2r_gather(int prec, int N, const void* in, long long in_stride,
                                     const PlanePoints& pts, int count, const void* tw, cudaStream_t st);
-// x-axis pass over count chains.  PM_VEL: 1 spectrum -> 3; PM_ADJ: 3 -> 1.
+// x-axis pass over count chains.  PM_VEL: 1 spectrum -> 3; PM_ADJ: 3 -> 1;
+// PM_SCALE: 1 -> 1, the spectrum times the real table amp[n^2] (the
+// colouring sqrt(P/Delta^3)/N^3 of the density field).
 // For PM_ADJ, plane_off (the chains' point-bucket offsets, [count][N*K+1])
 // marks the x-planes that the scatter plane pass left unwritten because no
 // point touches them; they are read as zero.  nullptr reads every plane.
@@ -251,5 +258,34 @@ enum FinalizeWhat : int {
   FIN_ACCEPT = 4,    // H_new, Metropolis test, traj++
   FIN_KIN = 8,       // kin = sum of the kinetic partials given
 };
+
+
+// ---- chain analytics (hm_analytics.cu) ----
+constexpr int kMaxShells = 32;   // sphere radii per state
+struct AnArgs {
+  int C, N, nsh, max_samples, nblk;
+  long long n3;
+  double delta;              // grid spacing
+  double f;                  // growth rate: monopole = a f <delta>, a = 1
+  const double* obs;         // [C][3] observer of each chain
+  const void* delta_g;       // T [C][n3] density field of the current sample
+  const void* vel_g;         // T [C][3][n3] velocity field of the current sample
+  void *mean_d, *m2_d, *mean_vr, *m2_vr;   // T [C][n3] Welford mean and M2
+  const unsigned char* shell;  // [C][n3] innermost sphere holding the node, 255 for none
+  const double* sph_cnt;     // [C][nsh] nodes inside sphere k
+  double* sig_part;          // [C][nblk][2] partial sums of delta and delta^2
+  double* met_part;          // [C][nblk] partial sums of the metric's squares
+  double* shell_part;        // [C][nblk][nsh][4] per-shell sums of delta, v_x, v_y, v_z
+  double* sig_prev;          // [C] Sigma of the previous sample
+  double* sig_cur;           // [C] Sigma of the current sample
+  long long* count;          // [C] samples accumulated
+  double* hist;              // [C][max_samples] metric of sample s >= 2 at index s - 2
+  double* sph_acc;           // [C][nsh][5][2] Welford mean and M2 over samples of
+                             // (monopole, V_x, V_y, V_z, |V|) in sphere k
+};
+// One sample: sigma partials, node moments and shell sums, per-chain finalize.
+cudaError_t launch_analytics(int prec, const AnArgs& a, cudaStream_t st);
+// out[i] = in[i] * scale for i < n (field precision prec).
+cudaError_t launch_an_scale(int prec, long long n, const void* in, void* out, double scale, cudaStream_t st);
 
 }  // namespace hm

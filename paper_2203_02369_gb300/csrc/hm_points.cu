@@ -395,23 +395,23 @@ int points_blocks(int max_pts) { return max_pts > 0 ? (max_pts + kPtsNT - 1) / k
 cudaError_t launch_points_prep(int n_chains, int max_pts, const PointParams* pp, PointArrays pa,
                                cudaStream_t st) {
   if (max_pts <= 0) return cudaSuccess;
-  return launch_k(k_points_prep, pts_grid(n_chains, max_pts), dim3(kPtsNT), 0, st, pp, pa);
+  return launch_k<PDL_POINTS>(k_points_prep, pts_grid(n_chains, max_pts), dim3(kPtsNT), 0, st, pp, pa);
 }
 
 cudaError_t launch_points_place(int prec, int n_chains, int max_pts, const PointParams* pp,
                                 PointArrays pa, ChainScal* cs, cudaStream_t st) {
   // runs even without points: block 0 writes the (empty) bucket offsets
-  if (prec == 0) return launch_k(k_points_place<float>, pts_grid(n_chains, max_pts), dim3(kPtsNT), 0, st, pp, pa, cs);
-  return launch_k(k_points_place<double>, pts_grid(n_chains, max_pts), dim3(kPtsNT), 0, st, pp, pa, cs);
+  if (prec == 0) return launch_k<PDL_POINTS>(k_points_place<float>, pts_grid(n_chains, max_pts), dim3(kPtsNT), 0, st, pp, pa, cs);
+  return launch_k<PDL_POINTS>(k_points_place<double>, pts_grid(n_chains, max_pts), dim3(kPtsNT), 0, st, pp, pa, cs);
 }
 
 cudaError_t launch_points_lik(int prec, int n_chains, int max_pts, const PointParams* pp, PointArrays pa,
                               double* pts_part, int part_stride, int mode, double* kin_part, ChainScal* cs,
                               double* gsig_part, cudaStream_t st) {
   if (prec == 0)
-    return launch_k(k_points_lik<float>, pts_grid(n_chains, max_pts), dim3(kPtsNT), 0, st, pp, pa, pts_part,
+    return launch_k<PDL_POINTS>(k_points_lik<float>, pts_grid(n_chains, max_pts), dim3(kPtsNT), 0, st, pp, pa, pts_part,
                     part_stride, mode, kin_part, cs, gsig_part);
-  return launch_k(k_points_lik<double>, pts_grid(n_chains, max_pts), dim3(kPtsNT), 0, st, pp, pa, pts_part,
+  return launch_k<PDL_POINTS>(k_points_lik<double>, pts_grid(n_chains, max_pts), dim3(kPtsNT), 0, st, pp, pa, pts_part,
                   part_stride, mode, kin_part, cs, gsig_part);
 }
 

@@ -12,7 +12,7 @@ import numpy as np
 import torch
 
 from . import _lib
-from ._lib import check
+from ._lib import HamletError, check
 from .mock import Cosmology, MockSpec
 
 _FT = {0: torch.float32, 1: torch.float64}
@@ -204,6 +204,7 @@ class State:
                                              ct.c_uint64(int(seed)), darr, ct.byref(self.h)))
         p0 = self.problems[0]
         self.N, self.dtype, self.device = p0.N, p0.dtype, p0.device
+        self._an_radii = None
 
     def close(self):
         if self.h:
@@ -279,6 +280,35 @@ class State:
         g = np.zeros(self.C)
         check(self.lib.hm_state_get_sigma_nl(self.h, _dptr(s), _dptr(g), _stream()))
         return s, g
+
+    def analytics(self, enable=True, radii=(), max_samples=1024):
+        """Turn the on-device chain analytics on (zeroed) or off; radii of the
+        spheres about the observer for the monopole and dipole."""
+        r = np.ascontiguousarray(radii, dtype=np.float64)
+        check(self.lib.hm_state_analytics(self.h, int(bool(enable)), int(r.shape[0]), _dptr(r) if r.size else None,
+                                          int(max_samples), _stream()))
+        self._an_radii = r.copy() if enable else None
+        self._an_max = int(max_samples)
+
+    def analytics_read(self, chain=0, max_metric=None):
+        """Mean/variance fields of delta and v_r, the convergence values and
+        the sphere moments (mean, variance over samples) of one chain."""
+        dt = self.dtype
+        shape = (self.N,) * 3
+        md, vd, mv, vv = (torch.empty(shape, dtype=dt, device=self.device) for _ in range(4))
+        if self._an_radii is None:
+            raise HamletError(-5, "chain analytics are off (State.analytics)")
+        nr = self._an_radii.shape[0]
+        if max_metric is None:
+            max_metric = self._an_max
+        met = np.zeros(max(1, max_metric))
+        sph = np.zeros((max(nr, 1), 5, 2))
+        n = ct.c_int64()
+        check(self.lib.hm_state_analytics_read(self.h, int(chain), _ptr(md), _ptr(vd), _ptr(mv), _ptr(vv),
+                                               _dptr(met), int(max_metric), _dptr(sph), ct.byref(n), _stream()))
+        ns = n.value
+        return {"n_samples": ns, "mean_delta": md, "var_delta": vd, "mean_vr": mv, "var_vr": vv,
+                "metric": met[:max(0, min(ns - 1, max_metric))].copy(), "sphere": sph[:nr].copy()}
 
     def adapt_step_size(self, n_warmup, n_leapfrog, eps0, target=0.65, sample_distances=True):
         """Dual-averaging warm-up; returns (tuned eps per chain, trace)."""
