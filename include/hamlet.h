@@ -210,6 +210,56 @@ int hm_leapfrog(hm_state* s, int32_t n_steps, double eps, int32_t sample_distanc
 int hm_run_chain(hm_state* s, int32_t n_traj, int32_t n_leapfrog, const double* eps_host,
                  int32_t sample_distances, int32_t use_graph, hm_trace* trace_host, void* stream);
 
+/* Slotted states: continuous batching of independent reconstruction jobs
+ * of one grid (the HMC transitions of section "Construction of HMC chains",
+ * run for many jobs at once; the batching is a serving pattern the paper
+ * does not have).  A slotted state holds up to n_slots chains of the grid,
+ * precision, box and power spectrum of `templ`, each with room for
+ * max_points catalogue points.  Jobs are loaded and released while the
+ * others keep running; every trajectory of hm_slots_run advances all loaded
+ * chains in the same kernel launches (one captured graph per number of
+ * loaded chains).  The loaded chains are packed at indices 0..n_active-1,
+ * which hm_state_get/set/get_grad/scalars take as the chain index.  Each
+ * chain keeps its own catalogue, step, trajectory counter and Philox chain
+ * word, so its samples are those it would draw alone in a one-chain state
+ * with the same seed and chain word (up to the order of the atomic scatter
+ * additions).  Calls on one slotted state must be ordered on one stream.
+ * Device memory is allocated once, at creation (HM_ENOMEM if it does not
+ * fit): about 5 grids + 6 half spectra per slot and ~700 B per point of
+ * room.  Not available on a slotted state: hm_adapt_step_size (use the
+ * per-job adaptation below), sigma_NL sampling and chain analytics
+ * (HM_ESTATE). */
+int hm_slots_create(hm_problem* templ, int32_t n_slots, int64_t max_points, uint64_t seed, hm_state** out);
+/* Number of loaded chains and of slots. */
+int hm_slots_count(hm_state* s, int32_t* n_active_out, int32_t* n_slots_out);
+/* Load job `job` (same N, precision, device, box and P(k) as the template;
+ * its catalogue, set with hm_set_catalog, is copied; its distance-prior
+ * table is read in place, so `job` must outlive the slot) as chain index
+ * n_active: w = 0, d = d_init_host (job's n doubles, host), momenta 0,
+ * trajectory counter 0, Philox chain word chain_id, step eps0.  With
+ * adapt_target in (0, 1) the step adapts by dual averaging after every
+ * trajectory (as hm_adapt_step_size) until hm_slots_adapt_end; 0 keeps it
+ * fixed.  Psi and the gradient of the new chain are evaluated on `stream`.
+ * *index_out receives the chain index.  Errors: HM_EINVAL (mismatched job,
+ * catalogue larger than a slot, bad eps0 or target, non-finite d),
+ * HM_ESTATE (every slot in use). */
+int hm_slots_load(hm_state* s, hm_problem* job, int32_t chain_id, const double* d_init_host, double eps0,
+                  double adapt_target, int32_t* index_out, void* stream);
+/* End the step adaptation of chain `index`: its step becomes the averaged
+ * iterate, copied to *eps_out_host (may be NULL).  Synchronises the stream. */
+int hm_slots_adapt_end(hm_state* s, int32_t index, double* eps_out_host, void* stream);
+/* Release chain `index` (read its state first with hm_state_get).  The last
+ * loaded chain moves into `index`; *moved_from_out (may be NULL) receives
+ * its old index, or -1 when none moved.  Stream-ordered. */
+int hm_slots_release(hm_state* s, int32_t index, int32_t* moved_from_out, void* stream);
+/* n_traj HMC transitions of every loaded chain at its own step (fresh
+ * momenta, n_leapfrog leapfrog steps, Metropolis test, restore on
+ * rejection).  trace_host (may be NULL) receives n_traj * n_active records,
+ * trajectory-major; the call then synchronises the stream.  No loaded chain:
+ * nothing runs. */
+int hm_slots_run(hm_state* s, int32_t n_traj, int32_t n_leapfrog, int32_t use_graph, hm_trace* trace_host,
+                 void* stream);
+
 /* sigma_NL as a sampled parameter (eq. q; section "The Likelihood function:
  * velocities" makes it a model parameter, eq. M_ab gives it unit mass): with
  * enable != 0 every chain carries sigma_NL (starting at sigma0_host[c], or

@@ -311,12 +311,33 @@ struct hm_state {
     DevBuf delta_g, vel_g, mean_d, m2_d, mean_vr, m2_vr, shell, sph_cnt, sig_part, met_part, shell_part;
     DevBuf sig_prev, sig_cur, count, hist, sph_acc, obs;
   } an;
-  // captured trajectory graph
+  // captured trajectory graphs, one per (active chains, leapfrog steps,
+  // distances sampled, profiled); a slotted state changes its active count
+  struct Graph {
+    int C, L, sd, prof, pairs;
+    cudaGraphExec_t exec;
+  };
+  std::vector<Graph> graphs;
   cudaStream_t gstream = nullptr;
-  cudaGraphExec_t gexec = nullptr;
-  int g_L = -1, g_sd = -1, g_prof = 0;
+  // slotted state (continuous batching): capacity, point room per slot,
+  // point region of each active chain, free regions
+  int C_cap = 0;
+  bool slotted = false;
+  long long slot_pts = 0;
+  std::vector<int> region_of;
+  std::vector<int> free_regions;
+  void drop_graphs(bool profiled_only = false) {
+    for (size_t k = 0; k < graphs.size();) {
+      if (!profiled_only || graphs[k].prof) {
+        cudaGraphExecDestroy(graphs[k].exec);
+        graphs.erase(graphs.begin() + (long)k);
+      } else {
+        ++k;
+      }
+    }
+  }
   ~hm_state() {
-    if (gexec) cudaGraphExecDestroy(gexec);
+    drop_graphs();
     if (gstream) cudaStreamDestroy(gstream);
   }
 };
@@ -1162,11 +1183,10 @@ static int run_traj_loop(hm_state* s, int32_t n_traj, int32_t n_leapfrog, int32_
   } else if (n_traj > 0) {
     if (!s->gstream) HM_CUDA(cudaStreamCreateWithFlags(&s->gstream, cudaStreamNonBlocking));
     const int want_prof = pf ? 1 : 0;
-    if (!s->gexec || s->g_L != n_leapfrog || s->g_sd != sample_distances || s->g_prof != want_prof) {
-      if (s->gexec) {
-        cudaGraphExecDestroy(s->gexec);
-        s->gexec = nullptr;
-      }
+    hm_state::Graph* gr = nullptr;
+    for (auto& x : s->graphs)
+      if (x.C == s->C && x.L == n_leapfrog && x.sd == sample_distances && x.prof == want_prof) gr = &x;
+    if (!gr) {
       cudaGraph_t g = nullptr;
       if (pf) pf->idx = 0;
       HM_CUDA(cudaStreamBeginCapture(s->gstream, cudaStreamCaptureModeThreadLocal));
@@ -1177,20 +1197,21 @@ static int run_traj_loop(hm_state* s, int32_t n_traj, int32_t n_leapfrog, int32_
         return rc;
       }
       if (ce != cudaSuccess) return fail(HM_ECUDA, std::string("graph capture: ") + cudaGetErrorString(ce));
-      ce = cudaGraphInstantiate(&s->gexec, g, 0);
+      cudaGraphExec_t ex = nullptr;
+      ce = cudaGraphInstantiate(&ex, g, 0);
       cudaGraphDestroy(g);
       if (ce != cudaSuccess) return fail(HM_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(ce));
-      s->g_L = n_leapfrog;
-      s->g_sd = sample_distances;
-      s->g_prof = want_prof;
-      if (pf) s->prof_pairs = pf->idx;
+      s->graphs.push_back({s->C, n_leapfrog, sample_distances, want_prof, pf ? pf->idx : 0, ex});
+      gr = &s->graphs.back();
     }
+    if (pf) s->prof_pairs = gr->pairs;
+    const cudaGraphExec_t gexec = gr->exec;
     cudaEvent_t ev;
     HM_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
     HM_CUDA(cudaEventRecord(ev, st));
     HM_CUDA(cudaStreamWaitEvent(s->gstream, ev, 0));
     for (int t = 0; t < n_traj; ++t) {
-      HM_CUDA(cudaGraphLaunch(s->gexec, s->gstream));
+      HM_CUDA(cudaGraphLaunch(gexec, s->gstream));
       if (an) HM_TRY(analytics_sample(s, s->gstream));
       if (pf) {
         if (n_traj == 1) {
@@ -1219,10 +1240,7 @@ int hm_run_chain(hm_state* s, int32_t n_traj, int32_t n_leapfrog, const double* 
   if (s->trace_cap < need) {
     HM_TRY(s->trace_dev.alloc(need));
     s->trace_cap = need;
-    if (s->gexec) {
-      cudaGraphExecDestroy(s->gexec);
-      s->gexec = nullptr;
-    }
+    s->drop_graphs();
   }
   HM_TRY(set_run(s, eps_host, sample_distances, st));
   HM_TRY(run_traj_loop(s, n_traj, n_leapfrog, sample_distances, use_graph, st, 1));
@@ -1238,6 +1256,7 @@ int hm_adapt_step_size(hm_state* s, int32_t n_warmup, int32_t n_leapfrog, double
                        const double* eps0_host, int32_t sample_distances, double* eps_out_host,
                        hm_trace* trace_host, void* stream) {
   if (!s || !eps0_host || !eps_out_host) return fail(HM_EINVAL, "null argument");
+  if (s->slotted) return fail(HM_ESTATE, "a slotted state adapts per job (hm_slots_load, hm_slots_adapt_end)");
   if (n_warmup <= 0 || n_leapfrog <= 0) return fail(HM_EINVAL, "n_warmup and n_leapfrog must be > 0");
   if (!(target_accept > 0 && target_accept < 1)) return fail(HM_EINVAL, "target_accept must be in (0, 1)");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -1246,10 +1265,7 @@ int hm_adapt_step_size(hm_state* s, int32_t n_warmup, int32_t n_leapfrog, double
   if (s->trace_cap < need) {
     HM_TRY(s->trace_dev.alloc(need));
     s->trace_cap = need;
-    if (s->gexec) {
-      cudaGraphExecDestroy(s->gexec);
-      s->gexec = nullptr;
-    }
+    s->drop_graphs();
   }
   HM_TRY(set_run(s, eps0_host, sample_distances, st));
   HM_CUDA(launch_da(s->C, 1, target_accept, nullptr, s->cs.as<ChainScal>(), st));
@@ -1265,6 +1281,7 @@ int hm_adapt_step_size(hm_state* s, int32_t n_warmup, int32_t n_leapfrog, double
 
 int hm_state_sample_sigma_nl(hm_state* s, int32_t enable, const double* sigma0_host, void* stream) {
   if (!s) return fail(HM_EINVAL, "null state");
+  if (s->slotted) return fail(HM_ESTATE, "sigma_NL sampling is not available on a slotted state");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   HM_CUDA(cudaSetDevice(s->device));
   std::vector<double> sig(s->C);
@@ -1276,10 +1293,7 @@ int hm_state_sample_sigma_nl(hm_state* s, int32_t enable, const double* sigma0_h
   HM_CUDA(launch_sig_set(s->C, enable ? 1 : 0, s->sig_dev.as<double>(), s->cs.as<ChainScal>(), st));
   HM_CUDA(cudaStreamSynchronize(st));   // the host copy of sig must outlive the transfer
   s->sample_sig = enable != 0;
-  if (s->gexec) {
-    cudaGraphExecDestroy(s->gexec);
-    s->gexec = nullptr;
-  }
+  s->drop_graphs();
   return state_refresh(s, st);
 }
 
@@ -1293,6 +1307,230 @@ int hm_state_get_sigma_nl(hm_state* s, double* sigma_out_host, double* grad_out_
   for (int c = 0; c < s->C; ++c) {
     sigma_out_host[c] = s->sample_sig ? cs[c].sig : s->chain_prob[c]->desc.sigma_nl;
     if (grad_out_host) grad_out_host[c] = s->sample_sig ? cs[c].g_sig : 0.0;
+  }
+  return HM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Slotted states: continuous batching of independent jobs of one grid.  The
+// active chains are packed at indices 0..C-1 so that every kernel launch of
+// a trajectory covers exactly the loaded jobs; a released index is refilled
+// by the last active chain.  Each chain keeps its catalogue in a point region
+// of slot_pts entries (regions never move), its own step, trajectory counter
+// and Philox chain word, so a job's chain does not depend on its neighbours.
+// ---------------------------------------------------------------------------
+static bool same_field_model(const hm_problem* a, const hm_problem* b) {
+  return a->N == b->N && a->prec == b->prec && a->device == b->device && a->L == b->L && a->aHf == b->aHf &&
+         a->pkA == b->pkA;
+}
+
+// Psi and the gradient of chain c alone (its position, its catalogue); the
+// workspace of chain index 0 serves as scratch.
+static int eval_chain(hm_state* s, int c, cudaStream_t st) {
+  GradArgs a = state_args(s);
+  const size_t gb = s->rsz * s->n3;
+  a.C = 1;
+  a.w = static_cast<char*>(s->w.p) + gb * c;
+  a.pw = static_cast<char*>(s->pw.p) + gb * c;
+  a.gw = static_cast<char*>(s->gw.p) + gb * c;
+  a.pp = s->pp.as<PointParams>() + c;
+  a.cs = s->cs.as<ChainScal>() + c;
+  HM_TRY(eval_single(a, st));
+  HM_CUDA(launch_finalize(1, a.prior_part, s->NP, a.pts_part, s->pts_blocks, nullptr, 0, nullptr, 0, FIN_PSI,
+                          s->seed, s->chain_id.as<int>() + c, a.cs, nullptr, st));
+  return HM_OK;
+}
+
+static int slotted_ok(hm_state* s) {
+  if (!s) return fail(HM_EINVAL, "null state");
+  if (!s->slotted) return fail(HM_ESTATE, "not a slotted state (hm_slots_create)");
+  return HM_OK;
+}
+
+int hm_slots_create(hm_problem* templ, int32_t n_slots, int64_t max_points, uint64_t seed, hm_state** out) {
+  if (!templ || !out || n_slots <= 0 || max_points < 0) return fail(HM_EINVAL, "bad argument");
+  *out = nullptr;
+  if (n_slots > 65535) return fail(HM_EINVAL, "n_slots must be <= 65535");
+  const long long tot = (long long)n_slots * max_points;
+  if (max_points > (1LL << 30) || tot > (1LL << 31) - 1) return fail(HM_EINVAL, "max_points too large");
+  auto s = std::make_unique<hm_state>();
+  s->slotted = true;
+  s->C_cap = n_slots;
+  s->C = 0;
+  s->slot_pts = max_points;
+  s->N = templ->N;
+  s->NP = templ->N * plane_split(templ->N);
+  s->prec = templ->prec;
+  s->device = templ->device;
+  s->n3 = templ->n3;
+  s->nspec = templ->nspec;
+  s->rsz = templ->rsz;
+  s->seed = seed;
+  s->p0 = templ;
+  HM_CUDA(cudaSetDevice(s->device));
+  s->ntot = tot;
+  s->max_pts = (int)max_points;
+  s->pts_blocks = points_blocks(s->max_pts);
+  s->nparts_f = (int)std::min<long long>(256, std::max<long long>(1, (s->n3 / 2 + 255) / 256));
+  s->nparts_p = std::max(1, std::min(64, (s->max_pts / 2 + 255) / 256));
+  const size_t C = n_slots, rs = s->rsz;
+  DevBuf* grids[] = {&s->w, &s->pw, &s->gw, &s->w0, &s->gw0};
+  for (DevBuf* b : grids) HM_TRY(b->alloc(rs * C * s->n3));
+  HM_TRY(s->S1.alloc(2 * rs * 3 * C * s->nspec));
+  HM_TRY(s->S2.alloc(2 * rs * 3 * C * s->nspec));
+  const size_t nt = (size_t)std::max<long long>(tot, 1);
+  DevBuf* dbl[] = {&s->rx, &s->ry, &s->rz, &s->mu, &s->smu, &s->zobs, &s->scz, &s->d, &s->pd, &s->gd, &s->d0, &s->gd0};
+  for (DevBuf* b : dbl) HM_TRY(b->alloc(8 * nt));
+  HM_TRY(s->work.alloc(s->prec, n_slots, s->N, tot));
+  s->pp_host.assign(C, PointParams{});
+  s->chain_prob.assign(C, nullptr);
+  s->eps_host.assign(C, 0.0);
+  HM_TRY(s->pp.alloc(sizeof(PointParams) * C));
+  HM_TRY(s->cs.alloc(sizeof(ChainScal) * C));
+  HM_TRY(s->chain_id.alloc(sizeof(int) * C));
+  HM_TRY(s->prior_part.alloc(8 * C * s->NP));
+  HM_TRY(s->pts_part.alloc(8 * C * s->pts_blocks));
+  HM_TRY(s->kinb_f.alloc(8 * C * s->nparts_f));
+  HM_TRY(s->kinb_p.alloc(8 * C * s->nparts_p));
+  HM_TRY(s->kinl_f.alloc(8 * C * s->NP));
+  HM_TRY(s->kinl_p.alloc(8 * C * s->pts_blocks));
+  HM_TRY(s->eps_dev.alloc(8 * C));
+  HM_TRY(s->sig_dev.alloc(8 * C));
+  HM_TRY(s->gsig_part.alloc(8 * C * s->pts_blocks));
+  HM_CUDA(cudaMemset(s->kinl_p.p, 0, 8 * C * s->pts_blocks));
+  HM_CUDA(cudaMemset(s->kinb_p.p, 0, 8 * C * s->nparts_p));
+  s->region_of.assign(C, -1);
+  s->free_regions.clear();
+  for (int r = n_slots - 1; r >= 0; --r) s->free_regions.push_back(r);
+  *out = s.release();
+  return HM_OK;
+}
+
+int hm_slots_count(hm_state* s, int32_t* n_active_out, int32_t* n_slots_out) {
+  HM_TRY(slotted_ok(s));
+  if (n_active_out) *n_active_out = s->C;
+  if (n_slots_out) *n_slots_out = s->C_cap;
+  return HM_OK;
+}
+
+int hm_slots_load(hm_state* s, hm_problem* job, int32_t chain_id, const double* d_init_host, double eps0,
+                  double adapt_target, int32_t* index_out, void* stream) {
+  HM_TRY(slotted_ok(s));
+  if (!job || !index_out) return fail(HM_EINVAL, "null argument");
+  if (!same_field_model(job, s->p0))
+    return fail(HM_EINVAL, "the job's grid, precision, device, box and power spectrum must be the state's");
+  if (job->n > s->slot_pts) return fail(HM_EINVAL, "catalogue larger than the room of a slot");
+  if (job->n > 0 && (!d_init_host || !job->rx.p)) return fail(HM_EINVAL, "catalogue and d_init_host required");
+  if (!(eps0 > 0) || !std::isfinite(eps0)) return fail(HM_EINVAL, "eps0 must be finite and > 0");
+  if (adapt_target != 0.0 && !(adapt_target > 0.0 && adapt_target < 1.0))
+    return fail(HM_EINVAL, "adapt_target must be 0 (off) or in (0, 1)");
+  if (s->C >= s->C_cap || s->free_regions.empty()) return fail(HM_ESTATE, "every slot is in use");
+  if (job->n > 0) HM_TRY(check_finite(d_init_host, job->n, "d_init"));
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  HM_CUDA(cudaSetDevice(s->device));
+  const int c = s->C;
+  const int r = s->free_regions.back();
+  const long long off = (long long)r * s->slot_pts;
+  const long long n = job->n;
+  if (n > 0) {
+    const size_t b = 8 * (size_t)n, o = 8 * (size_t)off;
+    const DevBuf* src[] = {&job->rx, &job->ry, &job->rz, &job->mu, &job->smu, &job->zobs, &job->scz};
+    DevBuf* dst[] = {&s->rx, &s->ry, &s->rz, &s->mu, &s->smu, &s->zobs, &s->scz};
+    for (int k = 0; k < 7; ++k)
+      HM_CUDA(cudaMemcpyAsync(static_cast<char*>(dst[k]->p) + o, src[k]->p, b, cudaMemcpyDeviceToDevice, st));
+    // pageable host sources: each copy has consumed its source when it returns
+    HM_CUDA(cudaMemcpyAsync(static_cast<char*>(s->d.p) + o, d_init_host, b, cudaMemcpyHostToDevice, st));
+    HM_CUDA(cudaMemsetAsync(static_cast<char*>(s->pd.p) + o, 0, b, st));
+  }
+  s->pp_host[c] = point_params(job, off);
+  HM_CUDA(cudaMemcpyAsync(s->pp.as<PointParams>() + c, &s->pp_host[c], sizeof(PointParams), cudaMemcpyHostToDevice,
+                          st));
+  ChainScal x{};
+  x.sample_d = 1;
+  x.eps = eps0;
+  HM_CUDA(cudaMemcpyAsync(s->cs.as<ChainScal>() + c, &x, sizeof(x), cudaMemcpyHostToDevice, st));
+  const int id = chain_id;
+  HM_CUDA(cudaMemcpyAsync(s->chain_id.as<int>() + c, &id, sizeof(int), cudaMemcpyHostToDevice, st));
+  const size_t gb = s->rsz * s->n3;
+  HM_CUDA(cudaMemsetAsync(static_cast<char*>(s->w.p) + gb * c, 0, gb, st));
+  HM_CUDA(cudaMemsetAsync(static_cast<char*>(s->pw.p) + gb * c, 0, gb, st));
+  s->free_regions.pop_back();
+  s->region_of[c] = r;
+  s->chain_prob[c] = job;
+  s->eps_host[c] = eps0;
+  s->C = c + 1;
+  if (adapt_target != 0.0) HM_CUDA(launch_da(1, 1, adapt_target, nullptr, s->cs.as<ChainScal>() + c, st));
+  HM_TRY(eval_chain(s, c, st));
+  *index_out = c;
+  return HM_OK;
+}
+
+int hm_slots_adapt_end(hm_state* s, int32_t index, double* eps_out_host, void* stream) {
+  HM_TRY(slotted_ok(s));
+  HM_TRY(chain_ok(s, index));
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  HM_CUDA(cudaSetDevice(s->device));
+  HM_CUDA(launch_da(1, 0, 0.0, s->eps_dev.as<double>() + index, s->cs.as<ChainScal>() + index, st));
+  double e = 0.0;
+  HM_CUDA(cudaMemcpyAsync(&e, s->eps_dev.as<double>() + index, 8, cudaMemcpyDeviceToHost, st));
+  HM_CUDA(cudaStreamSynchronize(st));
+  s->eps_host[index] = e;
+  if (eps_out_host) *eps_out_host = e;
+  return HM_OK;
+}
+
+int hm_slots_release(hm_state* s, int32_t index, int32_t* moved_from_out, void* stream) {
+  HM_TRY(slotted_ok(s));
+  HM_TRY(chain_ok(s, index));
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  HM_CUDA(cudaSetDevice(s->device));
+  const int j = s->C - 1;
+  s->free_regions.push_back(s->region_of[index]);
+  if (index != j) {
+    // the last active chain takes the released index: its grids, scalars
+    // and chain word move; its point region stays where it is
+    const size_t gb = s->rsz * s->n3;
+    DevBuf* grids[] = {&s->w, &s->pw, &s->gw};
+    for (DevBuf* b : grids)
+      HM_CUDA(cudaMemcpyAsync(static_cast<char*>(b->p) + gb * index, static_cast<char*>(b->p) + gb * j, gb,
+                              cudaMemcpyDeviceToDevice, st));
+    HM_CUDA(cudaMemcpyAsync(s->cs.as<ChainScal>() + index, s->cs.as<ChainScal>() + j, sizeof(ChainScal),
+                            cudaMemcpyDeviceToDevice, st));
+    HM_CUDA(cudaMemcpyAsync(s->chain_id.as<int>() + index, s->chain_id.as<int>() + j, sizeof(int),
+                            cudaMemcpyDeviceToDevice, st));
+    HM_CUDA(cudaMemcpyAsync(s->pp.as<PointParams>() + index, s->pp.as<PointParams>() + j, sizeof(PointParams),
+                            cudaMemcpyDeviceToDevice, st));
+    s->pp_host[index] = s->pp_host[j];
+    s->chain_prob[index] = s->chain_prob[j];
+    s->region_of[index] = s->region_of[j];
+    s->eps_host[index] = s->eps_host[j];
+  }
+  s->region_of[j] = -1;
+  s->chain_prob[j] = nullptr;
+  s->C = j;
+  if (moved_from_out) *moved_from_out = index != j ? j : -1;
+  return HM_OK;
+}
+
+int hm_slots_run(hm_state* s, int32_t n_traj, int32_t n_leapfrog, int32_t use_graph, hm_trace* trace_host,
+                 void* stream) {
+  HM_TRY(slotted_ok(s));
+  if (n_traj < 0 || n_leapfrog <= 0) return fail(HM_EINVAL, "n_traj >= 0 and n_leapfrog > 0 required");
+  if (s->C == 0 || n_traj == 0) return HM_OK;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  HM_CUDA(cudaSetDevice(s->device));
+  const size_t need = sizeof(hm_trace) * (size_t)n_traj * s->C_cap;
+  if (s->trace_cap < need) {
+    HM_TRY(s->trace_dev.alloc(need));
+    s->trace_cap = need;
+    s->drop_graphs();
+  }
+  HM_CUDA(launch_set_run(s->C, nullptr, 1, s->cs.as<ChainScal>(), st));
+  HM_TRY(run_traj_loop(s, n_traj, n_leapfrog, 1, use_graph, st));
+  if (trace_host) {
+    HM_CUDA(cudaMemcpyAsync(trace_host, s->trace_dev.p, sizeof(hm_trace) * (size_t)n_traj * s->C,
+                            cudaMemcpyDeviceToHost, st));
+    HM_CUDA(cudaStreamSynchronize(st));
   }
   return HM_OK;
 }
@@ -1364,6 +1602,7 @@ static int analytics_sample(hm_state* s, cudaStream_t st) {
 int hm_state_analytics(hm_state* s, int32_t enable, int32_t n_radii, const double* radii_host, int32_t max_samples,
                        void* stream) {
   if (!s) return fail(HM_EINVAL, "null state");
+  if (s->slotted) return fail(HM_ESTATE, "chain analytics are not available on a slotted state");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   HM_CUDA(cudaSetDevice(s->device));
   HM_CUDA(cudaStreamSynchronize(st));   // no sample in flight still uses the buffers
@@ -1502,10 +1741,7 @@ int hm_state_profile(hm_state* s, int32_t enable) {
   } else {
     HM_TRY(profile_collect(s));
     // a graph captured with profiling holds these events: drop it first
-    if (s->gexec && s->g_prof) {
-      cudaGraphExecDestroy(s->gexec);
-      s->gexec = nullptr;
-    }
+    s->drop_graphs(true);
     s->prof.reset();
   }
   return HM_OK;

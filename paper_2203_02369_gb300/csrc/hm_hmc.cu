@@ -341,7 +341,7 @@ __global__ void k_set_run(int n_chains, const double* __restrict__ eps, int samp
   pdl_trigger();
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= n_chains) return;
-  cs[c].eps = eps[c];
+  if (eps) cs[c].eps = eps[c];   // nullptr: every chain keeps its own step
   cs[c].sample_d = sample_d;
   cs[c].traj_run0 = cs[c].traj;
   cs[c].status = 0;

@@ -334,6 +334,98 @@ class State:
         return out.reshape(n_traj, self.C)
 
 
+class Slots:
+    """Slotted state for continuous batching: up to n_slots jobs of one grid
+    (the template's N, precision, box and P(k)) advance together, each
+    trajectory of every loaded job in the same kernel launches.  Jobs are
+    loaded and released between trajectories; loaded chains are packed at
+    indices 0..n_active-1 (a release moves the last one into the freed
+    index, which release() reports)."""
+
+    def __init__(self, template, n_slots, max_points, seed=0):
+        self.lib = template.lib
+        self.template = template
+        self.N, self.dtype, self.device = template.N, template.dtype, template.device
+        self.h = ct.c_void_p()
+        check(self.lib.hm_slots_create(template.h, int(n_slots), int(max_points), ct.c_uint64(int(seed)),
+                                       ct.byref(self.h)))
+        self.n_slots = int(n_slots)
+        self.max_points = int(max_points)
+        self.problems = []      # problem of each loaded index (the library reads its prior in place)
+        self._keep = []
+
+    def close(self):
+        if self.h:
+            self.lib.hm_destroy_state(self.h)
+            self.h = ct.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def n_active(self):
+        a, n = ct.c_int32(), ct.c_int32()
+        check(self.lib.hm_slots_count(self.h, ct.byref(a), ct.byref(n)))
+        return a.value
+
+    def load(self, problem, d_init, chain_id, eps0, adapt_target=0.0):
+        """Load a job; returns its chain index."""
+        d = np.ascontiguousarray(d_init, dtype=np.float64)
+        idx = ct.c_int32()
+        check(self.lib.hm_slots_load(self.h, problem.h, int(chain_id), _dptr(d) if d.size else None,
+                                     float(eps0), float(adapt_target), ct.byref(idx), _stream()))
+        assert idx.value == len(self.problems)
+        self.problems.append(problem)
+        return idx.value
+
+    def adapt_end(self, index):
+        e = np.zeros(1)
+        check(self.lib.hm_slots_adapt_end(self.h, int(index), _dptr(e), _stream()))
+        return float(e[0])
+
+    def release(self, index):
+        """Release a job; returns the old index of the chain now at `index`
+        (-1 if none moved)."""
+        mv = ct.c_int32()
+        check(self.lib.hm_slots_release(self.h, int(index), ct.byref(mv), _stream()))
+        last = self.problems.pop()
+        if mv.value >= 0:
+            self.problems[index] = last
+        return mv.value
+
+    def run(self, n_traj=1, n_leapfrog=20, use_graph=True):
+        """n_traj trajectories of every loaded job; trace [n_traj, n_active]."""
+        na = len(self.problems)
+        tr = (_lib.hm_trace * (max(n_traj, 1) * max(na, 1)))()
+        check(self.lib.hm_slots_run(self.h, int(n_traj), int(n_leapfrog), int(bool(use_graph)), tr, _stream()))
+        out = np.frombuffer(tr, dtype=TRACE_DTYPE, count=n_traj * na).copy()
+        return out.reshape(n_traj, na)
+
+    def get(self, index):
+        w = torch.empty((self.N,) * 3, dtype=self.dtype, device=self.device)
+        pw = torch.empty_like(w)
+        n = self.problems[index].n
+        d = torch.empty(n, dtype=torch.float64, device=self.device)
+        pd = torch.empty_like(d)
+        check(self.lib.hm_state_get(self.h, int(index), _ptr(w), _ptr(d), _ptr(pw), _ptr(pd), _stream()))
+        return dict(w=w, d=d, pw=pw, pd=pd)
+
+    def grad(self, index):
+        gw = torch.empty((self.N,) * 3, dtype=self.dtype, device=self.device)
+        gd = torch.empty(self.problems[index].n, dtype=torch.float64, device=self.device)
+        check(self.lib.hm_state_get_grad(self.h, int(index), _ptr(gw), _ptr(gd), _stream()))
+        return gw, gd
+
+    def scalars(self, index):
+        psi, kin, traj = ct.c_double(), ct.c_double(), ct.c_int64()
+        check(self.lib.hm_state_scalars(self.h, int(index), ct.byref(psi), ct.byref(kin), ct.byref(traj),
+                                        _stream()))
+        return dict(psi=psi.value, kinetic=kin.value, traj=traj.value)
+
+
 def philox(seed, n, c1, c2, c3, device=0):
     lib = _lib.load()
     out = torch.empty(4 * n, dtype=torch.int32, device=torch.device("cuda", device))

@@ -1,16 +1,29 @@
-"""Continuous-batching serving loop for HAMLET reconstruction jobs.
+"""Serving loops for HAMLET reconstruction jobs.
 
-Jobs (a catalogue on a grid, a number of HMC trajectories) arrive over time.
-A job is admitted as soon as a slot is free and its device-memory footprint
-fits the free memory minus a reserve; its chain state then stays resident
-on the device until it finishes.  Each slot is a worker thread with its own
-CUDA stream: the library's calls release the GIL, so the admitted jobs'
-trajectory graphs run concurrently on the GPU while the host admits new
-arrivals.  Reported: latency percentiles per trajectory and per job,
-aggregate gradient evaluations/s and effective samples/s.
+Jobs (a catalogue on a grid, a number of HMC trajectories) arrive over time
+and their chain states stay resident on the device until they finish.
+
+BatchedServingLoop is continuous batching: jobs that share a field model
+(grid, box, precision, leapfrog count) are served by one slotted state
+(libhamlet's hm_slots_*), which advances every loaded job in the same kernel
+launches, one captured CUDA graph per trajectory.  A job arriving while
+others run is prepared on a host thread and loaded into a free slot between
+two trajectories; a finished job leaves its slot at once.  Each group runs
+on its own host thread and CUDA stream, so groups of different grids overlap
+on the device.  A group's slot count is set when its first job arrives, from
+the free device memory minus a reserve (admission by footprint).
+
+ServingLoop runs each admitted job as a worker thread with its own CUDA
+stream (jobs overlap on the device, each in its own launches); with one slot
+it is the plain one-job-at-a-time baseline.
+
+Reported by both: latency percentiles per trajectory and per job, aggregate
+gradient evaluations/s and effective samples/s.
 """
 from __future__ import annotations
 
+import collections
+import concurrent.futures
 import queue
 import threading
 import time
@@ -21,7 +34,7 @@ import torch
 
 from . import mock
 from .ess import ess
-from .hamlet import Problem, State
+from .hamlet import Problem, Slots, State
 
 
 @dataclass
@@ -55,6 +68,16 @@ def footprint_bytes(N, n_points, precision="fp32"):
     R = rsz * N ** 3
     S = 2 * rsz * N * N * (N // 2 + 1)
     return 5 * R + 6 * S + n_points * 700 + (8 << 20)
+
+
+def slots_footprint_bytes(N, n_slots, max_points, precision="fp32"):
+    """Device memory of one slotted state: per slot five real grids and six
+    half spectra, per point of room about 300 B of catalogue, chain and
+    bucket arrays."""
+    rsz = 4 if precision == "fp32" else 8
+    R = rsz * N ** 3
+    S = 2 * rsz * N * N * (N // 2 + 1)
+    return n_slots * (5 * R + 6 * S) + n_slots * max_points * 300 + (16 << 20)
 
 
 class ServingLoop:
@@ -157,6 +180,264 @@ class ServingLoop:
             th.join()
         makespan = time.perf_counter() - t0
         return summarize(finished, makespan)
+
+
+def group_key(job):
+    """Jobs that can share a slotted state."""
+    sp = job.spec
+    return (sp.N, float(sp.L), sp.precision, job.n_leapfrog, tuple(sorted(vars(sp.cosmo).items())))
+
+
+class SlotsBackend:
+    """One slotted state on its own CUDA stream (the device side of a group)."""
+
+    def __init__(self, job, n_slots, max_points, seed, device=0, use_graph=True):
+        torch.cuda.set_device(device)
+        self.stream = torch.cuda.Stream(device=device)
+        sp = job.spec
+        self.n_leapfrog = job.n_leapfrog
+        self.use_graph = use_graph
+        with torch.cuda.stream(self.stream):
+            self.template = Problem(sp.N, sp.L, sp.cosmo, sp.sigma_nl, sp.precision, device=device)
+            self.slots = Slots(self.template, n_slots, max_points, seed=seed)
+
+    def load(self, job):
+        with torch.cuda.stream(self.stream):
+            return self.slots.load(job._prob, job._cat["d_init"], job.job_id, job.eps,
+                                   job.accept_target if job.adapt_warmup > 0 else 0.0)
+
+    def run(self, n_traj):
+        with torch.cuda.stream(self.stream):
+            return self.slots.run(n_traj, self.n_leapfrog, self.use_graph)
+
+    def adapt_end(self, index):
+        with torch.cuda.stream(self.stream):
+            return self.slots.adapt_end(index)
+
+    def get(self, index):
+        with torch.cuda.stream(self.stream):
+            g = self.slots.get(index)
+            self.stream.synchronize()
+            return g["w"].cpu(), g["d"].cpu()
+
+    def release(self, index):
+        with torch.cuda.stream(self.stream):
+            return self.slots.release(index)
+
+    def close(self):
+        with torch.cuda.stream(self.stream):
+            self.slots.close()
+            self.template.close()
+            self.stream.synchronize()
+
+
+def _prepare_job(job, device):
+    """Host side of an arrival: the catalogue and its problem (tables, copies)."""
+    torch.cuda.set_device(device)
+    job._cat = mock.make_catalog(job.spec)
+    job._prob = Problem.from_mock(job.spec, job._cat, device=device)
+    return job
+
+
+class BatchedServingLoop:
+    """Continuous batching over slotted states (see the module docstring).
+
+    backend_factory(job, n_slots) -> backend with load/run/adapt_end/get/
+    release/close, prepare(job) -> job and free_bytes() are injectable so the
+    scheduling can be exercised without a GPU.
+
+    While no job waits for a slot of a group, one call runs as many
+    trajectories (at most max_batch_traj) as the loaded job closest to an
+    event (end of its warm-up or of its run) still needs, so the host's
+    bookkeeping is paid once per call; the trajectory latency recorded is
+    the call's time divided by its trajectories."""
+
+    def __init__(self, max_slots=8, max_points=100_000, reserve_bytes=2 << 30, device=0, use_graph=True,
+                 keep_state=False, seed=0, backend_factory=None, prepare=None, free_bytes=None, prep_threads=2,
+                 max_batch_traj=4):
+        self.max_batch_traj = max(1, int(max_batch_traj))
+        self.max_slots = max_slots
+        self.max_points = max_points
+        self.reserve = reserve_bytes
+        self.device = device
+        self.keep_state = keep_state
+        self.seed = seed
+        self.backend_factory = backend_factory or (
+            lambda job, n: SlotsBackend(job, n, max_points, seed, device=device, use_graph=use_graph))
+        self.prepare = prepare or (lambda job: _prepare_job(job, device))
+        self.free_bytes = free_bytes or (lambda: torch.cuda.mem_get_info(self.device)[0])
+        self.prep_threads = prep_threads
+        self._cv = threading.Condition()
+        self.groups = {}            # key -> dict(backend, ready deque, slots, thread)
+        self.max_active_seen = 0
+        self.admission_log = []     # (time, job_id, group slots in use after admission)
+
+    def _group_worker(self, g, t0, done):
+        be = g["backend"]
+        active = {}                 # chain index -> job
+        while True:
+            with self._cv:
+                while not g["ready"] and not active and not g["stop"]:
+                    self._cv.wait(timeout=0.05)
+                if g["stop"] and not g["ready"] and not active:
+                    return
+                admit = []
+                while g["ready"] and len(active) + len(admit) < g["slots"]:
+                    admit.append(g["ready"].popleft())
+            for job in admit:
+                try:
+                    idx = be.load(job)
+                except Exception as exc:   # reported per job; the group keeps serving
+                    job.error = repr(exc)
+                    job.finished = time.perf_counter() - t0
+                    done.put(job)
+                    continue
+                job.admitted = time.perf_counter() - t0
+                job._warm = job.adapt_warmup
+                job.eps_used = job.eps
+                active[idx] = job
+                with self._cv:
+                    self.admission_log.append((job.admitted, job.job_id, len(active)))
+                    self.max_active_seen = max(self.max_active_seen, len(active))
+            if not active:
+                continue
+
+            def left(j):
+                return j._warm if j._warm > 0 else j.n_traj - len(j.traj_latency)
+            with self._cv:
+                waiting = bool(g["ready"])
+            k = 1 if waiting else max(1, min(self.max_batch_traj, min(left(j) for j in active.values())))
+            a = time.perf_counter()
+            try:
+                rows = be.run(k)
+            except Exception as exc:
+                for job in active.values():
+                    job.error = repr(exc)
+                    job.finished = time.perf_counter() - t0
+                    done.put(job)
+                active.clear()
+                continue
+            dt = (time.perf_counter() - a) / k
+            finished = []
+            for idx in sorted(active):
+                job = active[idx]
+                for t in range(k):
+                    rec = rows[t][idx]
+                    if job._warm > 0:
+                        job._warm -= 1
+                        if job._warm == 0:
+                            job.eps_used = be.adapt_end(idx)
+                        continue
+                    job.traj_latency.append(dt)
+                    job.psi.append(float(rec["psi"]))
+                    job.accept.append(int(rec["accept"]))
+                if len(job.traj_latency) >= job.n_traj:
+                    finished.append(idx)
+            # release from the highest index down: each release moves the
+            # last loaded chain into the freed index
+            for idx in sorted(finished, reverse=True):
+                job = active.pop(idx)
+                if self.keep_state:
+                    job.final_w, job.final_d = be.get(idx)
+                moved = be.release(idx)
+                if moved >= 0:
+                    active[idx] = active.pop(moved)
+                job.finished = time.perf_counter() - t0
+                prob = getattr(job, "_prob", None)
+                if prob is not None and hasattr(prob, "close"):
+                    prob.close()
+                done.put(job)
+
+    def _group_for(self, job, t0, done):
+        """The job's group, created (with its slot count from the free
+        memory) on first use; None while it does not fit."""
+        key = group_key(job)
+        g = self.groups.get(key)
+        if g is not None:
+            return g
+        sp = job.spec
+        per = slots_footprint_bytes(sp.N, 1, self.max_points, sp.precision)
+        room = self.free_bytes() - self.reserve - (16 << 20)
+        n = min(self.max_slots, int(room // per)) if room > 0 else 0
+        if n < 1:
+            return None
+        g = {"backend": self.backend_factory(job, n), "ready": collections.deque(), "slots": n, "stop": False}
+        g["thread"] = threading.Thread(target=self._group_worker, args=(g, t0, done), daemon=True)
+        self.groups[key] = g
+        g["thread"].start()
+        return g
+
+    def run(self, jobs):
+        """Serve `jobs` (arrival times in seconds from now); returns stats."""
+        pending = sorted(jobs, key=lambda j: j.arrival)
+        done = queue.Queue()
+        finished = []
+        blocked = []                # prepared jobs whose group does not fit yet
+        preps = []
+        t0 = time.perf_counter()
+        i = 0
+        pool = concurrent.futures.ThreadPoolExecutor(max_workers=self.prep_threads)
+        try:
+            while len(finished) < len(jobs):
+                now = time.perf_counter() - t0
+                while i < len(pending) and pending[i].arrival <= now:
+                    j = pending[i]
+                    i += 1
+                    if j.spec.n_points > self.max_points:
+                        j.error = f"catalogue of {j.spec.n_points} points exceeds the slot room {self.max_points}"
+                        j.finished = now
+                        finished.append(j)
+                        continue
+                    preps.append(pool.submit(self._prepare_safe, j))
+                still = []
+                for f in preps:
+                    if not f.done():
+                        still.append(f)
+                        continue
+                    j = f.result()
+                    if j.error:
+                        j.finished = time.perf_counter() - t0
+                        finished.append(j)
+                    else:
+                        blocked.append(j)
+                preps = still
+                keep = []
+                for j in blocked:
+                    g = self._group_for(j, t0, done)
+                    if g is None:
+                        if not self.groups:
+                            j.error = "does not fit in device memory"
+                            j.finished = time.perf_counter() - t0
+                            finished.append(j)
+                        else:
+                            keep.append(j)
+                        continue
+                    with self._cv:
+                        g["ready"].append(j)
+                        self._cv.notify_all()
+                blocked = keep
+                try:
+                    finished.append(done.get(timeout=0.002))
+                except queue.Empty:
+                    pass
+        finally:
+            pool.shutdown(wait=True)
+            with self._cv:
+                for g in self.groups.values():
+                    g["stop"] = True
+                self._cv.notify_all()
+            for g in self.groups.values():
+                g["thread"].join()
+                g["backend"].close()
+        makespan = time.perf_counter() - t0
+        return summarize(finished, makespan)
+
+    def _prepare_safe(self, job):
+        try:
+            return self.prepare(job)
+        except Exception as exc:   # reported per job; the loop keeps serving
+            job.error = repr(exc)
+            return job
 
 
 def summarize(jobs, makespan):

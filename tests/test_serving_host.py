@@ -75,3 +75,134 @@ def test_poisson_stream_shape():
     assert {j.spec.N for j in jobs} <= {64, 128}
     ns = [j.spec.n_points for j in jobs]
     assert min(ns) >= 1000 and max(ns) <= 100000
+
+
+# ---------------------------------------------------------------------------
+# continuous batching (BatchedServingLoop) with a fake slotted backend
+# ---------------------------------------------------------------------------
+from paper_2203_02369_gb300.serve import BatchedServingLoop, group_key  # noqa: E402
+
+
+class FakeSlots:
+    """Mirrors hm_slots_* bookkeeping: packed indices, release moves the last
+    loaded chain into the freed index; every trajectory advances all loaded jobs."""
+
+    instances = []
+
+    def __init__(self, job, n_slots):
+        self.key = group_key(job)
+        self.n_slots = n_slots
+        self.loaded = []          # job ids by chain index
+        self.runs = []            # job ids advanced together by each trajectory
+        self.closed = False
+        self.lock = threading.Lock()
+        FakeSlots.instances.append(self)
+
+    def load(self, job):
+        assert group_key(job) == self.key
+        assert len(self.loaded) < self.n_slots
+        self.loaded.append(job.job_id)
+        return len(self.loaded) - 1
+
+    def run(self, k):
+        time.sleep(0.002 * k)
+        rec = np.zeros((k, len(self.loaded)), dtype=[("psi", float), ("accept", np.int32)])
+        for t in range(k):
+            self.runs.append(tuple(self.loaded))
+            rec["psi"][t] = [float(j) for j in self.loaded]
+        rec["accept"] = 1
+        return rec
+
+    def adapt_end(self, index):
+        return 0.02
+
+    def get(self, index):
+        return None, None
+
+    def release(self, index):
+        last = len(self.loaded) - 1
+        if index != last:
+            self.loaded[index] = self.loaded[last]
+        self.loaded.pop()
+        return last if index != last else -1
+
+    def close(self):
+        self.closed = True
+
+
+def _bloop(**kw):
+    FakeSlots.instances = []
+    kw.setdefault("free_bytes", lambda: 1 << 40)
+    return BatchedServingLoop(reserve_bytes=0, backend_factory=FakeSlots, prepare=lambda j: j, **kw)
+
+
+import numpy as np  # noqa: E402
+
+
+def test_batched_jobs_share_launches_and_late_arrivals_join_running_groups():
+    loop = _bloop(max_slots=4)
+    jobs = [_job(k, N=64, arrival=0.0 if k < 2 else 0.03, n_traj=20) for k in range(4)]
+    stats = loop.run(jobs)
+    assert stats["jobs"] == 4 and not stats["errors"]
+    (be,) = FakeSlots.instances           # one field model, one slotted state
+    assert be.closed
+    # continuous batching: late arrivals were loaded while the first two ran
+    assert any(len(r) == 4 for r in be.runs)
+    assert any(len(r) == 2 for r in be.runs)
+    for j in jobs:
+        assert len(j.traj_latency) == 20 and j.psi == [float(j.job_id)] * 20
+        assert j.admitted >= j.arrival and j.finished >= j.admitted
+
+
+def test_batched_groups_by_field_model_and_bounds_slots():
+    loop = _bloop(max_slots=2)
+    jobs = [_job(k, N=64 if k % 2 else 128, arrival=0.001 * k, n_traj=5) for k in range(8)]
+    stats = loop.run(jobs)
+    assert stats["jobs"] == 8 and not stats["errors"]
+    assert len(FakeSlots.instances) == 2
+    for be in FakeSlots.instances:
+        assert max(len(r) for r in be.runs) <= 2
+        assert len({group_key(j) for j in jobs if j.spec.N == (64 if be.key[0] == 64 else 128)}) == 1
+    assert loop.max_active_seen <= 2
+
+
+def test_batched_release_moves_keep_each_jobs_records_its_own():
+    # jobs of different lengths leave from the middle of the packed indices
+    loop = _bloop(max_slots=4)
+    jobs = [_job(k, N=64, arrival=0.0, n_traj=3 + 4 * k) for k in range(4)]
+    stats = loop.run(jobs)
+    assert not stats["errors"]
+    for j in jobs:
+        assert j.psi == [float(j.job_id)] * j.n_traj
+
+
+def test_batched_warmup_trajectories_are_not_timed():
+    loop = _bloop(max_slots=2)
+    j = _job(0, N=64, n_traj=4)
+    j.adapt_warmup = 3
+    loop.run([j])
+    (be,) = FakeSlots.instances
+    assert len(be.runs) == 7 and len(j.traj_latency) == 4 and j.eps_used == 0.02
+
+
+def test_batched_slot_count_follows_free_memory_and_oversize_jobs_fail():
+    from paper_2203_02369_gb300.serve import slots_footprint_bytes
+    per = slots_footprint_bytes(128, 1, 1000)
+    loop = _bloop(max_slots=8, max_points=1000, free_bytes=lambda: 3 * per)
+    jobs = [_job(k, N=128, n=500, n_traj=2) for k in range(5)] + [_job(9, N=128, n=5000, n_traj=2)]
+    stats = loop.run(jobs)
+    assert FakeSlots.instances[0].n_slots == 2
+    assert len(stats["errors"]) == 1 and "exceeds the slot room" in stats["errors"][0]
+
+
+def test_batched_failing_prepare_is_reported():
+    FakeSlots.instances = []
+
+    def prep(j):
+        if j.job_id == 1:
+            raise RuntimeError("injected catalogue failure")
+        return j
+
+    loop = BatchedServingLoop(reserve_bytes=0, backend_factory=FakeSlots, prepare=prep, free_bytes=lambda: 1 << 40)
+    stats = loop.run([_job(k, n_traj=2) for k in range(3)])
+    assert stats["jobs"] == 3 and len(stats["errors"]) == 1 and "injected" in stats["errors"][0]
