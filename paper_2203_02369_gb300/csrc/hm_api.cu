@@ -508,7 +508,7 @@ int hm_init_problem(const hm_problem_desc* desc, hm_problem** out) {
   const hm_problem_desc& d = *desc;
   if (d.precision != HM_FP32 && d.precision != HM_FP64) return fail(HM_EINVAL, "precision must be HM_FP32 or HM_FP64");
   if (!fft_supported(d.precision, d.N)) return fail(HM_EINVAL, "unsupported grid size N for this precision");
-  if (d.N * plane_split(d.N) >= 2048) return fail(HM_EINVAL, "too many point buckets per chain for this N");
+  if (d.N * plane_split(d.N) >= kMaxBuckets) return fail(HM_EINVAL, "too many point buckets per chain for this N");
   if (!(d.L > 0) || !(d.omega_m > 0) || !(d.omega_b > 0) || !(d.h > 0) || !(d.sigma8 > 0) ||
       !(d.T_cmb > 0) || !std::isfinite(d.n_s) || !(d.sigma_nl >= 0))
     return fail(HM_EINVAL, "bad cosmology or box parameters");

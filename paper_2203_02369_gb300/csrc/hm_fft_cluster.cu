@@ -1,8 +1,11 @@
 // Plane passes for grids whose x-plane does not fit one CTA's shared memory
-// (N = 256): a thread-block cluster of four CTAs per plane.  CTA q owns N/4
+// (N = 256): a thread-block cluster of eight CTAs per plane.  CTA q owns N/8
 // real rows (two packed per complex row) for the z transform; the CTAs then
 // exchange their row slabs for column slabs through distributed shared
-// memory and each runs the y transform of about (N/2+1)/4 columns.  The
+// memory and each runs the y transform of about (N/2+1)/8 columns.  At 66 KB
+// of shared memory and ~75 registers a thread, three CTAs share an SM (at
+// four CTAs a plane one 134 KB CTA filled an SM, which left it short of
+// warps).  The
 // point work of a plane (CIC gather after the inverse, CIC scatter before the
 // forward) and the field's leapfrog epilogue are the same as in the
 // single-CTA plane passes; a point's corner in the next CTA's row is read or
@@ -25,7 +28,7 @@ enum C2RModeCl : int { C2R_STORE = 0, C2R_EPI = 1, C2R_GATHER = 2 };
 template <int N> struct ClCfg {
   static constexpr int NH = N / 2 + 1;
   static constexpr int ZP = 2 * NH;           // pitch of a packed row (= two half-spectrum rows)
-  static constexpr int K = 4;                 // CTAs per plane (cluster size)
+  static constexpr int K = 8;                 // CTAs per plane (cluster size)
   static constexpr int RQ = N / K;            // real rows per CTA
   static constexpr int PR = RQ / 2;           // packed rows per CTA
   static constexpr int CW = (NH + K - 1) / K; // most half-spectrum columns of one CTA
@@ -486,7 +489,11 @@ static cudaError_t prepare_cl_t() {
   return cudaFuncSetAttribute(k_plane_c2r_cl<T, N, C2R_GATHER>, A, sp);
 }
 
-cudaError_t plane_cl_prepare() { return prepare_cl_t<float, 256>(); }
+cudaError_t plane_cl_prepare() {
+  // the point sub-buckets of a plane are the cluster's row slabs
+  if (plane_split(256) != ClCfg<256>::K) return cudaErrorInvalidConfiguration;
+  return prepare_cl_t<float, 256>();
+}
 
 cudaError_t launch_plane_r2c_cl(const void* in, long long in_stride, void* out, long long out_stride, int count,
                                 const void* tw, const PlanePoints* pts, cudaStream_t st) {

@@ -537,9 +537,14 @@ k_plane_c2r(const cplx<T>* __restrict__ in, long long in_stride, T* __restrict__
 // memory.
 // ---------------------------------------------------------------------------
 constexpr int kTC = 16;       // (ky, kz) columns per tile
-constexpr int kPencilNT = 128;
+// Threads of a pencil CTA: 128, or 256 at N = 256, where the three
+// component tiles (96 KB) let only two CTAs share an SM and every thread
+// then takes one stage-1 group instead of two.
+template <int N> struct PencilNT { static constexpr int v = N >= 256 ? 256 : 128; };
 
-template <typename T> struct PencilMinB { static constexpr int v = sizeof(T) == 4 ? 4 : 2; };
+template <typename T, int N> struct PencilMinB {
+  static constexpr int v = N >= 256 ? 2 : (sizeof(T) == 4 ? 4 : 2);
+};
 
 // Stage 1 of the x transform for group (t, m), operands read from global
 // memory (zero for a column past the end), result to the component buffer.
@@ -567,12 +572,12 @@ __device__ __forceinline__ void px_s2_smem(cplx<T>* buf) {
   constexpr int R1 = Radix<N>::R1, M = Radix<N>::M;
   if constexpr (M > 1) {
     constexpr int G2 = kTC * R1;
-    constexpr int PER = (G2 + kPencilNT - 1) / kPencilNT;
+    constexpr int PER = (G2 + PencilNT<N>::v - 1) / PencilNT<N>::v;
     C a[PER][M];
 #pragma unroll
     for (int i = 0; i < PER; ++i) {
-      const int g = threadIdx.x + i * kPencilNT;
-      if (G2 % kPencilNT == 0 || g < G2) {
+      const int g = threadIdx.x + i * PencilNT<N>::v;
+      if (G2 % PencilNT<N>::v == 0 || g < G2) {
         const int t = g % kTC, k2 = g / kTC;
 #pragma unroll
         for (int m = 0; m < M; ++m) a[i][m] = buf[(M * k2 + m) * W + t];
@@ -582,8 +587,8 @@ __device__ __forceinline__ void px_s2_smem(cplx<T>* buf) {
     __syncthreads();
 #pragma unroll
     for (int i = 0; i < PER; ++i) {
-      const int g = threadIdx.x + i * kPencilNT;
-      if (G2 % kPencilNT == 0 || g < G2) {
+      const int g = threadIdx.x + i * PencilNT<N>::v;
+      if (G2 % PencilNT<N>::v == 0 || g < G2) {
         const int t = g % kTC, k2 = g / kTC;
 #pragma unroll
         for (int k1 = 0; k1 < M; ++k1) buf[(k2 + R1 * k1) * W + t] = a[i][k1];
@@ -600,7 +605,7 @@ __device__ __forceinline__ void px_s2_global(const cplx<T>* buf, cplx<T>* __rest
   using C = cplx<T>;
   constexpr int R1 = Radix<N>::R1, M = Radix<N>::M, NCOL = N * (N / 2 + 1);
 #pragma unroll 1
-  for (int g = threadIdx.x; g < kTC * R1; g += kPencilNT) {
+  for (int g = threadIdx.x; g < kTC * R1; g += PencilNT<N>::v) {
     const int t = g % kTC, k2 = g / kTC;
     C a[M];
 #pragma unroll
@@ -637,7 +642,7 @@ template <int N> __device__ __forceinline__ ColGeom<N> col_geom(long long col) {
 // plane x is nonzero when bucket x or x-1 is non-empty.  plane_off ==
 // nullptr reads every plane.
 template <typename T, int N, int MODE>
-__global__ void __launch_bounds__(kPencilNT, PencilMinB<T>::v)
+__global__ void __launch_bounds__(PencilNT<N>::v, PencilMinB<T, N>::v)
 k_pencil(const cplx<T>* __restrict__ in, long long in_stride, cplx<T>* __restrict__ out,
          long long out_stride, const cplx<T>* __restrict__ tw, const T* __restrict__ amp,
          const int* __restrict__ plane_off, int ksplit) {
@@ -653,7 +658,7 @@ k_pencil(const cplx<T>* __restrict__ in, long long in_stride, cplx<T>* __restric
     if (plane_off != nullptr) {
       const int* o = plane_off + (long long)blockIdx.y * (N * ksplit + 1);
       const int lane = threadIdx.x & 31;
-      for (int x0 = (threadIdx.x >> 5) * 32; x0 < N; x0 += kPencilNT) {
+      for (int x0 = (threadIdx.x >> 5) * 32; x0 < N; x0 += PencilNT<N>::v) {
         const int x = x0 + lane, xm = (x + N - 1) & (N - 1);
         const bool on = x < N && ((o[(x + 1) * ksplit] != o[x * ksplit]) || (o[(xm + 1) * ksplit] != o[xm * ksplit]));
         const unsigned word = __ballot_sync(0xffffffffu, on);
@@ -677,7 +682,7 @@ k_pencil(const cplx<T>* __restrict__ in, long long in_stride, cplx<T>* __restric
   const int s = blockIdx.y;
   // first transform (forward; inverse for PM_INV), stage 1 from global memory
 #pragma unroll 1
-  for (int g = threadIdx.x; g < NIN * kTC * M; g += kPencilNT) {
+  for (int g = threadIdx.x; g < NIN * kTC * M; g += PencilNT<N>::v) {
     const int t = g % kTC, m = (g / kTC) % M, j = g / (kTC * M);
     const long long col = c0 + t;
     // rows m + M jj of this group: word (M jj) / 32, bit m + (M jj) % 32
@@ -702,7 +707,7 @@ k_pencil(const cplx<T>* __restrict__ in, long long in_stride, cplx<T>* __restric
     if constexpr (MODE == PM_SCALE) {
       // real weight amp[n^2] applied as the inverse's first stage loads
 #pragma unroll 1
-      for (int g = threadIdx.x; g < kTC * M; g += kPencilNT) {
+      for (int g = threadIdx.x; g < kTC * M; g += PencilNT<N>::v) {
         const int t = g % kTC, m = g / kTC;
         const long long col = c0 + t;
         const ColGeom<N> cg = col_geom<N>(col < NCOL ? col : 0);
@@ -728,7 +733,7 @@ k_pencil(const cplx<T>* __restrict__ in, long long in_stride, cplx<T>* __restric
       for (int q = 0; q < 3; ++q) {
         const int jo = q == 2 ? 0 : q + 1;
 #pragma unroll 1
-        for (int g = threadIdx.x; g < kTC * M; g += kPencilNT) {
+        for (int g = threadIdx.x; g < kTC * M; g += PencilNT<N>::v) {
           const int t = g % kTC, m = g / kTC;
           const long long col = c0 + t;
           const ColGeom<N> cg = col_geom<N>(col < NCOL ? col : 0);
@@ -754,7 +759,7 @@ k_pencil(const cplx<T>* __restrict__ in, long long in_stride, cplx<T>* __restric
     } else {
       // PM_ADJ: -i amp sum_j n_j s_j, written over component 0
 #pragma unroll 1
-      for (int g = threadIdx.x; g < kTC * M; g += kPencilNT) {
+      for (int g = threadIdx.x; g < kTC * M; g += PencilNT<N>::v) {
         const int t = g % kTC, m = g / kTC;
         const long long col = c0 + t;
         const ColGeom<N> cg = col_geom<N>(col < NCOL ? col : 0);
@@ -812,19 +817,19 @@ static cudaError_t pencil_t(const void* in, long long in_stride, void* out, long
   constexpr int NCOMP = (MODE == PM_VEL || MODE == PM_ADJ) ? 3 : 1;
   constexpr size_t sm = sizeof(cplx<T>) * N * NCOMP * kTC;
   dim3 grid((N * NH + kTC - 1) / kTC, count);
-  return launch_k<PDL_PENCIL>(k_pencil<T, N, MODE>, grid, dim3(kPencilNT), sm, st, static_cast<const cplx<T>*>(in), in_stride,
+  return launch_k<PDL_PENCIL>(k_pencil<T, N, MODE>, grid, dim3(PencilNT<N>::v), sm, st, static_cast<const cplx<T>*>(in), in_stride,
                   static_cast<cplx<T>*>(out), out_stride, static_cast<const cplx<T>*>(tw),
                   static_cast<const T*>(amp), plane_off, ksplit);
 }
 
 // Supported grids: N in {8, 16, 32, 64, 128} at both precisions (one x-plane
 // of the half spectrum fits one CTA's shared memory), and N = 256 at FP32
-// (plane passes as 4-CTA clusters, hm_fft_cluster.cu).
+// (plane passes as 8-CTA clusters, hm_fft_cluster.cu).
 bool fft_supported(int prec, int N) {
   return N == 8 || N == 16 || N == 32 || N == 64 || N == 128 || (N == 256 && prec == 0);
 }
 
-int plane_split(int N) { return N == 256 ? 4 : 1; }
+int plane_split(int N) { return N == 256 ? 8 : 1; }
 
 #define HM_DISPATCH_N(PREC, N, CALL_F, CALL_D)                          \
   do {                                                                  \

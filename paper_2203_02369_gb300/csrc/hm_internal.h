@@ -45,6 +45,9 @@ template <int N> struct PlaneSplit {
   static constexpr int K = 1;
 };
 int plane_split(int N);
+// Most point sub-buckets per chain (N * plane_split(N) must stay below it):
+// the placement kernel scans the bucket counts of a chain in shared memory.
+constexpr int kMaxBuckets = 4096;
 
 // Per-chain constants of the point likelihood (device resident).
 struct PointParams {

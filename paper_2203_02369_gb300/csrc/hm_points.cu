@@ -92,7 +92,7 @@ __global__ void __launch_bounds__(kPtsNT)
 k_points_place(const PointParams* __restrict__ pp, PointArrays pa, ChainScal* __restrict__ cs) {
   pdl_wait();
   pdl_trigger();
-  constexpr int kMaxNB = 2048;          // sub-buckets per chain (N * ksplit)
+  constexpr int kMaxNB = kMaxBuckets;   // sub-buckets per chain (N * ksplit)
   constexpr int PERT = kMaxNB / kPtsNT;
   __shared__ int excl[kMaxNB + 1];   // written for b <= NB < kMaxNB
   __shared__ int wsum[kPtsNT / 32];

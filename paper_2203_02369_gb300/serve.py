@@ -444,13 +444,20 @@ def summarize(jobs, makespan):
     lat = np.array([x for j in jobs for x in j.traj_latency]) if jobs else np.zeros(0)
     job_lat = np.array([j.finished - j.arrival for j in jobs])
     evals = sum(len(j.traj_latency) * j.n_leapfrog for j in jobs)
-    ess_sum = sum(ess(np.array(j.psi)) for j in jobs if len(j.psi) >= 4)
+    evals_all = sum((len(j.traj_latency) + j.adapt_warmup) * j.n_leapfrog for j in jobs if not j.error)
+    ess_job = [(j, ess(np.array(j.psi))) for j in jobs if len(j.psi) >= 4]
+    ess_sum = sum(e for _, e in ess_job)
+    # seconds of a job's residence on the device per effective sample it drew
+    per_es = np.array([(j.finished - j.admitted) / e for j, e in ess_job if e > 0])
     acc = np.concatenate([np.array(j.accept) for j in jobs]) if jobs else np.zeros(0)
     return {
         "jobs": len(jobs), "errors": [j.error for j in jobs if j.error],
         "makespan_s": makespan,
         "grad_evals_per_s": evals / makespan if makespan > 0 else None,
+        "grad_evals_per_s_incl_warmup": evals_all / makespan if makespan > 0 else None,
         "ess_per_s": ess_sum / makespan if makespan > 0 else None,
+        "seconds_per_effective_sample": {"p50": float(np.percentile(per_es, 50)) if per_es.size else None,
+                                         "p99": float(np.percentile(per_es, 99)) if per_es.size else None},
         "trajectory_latency_ms": {"p50": float(np.percentile(lat, 50) * 1e3) if lat.size else None,
                                   "p99": float(np.percentile(lat, 99) * 1e3) if lat.size else None},
         "job_latency_s": {"p50": float(np.percentile(job_lat, 50)) if job_lat.size else None,

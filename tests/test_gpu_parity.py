@@ -302,7 +302,8 @@ def test_sampled_sigma_nl_gradient_and_leapfrog_vs_oracle(H):
 
 
 def test_logpost_grad_256_cluster_planes(H):
-    """256^3 (box 1000 Mpc/h), 2e4 points: the 4-CTA cluster plane passes."""
+    """256^3 (box 1000 Mpc/h), 2e4 points: the 8-CTA cluster plane passes,
+    the posterior gradient and one trajectory against the oracle's."""
     spec = mock.MockSpec(N=256, L=1000.0, n_points=20000, r_max=300.0, mask_deg=10.0, sigma_mu=(0.2, 0.45),
                          sigma_nl=250.0, seed=81)
     cat = mock.make_catalog(spec)
@@ -318,5 +319,8 @@ def test_logpost_grad_256_cluster_planes(H):
     v = gp.velocity_field(torch.tensor(w, device="cuda")).cpu().numpy()
     assert rel(v, O.velocity_field(op, w)) < 1e-5
     st = H.State(gp, [d], seed=3)
+    tr = st.run_chain(1, 3, 0.01, use_graph=True)
+    _, _, recs = O.run_chain(op, np.zeros((256,) * 3), d, seed=3, chain=0, traj0=0, n_traj=1, eps=0.01, n_steps=3)
+    assert abs(tr[0, 0]["H_new"] - recs[0]["H_new"]) <= 1e-5 * abs(recs[0]["H_new"])
     tr = st.run_chain(2, 5, 0.01, use_graph=True)
     assert np.all(np.isfinite(tr[:, 0]["H_new"]))
