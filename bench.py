@@ -239,6 +239,19 @@ def run_oracle_steps(n_steps, eps):
     return time.perf_counter() - t0, n_steps
 
 
+def replica_aggregate(my_ms, units_per_rank, ws, device="cpu"):
+    """Whole-job throughput of independent replicas: the slowest rank's timed
+    milliseconds (max over ranks, the only collective of the run) and all
+    ranks' units divided by that time."""
+    import torch
+    t = torch.tensor([float(my_ms)], dtype=torch.float64, device=device)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    max_ms = float(t.item())
+    return max_ms, ws * units_per_rank / (max_ms / 1e3)
+
+
 def reference_arm(args):
     ws, rank, _ = dist_env()
     if rank != 0:
@@ -497,12 +510,7 @@ def main():
     state.profile(False)
 
     # max over ranks of the timed device time
-    tot = torch.tensor([my_ms], dtype=torch.float64, device=dev)
-    if ws > 1:
-        dist.all_reduce(tot, op=dist.ReduceOp.MAX)
-    max_ms = float(tot.item())
-    evals = ws * args.steps * L
-    value = evals / (max_ms / 1e3)
+    max_ms, value = replica_aggregate(my_ms, args.steps * L, ws, dev)
 
     # ESS/s on the Psi trace of a continuing chain (no flush between trajectories)
     ess_info = None

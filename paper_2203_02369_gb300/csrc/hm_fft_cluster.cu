@@ -5,11 +5,12 @@
 // memory and each runs the y transform of about (N/2+1)/8 columns.  At 66 KB
 // of shared memory and ~75 registers a thread, three CTAs share an SM (at
 // four CTAs a plane one 134 KB CTA filled an SM, which left it short of
-// warps).  The
-// point work of a plane (CIC gather after the inverse, CIC scatter before the
-// forward) and the field's leapfrog epilogue are the same as in the
-// single-CTA plane passes; a point's corner in the next CTA's row is read or
-// atomically added through DSMEM.
+// warps).  The point work of a plane (CIC gather after the inverse, CIC
+// scatter before the forward) and the field's leapfrog epilogue are the same
+// as in the single-CTA plane passes; a point's corner in the next CTA's row
+// is read or atomically added through DSMEM.  The loops that read global or
+// distributed shared memory are unrolled so that each thread keeps several
+// loads in flight (the passes stalled on load latency).
 #include <cooperative_groups.h>
 
 #include "hm_fft.cuh"
@@ -135,6 +136,7 @@ template <typename T, int N>
 __device__ __forceinline__ void load_rows_packed_cl(cplx<T>* R, const T* __restrict__ src) {
   using P = ClCfg<N>;
   constexpr int ITEMS = P::PR * (N / 2);
+  #pragma unroll 8
   for (int e = threadIdx.x; e < ITEMS; e += P::NT) {
     const int r = e / (N / 2), z = 2 * (e % (N / 2));
     if constexpr (sizeof(T) == 4) {
@@ -271,6 +273,7 @@ k_plane_r2c_cl(const T* __restrict__ in, long long in_stride, cplx<T>* __restric
   int c0, c1;
   own_columns_cl<N>(q, c0, c1);
   const int nc = c1 - c0;
+  #pragma unroll 17
   for (int e = threadIdx.x; e < N * P::CW; e += NT) {
     const int y = e / P::CW, cc = e % P::CW;
     C v = C{(T)0, (T)0};
@@ -283,6 +286,7 @@ k_plane_r2c_cl(const T* __restrict__ in, long long in_stride, cplx<T>* __restric
   cl.sync();   // remote reads done before any CTA moves on or exits
   fft_smem<T, N, false, P::CW, NT, true>(Cs, 1, CWP, tw);
   C* dst = out + (long long)s * out_stride + (long long)ix * N * NH;
+  #pragma unroll 4
   for (int e = threadIdx.x; e < N * nc; e += NT) {
     const int y = e / nc, cc = e % nc;
     dst[y * NH + c0 + cc] = Cs[y * CWP + cc];
@@ -324,6 +328,7 @@ k_plane_c2r_cl(const cplx<T>* __restrict__ in, long long in_stride, T* __restric
   own_columns_cl<N>(q, c0, c1);
   const int nc = c1 - c0;
   const C* src = in + (long long)s * in_stride + (long long)ix * N * NH;
+  #pragma unroll 17
   for (int e = threadIdx.x; e < N * P::CW; e += NT) {
     const int y = e / P::CW, cc = e % P::CW;
     Cs[y * CWP + cc] = cc < nc ? src[y * NH + c0 + cc] : C{(T)0, (T)0};
@@ -331,6 +336,7 @@ k_plane_c2r_cl(const cplx<T>* __restrict__ in, long long in_stride, T* __restric
   __syncthreads();
   fft_smem<T, N, true, P::CW, NT, true>(Cs, 1, CWP, tw);
   cl.sync();   // every CTA of the cluster is running before remote stores
+  #pragma unroll 4
   for (int e = threadIdx.x; e < N * nc; e += NT) {
     const int y = e / nc, cc = e % nc;
     const int o = y / RQ;
@@ -392,6 +398,7 @@ k_plane_c2r_cl(const cplx<T>* __restrict__ in, long long in_stride, T* __restric
     const T eps = (T)epi.cs[s].eps;
     const T ck = (mode == GM_KICK_DRIFT) ? eps : (T)0.5 * eps;
     HalfSqAcc<T> aw, ap;
+    #pragma unroll 4
     for (int e = threadIdx.x; e < ITEMS; e += NT) {
       const int r = e / (N / 2), z = 2 * (e % (N / 2));
       T g[4];
@@ -453,6 +460,7 @@ k_plane_c2r_cl(const cplx<T>* __restrict__ in, long long in_stride, T* __restric
       fft_smem<T, N, false, P::PR, NT, false>(R, P::ZP, 1, tw);
       unpack_rows_cl<T, N>(R);
       cl.sync();
+      #pragma unroll 17
       for (int e = threadIdx.x; e < N * P::CW; e += NT) {
         const int y = e / P::CW, cc = e % P::CW;
         C v = C{(T)0, (T)0};
@@ -465,6 +473,7 @@ k_plane_c2r_cl(const cplx<T>* __restrict__ in, long long in_stride, T* __restric
       cl.sync();
       fft_smem<T, N, false, P::CW, NT, true>(Cs, 1, CWP, tw);
       C* dst = next + (long long)s * next_stride + (long long)ix * N * NH;
+      #pragma unroll 4
       for (int e = threadIdx.x; e < N * nc; e += NT) {
         const int y = e / nc, cc = e % nc;
         dst[y * NH + c0 + cc] = Cs[y * CWP + cc];
