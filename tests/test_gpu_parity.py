@@ -136,6 +136,17 @@ def test_logpost_grad_128_paper_scale_sampled(H):
     assert rel(gd.cpu().numpy(), rgd) < 1e-5
 
 
+def test_logpost_grad_128_fp64(H):
+    """128^3 on the FP64 path (the largest FP64 grid), 1e4 points, 1e-12."""
+    spec, cat, gp, op, w = make_case(H, 128, 500.0, 10000, "fp64", 21, mask=10.0, r_max=160.0)
+    d = cat["d_init"]
+    psi, gw, gd = gp.logpost_grad(torch.tensor(w, device="cuda"), torch.tensor(d, device="cuda"))
+    rpsi, rgw, rgd = O.logpost_grad(op, w, d)
+    assert abs(psi.item() - rpsi) <= 1e-12 * abs(rpsi)
+    assert rel(gw.cpu().numpy(), rgw) < 1e-12
+    assert rel(gd.cpu().numpy(), rgd) < 1e-12
+
+
 def test_empty_catalog_is_prior_only(H):
     p = H.Problem(16, 100.0, precision="fp64", prior=("power", 2.0, 0.5, 40.0))
     p.set_catalog(np.zeros((0, 3)), np.zeros(0), np.zeros(0), np.zeros(0))
@@ -157,9 +168,9 @@ def test_out_of_support_distance_is_infinite(H):
 
 
 # ------------------------------------------------------- index work ----
-@pytest.mark.parametrize("N", [16, 64])
+@pytest.mark.parametrize("N", [16, 64, 128, 256])
 def test_cells_and_sort_bit_exact(H, N):
-    spec, cat, gp, op, w = make_case(H, N, 400.0, 3001, "fp64" if N == 16 else "fp32", 11)
+    spec, cat, gp, op, w = make_case(H, N, 400.0, 3001 if N < 128 else 30000, "fp64" if N == 16 else "fp32", 11)
     d = cat["d_init"]
     cell, perm = gp.cells(torch.tensor(d, device="cuda"))
     lin, order = O.cell_sort_order(op, d)
