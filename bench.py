@@ -24,6 +24,7 @@ import math
 import os
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -78,7 +79,8 @@ class Clocks:
     def __init__(self, gpu_index):
         self.gpu = gpu_index
         self.p = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
+        self.path = os.path.join(os.environ.get("HM_CLOCKS_DIR", tempfile.gettempdir()),
+                                 f"clocks_bench_{os.getpid()}.csv")
 
     def start(self):
         try:
@@ -213,7 +215,7 @@ def ncu_traffic(kind):
 # --------------------------------------------------------------------------
 def oracle_problem():
     from oracle import hamlet_oracle as O
-    spec = mock.PRESETS["cfg3_128"]
+    spec = mock.PRESETS["grid128_30000pts"]
     cat = mock.make_catalog(spec)
     op = O.problem_from_catalog(spec.N, spec.L, mock.spec_dict(spec)["cosmo"], spec.sigma_nl, cat)
     return O, spec, cat, op
@@ -460,7 +462,7 @@ def main():
         torch.cuda.set_device(local)
         dist.init_process_group("nccl", init_method="env://")
     dev = torch.cuda.current_device()
-    spec = mock.PRESETS["cfg3_128"]
+    spec = mock.PRESETS["grid128_30000pts"]
     cat = mock.make_catalog(spec)
     prob = Problem.from_mock(spec, cat, device=dev)
     state = State(prob, [cat["d_init"]], seed=1000 + rank, chain_ids=[rank])

@@ -12,7 +12,7 @@ Everything is float64 numpy.  Library primitives used as single steps:
 the tests), ``numpy.linalg`` (dense Wiener-filter solve).  No blocking, fusion
 or reordering beyond what the equations state.
 
-Readings of points the paper leaves open (each one is listed in the design doc):
+Readings of points the paper leaves open (the CUDA path takes the same ones):
   * DFT forward is unnormalised with e^{-ik.x}; IDFT carries 1/N^3.  With this
     convention the linear velocity (eq. vel-field) is v_k = +i aHf k/k^2 delta_k,
     which is the sign that gives div v = -aHf delta (linear continuity).

@@ -4,8 +4,8 @@ This module is the ONE input source shared by the CUDA path and the CPU oracle.
 It holds none of the posterior's arithmetic: it only draws random numbers with
 the shapes, sizes and distributions of the paper's mock surveys (section
 "Mock Catalogue construction": observer at the box centre, isotropic
-directions, a radial cut at 160 Mpc/h, 7.5k-30k points; the BASELINE presets
-below fix the rest) and turns them into observables with first-order,
+directions, a radial cut at 160 Mpc/h, 7.5k-30k points; the presets below
+-- 16^3, 64^3 and 128^3 workloads and the batched catalogues -- fix the rest) and turns them into observables with first-order,
 textbook relations (luminosity distance ~ distance, cz ~ H0 d + v_pec).  The
 posterior absorbs that small mismatch with its own second-order relations.
 
@@ -51,11 +51,11 @@ class MockSpec:
 # Presets with the sizes of the paper's mocks (PAPER "Mock Catalogue
 # construction") as fixed for this build's workloads.
 PRESETS = {
-    "cfg1_16": MockSpec(N=16, L=200.0, n_points=500, r_max=80.0, mask_deg=0.0,
+    "grid16_500pts_fp64": MockSpec(N=16, L=200.0, n_points=500, r_max=80.0, mask_deg=0.0,
                         sigma_mu=(0.2, 0.2), sigma_nl=150.0, seed=0, precision="fp64"),
-    "cfg2_64": MockSpec(N=64, L=500.0, n_points=5000, r_max=160.0, mask_deg=10.0,
+    "grid64_5000pts": MockSpec(N=64, L=500.0, n_points=5000, r_max=160.0, mask_deg=10.0,
                         sigma_mu=(0.2, 0.45), sigma_nl=250.0, seed=1),
-    "cfg3_128": MockSpec(N=128, L=500.0, n_points=30000, r_max=160.0, mask_deg=10.0,
+    "grid128_30000pts": MockSpec(N=128, L=500.0, n_points=30000, r_max=160.0, mask_deg=10.0,
                          sigma_mu=(0.2, 0.45), sigma_nl=250.0, seed=2),
 }
 

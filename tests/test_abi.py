@@ -68,7 +68,7 @@ def test_dz_prior_table_host_entry_matches_oracle():
     from oracle import hamlet_oracle as O
     from paper_2203_02369_gb300 import mock
     from paper_2203_02369_gb300.hamlet import dz_prior_table
-    cat = mock.make_catalog(mock.PRESETS["cfg2_64"])
+    cat = mock.make_catalog(mock.PRESETS["grid64_5000pts"])
     got = dz_prior_table(cat["cz"], 0.3, 5.0, 12.0)
     ref = O.dz_prior_table(cat["cz"], 0.3, 5.0, 12.0)
     assert got.shape == ref.shape

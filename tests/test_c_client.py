@@ -46,7 +46,7 @@ def test_c_client_matches_oracle_and_binding(tmp_path):
     from paper_2203_02369_gb300 import mock
     from paper_2203_02369_gb300.hamlet import Problem
     exe = build_client(tmp_path)
-    spec = mock.PRESETS["cfg1_16"]          # 16^3, 200 Mpc/h, 500 points, FP64
+    spec = mock.PRESETS["grid16_500pts_fp64"]          # 16^3, 200 Mpc/h, 500 points, FP64
     cat = mock.make_catalog(spec)
     w = mock.white_field(16, 5)
     d = cat["d_init"]

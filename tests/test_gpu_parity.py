@@ -123,7 +123,7 @@ def test_logpost_grad_vs_oracle(H, N, L, n, prec, seed, mask):
 
 def test_logpost_grad_128_paper_scale_sampled(H):
     """128^3, 3e4 points (the paper-scale configuration): full oracle check."""
-    spec = mock.PRESETS["cfg3_128"]
+    spec = mock.PRESETS["grid128_30000pts"]
     cat = mock.make_catalog(spec)
     gp = H.Problem.from_mock(spec, cat)
     op = O.problem_from_catalog(spec.N, spec.L, mock.spec_dict(spec)["cosmo"], spec.sigma_nl, cat)

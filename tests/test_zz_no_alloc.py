@@ -53,7 +53,7 @@ def test_noalloc_matches_logpost_grad_twice(H, N, L, n, prec, seed):
 
 
 def test_noalloc_rejects_problems_beyond_the_static_scratch(H):
-    spec = mock.PRESETS["cfg2_64"]
+    spec = mock.PRESETS["grid64_5000pts"]
     cat = mock.make_catalog(spec)
     p = H.Problem.from_mock(spec, cat)
     w = torch.zeros((64,) * 3, dtype=torch.float32, device="cuda")
