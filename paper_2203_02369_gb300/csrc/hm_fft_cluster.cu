@@ -324,6 +324,18 @@ k_plane_c2r_cl(const cplx<T>* __restrict__ in, long long in_stride, T* __restric
   // that no point touches needs no transform (same answer in every CTA of
   // the cluster, so the whole cluster leaves before any cluster barrier)
   if (MODE == C2R_GATHER && plane_empty_cl<N>(pts.off, s / 3, ix)) return;
+  if constexpr (MODE == C2R_EPI) {
+    // pull this CTA's rows of w and p_w toward L2 during the transforms
+    const long long base = (long long)s * epi.grid_stride + ((long long)ix * N + row0) * N;
+    const char* wb = reinterpret_cast<const char*>(reinterpret_cast<const T*>(epi.w) + base);
+    const char* pb = reinterpret_cast<const char*>(reinterpret_cast<const T*>(epi.pw) + base);
+    constexpr int LINES = (int)(sizeof(T) * RQ * N / 128);
+    const bool kick = epi.mode != GM_GRAD;
+    for (int l = threadIdx.x; l < LINES; l += NT) {
+      asm volatile("prefetch.global.L2 [%0];" ::"l"(wb + 128 * (long long)l));
+      if (kick) asm volatile("prefetch.global.L2 [%0];" ::"l"(pb + 128 * (long long)l));
+    }
+  }
   int c0, c1;
   own_columns_cl<N>(q, c0, c1);
   const int nc = c1 - c0;
