@@ -311,11 +311,17 @@ class BatchedServingLoop:
             try:
                 rows = be.run(k)
             except Exception as exc:
-                for job in active.values():
+                # the jobs loaded in this group fail with the error; their
+                # slots are released so that later arrivals can be served
+                for idx in sorted(active, reverse=True):
+                    job = active.pop(idx)
+                    try:
+                        be.release(idx)
+                    except Exception:
+                        pass
                     job.error = repr(exc)
                     job.finished = time.perf_counter() - t0
                     done.put(job)
-                active.clear()
                 continue
             dt = (time.perf_counter() - a) / k
             finished = []

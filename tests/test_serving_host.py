@@ -206,3 +206,27 @@ def test_batched_failing_prepare_is_reported():
     loop = BatchedServingLoop(reserve_bytes=0, backend_factory=FakeSlots, prepare=prep, free_bytes=lambda: 1 << 40)
     stats = loop.run([_job(k, n_traj=2) for k in range(3)])
     assert stats["jobs"] == 3 and len(stats["errors"]) == 1 and "injected" in stats["errors"][0]
+
+
+def test_batched_device_failure_fails_that_groups_jobs_only():
+    """A run that fails on the device (here: the fake raises, as a library
+    error would surface) ends the jobs then loaded in that group with an
+    error; later jobs of the group and other groups are still served."""
+    class Flaky(FakeSlots):
+        def run(self, k):
+            if self.key[0] == 128 and len(self.runs) >= 2 and not getattr(self, "failed", False):
+                self.failed = True
+                raise RuntimeError("injected device failure")
+            return super().run(k)
+
+    FakeSlots.instances = []
+    loop = BatchedServingLoop(max_slots=2, reserve_bytes=0, backend_factory=Flaky, prepare=lambda j: j,
+                              free_bytes=lambda: 1 << 40)
+    jobs = ([_job(k, N=128, arrival=0.0, n_traj=6) for k in range(2)] + [_job(2, N=128, arrival=0.05, n_traj=3)]
+            + [_job(k, N=64, arrival=0.0, n_traj=4) for k in (3, 4)])
+    stats = loop.run(jobs)
+    assert stats["jobs"] == 5
+    errs = {j.job_id for j in jobs if j.error}
+    assert errs == {0, 1}
+    assert all("injected device failure" in jobs[k].error for k in (0, 1))
+    assert len(jobs[2].traj_latency) == 3 and all(len(jobs[k].traj_latency) == 4 for k in (3, 4))
