@@ -55,6 +55,7 @@ def parse():
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--batched-only", action="store_true", help="run only the 32-chain batched measurement")
     ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--no-fft-ref", action="store_true", help="skip the cuFFT reference timing")
     ap.add_argument("--accept-target", type=float, default=0.70,
                     help="acceptance the batched and served chains' step sizes are tuned to (dual averaging)")
     ap.add_argument("--tune-eps", action="store_true", help="print acceptance for a sweep of eps and exit")
@@ -379,6 +380,49 @@ def run_batched(args, eps, L, use_graph):
     return out
 
 
+def run_fft_reference(prob, dev, reps=30):
+    """The library's 3D r2c/c2r transforms (plane pass + x pencil) against
+    cuFFT (torch.fft, unnormalised both ways) on the same 128^3 FP32 grids,
+    one and three at a time: each call timed alone with CUDA events, median
+    of reps.  A reference only; the hot path fuses its transforms with the
+    velocity weights, the CIC work and the leapfrog epilogue."""
+    import torch
+    N = prob.N
+    stream = torch.cuda.current_stream()
+
+    def med(fn):
+        ts = []
+        for _ in range(reps + 3):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            b.synchronize()
+            ts.append(a.elapsed_time(b) * 1e3)
+        return float(np.median(ts[3:]))
+
+    out = {}
+    dims = (-3, -2, -1)
+    for count in (1, 3):
+        g = torch.Generator(device=dev).manual_seed(5 + count)
+        x = torch.randn((count, N, N, N), device=dev, dtype=torch.float32, generator=g)
+        X = prob.fft_r2c(x)
+        Xc = torch.fft.rfftn(x, dim=dims)
+        y = prob.fft_c2r(X)
+        yc = torch.fft.irfftn(Xc, s=(N, N, N), dim=dims, norm="forward")
+        out[f"count_{count}"] = {
+            "ours_r2c_us": med(lambda: prob.fft_r2c(x)),
+            "cufft_r2c_us": med(lambda: torch.fft.rfftn(x, dim=dims)),
+            "ours_c2r_us": med(lambda: prob.fft_c2r(X)),
+            "cufft_c2r_us": med(lambda: torch.fft.irfftn(Xc, s=(N, N, N), dim=dims, norm="forward")),
+            "rel_diff_r2c": float(torch.linalg.vector_norm(X - Xc) / torch.linalg.vector_norm(Xc)),
+            "rel_diff_c2r": float(torch.linalg.vector_norm(y - yc) / torch.linalg.vector_norm(yc)),
+        }
+    out["note"] = ("3D FFT of 128^3 FP32 grids, each call timed alone (CUDA events, median); ours = z-y plane "
+                   "pass + x pencil kernels, cuFFT via torch.fft; data L2-resident in both")
+    return out
+
+
 def run_batched_same(prob, d_init, eps, L, use_graph, n_chains=16, K=20, M=60):
     """n_chains chains of the plain workload itself (same catalogue, same
     step, own Philox chain words) in one state: the batched form against the
@@ -649,6 +693,10 @@ def main():
                   "note": "reference traffic model (17R + 4C + 300 B/point per evaluation) x evaluations/s / "
                           "measured HBM peak; the fused kernels move fewer bytes than the model"}
 
+    fft_ref = None
+    if not args.no_fft_ref:
+        fft_ref = run_fft_reference(prob, dev)
+
     # CPU baseline: the oracle on a bounded sample, rank 0, N = 1 only
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -690,7 +738,7 @@ def main():
                 "gpu_launches": int(sum(v[1] * KERNELS_PER_PAIR.get(k, 1) for k, v in prof.items())),
                 "clocks": clk, "roofline": roofline, "model_roofline": model_roof, "kernels": kernels,
                 "ess": ess_info,
-                "e2e": e2e, "cpu_baseline": cpu, "batched": batched, "serving": serving,
+                "e2e": e2e, "cpu_baseline": cpu, "batched": batched, "serving": serving, "fft_reference": fft_ref,
                 "wall_s_timed": t_wall}
         print(json.dumps(line), flush=True)
     if ws > 1:
