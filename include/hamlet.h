@@ -116,6 +116,18 @@ int hm_problem_get_info(const hm_problem* p, hm_problem_info* out);
 int hm_set_catalog(hm_problem* p, int64_t n, const double* rhat_host, const double* mu_host,
                    const double* sigma_mu_host, const double* cz_host, const double* sigma_cz_host);
 
+/* The catalogue in the coordinates the paper states its data in (section
+ * "Mock Catalogue construction": supergalactic longitude SGL and latitude
+ * SGB in degrees per point, with mu, sigma_mu, cz and sigma_cz as in
+ * hm_set_catalog).  The direction of point i is
+ * rhat = (cos SGB cos SGL, cos SGB sin SGL, sin SGB) in the grid frame, whose
+ * axes are the supergalactic X, Y, Z; otherwise as hm_set_catalog.  Errors:
+ * as hm_set_catalog, and HM_EINVAL for SGB outside [-90, 90] or a
+ * non-finite angle. */
+int hm_set_catalog_sg(hm_problem* p, int64_t n, const double* sgl_deg_host, const double* sgb_deg_host,
+                      const double* mu_host, const double* sigma_mu_host, const double* cz_host,
+                      const double* sigma_cz_host);
+
 /* Psi(w, d) and its gradient (eqs. covfefe:bay, likelihood, lmu, vrobs,
  * vel-field, lvr, kappa, prior-k, D, Psi).  w_dev: N^3 field; d_dev: n
  * distances.  Outputs: psi_dev (1 double, device), grad_w_dev (N^3 field),

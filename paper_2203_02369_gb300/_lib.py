@@ -58,6 +58,8 @@ SIGNATURES = [
     ("hm_destroy_problem", None, [_P]),
     ("hm_problem_get_info", ct.c_int, [_P, ct.POINTER(hm_problem_info)]),
     ("hm_set_catalog", ct.c_int, [_P, ct.c_int64, c_double_p, c_double_p, c_double_p, c_double_p, c_double_p]),
+    ("hm_set_catalog_sg", ct.c_int, [_P, ct.c_int64, c_double_p, c_double_p, c_double_p, c_double_p, c_double_p,
+                                     c_double_p]),
     ("hm_logpost_grad", ct.c_int, [_P, _P, _P, _P, _P, _P, _P]),
     ("hm_logpost_grad_noalloc", ct.c_int, [_P, _P, _P, _P, _P, _P, _P]),
     ("hm_problem_last_status", ct.c_int, [_P, _P, ct.POINTER(ct.c_int32)]),

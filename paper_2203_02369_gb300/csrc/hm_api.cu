@@ -656,6 +656,29 @@ int hm_set_catalog(hm_problem* p, int64_t n, const double* rhat, const double* m
   return HM_OK;
 }
 
+int hm_set_catalog_sg(hm_problem* p, int64_t n, const double* sgl_deg, const double* sgb_deg, const double* mu,
+                      const double* smu, const double* cz, const double* scz) {
+  if (!p) return fail(HM_EINVAL, "null problem");
+  if (n < 0) return fail(HM_EINVAL, "n < 0");
+  if (n > (1ll << 30)) return fail(HM_EINVAL, "catalogue larger than 2^30 points");
+  if (n > 0 && (!sgl_deg || !sgb_deg)) return fail(HM_EINVAL, "null catalogue array");
+  HM_TRY(check_finite(sgl_deg, n, "SGL"));
+  HM_TRY(check_finite(sgb_deg, n, "SGB"));
+  // the direction on the sky in the grid frame, whose axes are the
+  // supergalactic X, Y, Z
+  const double rad = 3.14159265358979323846 / 180.0;
+  std::vector<double> rhat(3 * (size_t)n);
+  for (long long i = 0; i < n; ++i) {
+    if (!(sgb_deg[i] >= -90.0 && sgb_deg[i] <= 90.0)) return fail(HM_EINVAL, "SGB must be in [-90, 90] degrees");
+    const double l = sgl_deg[i] * rad, b = sgb_deg[i] * rad;
+    const double cb = std::cos(b);
+    rhat[3 * i] = cb * std::cos(l);
+    rhat[3 * i + 1] = cb * std::sin(l);
+    rhat[3 * i + 2] = std::sin(b);
+  }
+  return hm_set_catalog(p, n, rhat.data(), mu, smu, cz, scz);
+}
+
 // standalone workspace of a problem (one chain)
 static int ensure_ws(hm_problem* p) {
   if (p->ws_points == p->n && p->S1.p) return HM_OK;

@@ -110,6 +110,15 @@ class Problem:
                                       _dptr(arrs[2]), _dptr(scz) if scz is not None else None))
         self.n = n
 
+    def set_catalog_sg(self, sgl_deg, sgb_deg, mu, sigma_mu, cz, sigma_cz=None):
+        """The catalogue as supergalactic longitude/latitude in degrees."""
+        arrs = [np.ascontiguousarray(a, dtype=np.float64) for a in (sgl_deg, sgb_deg, mu, sigma_mu, cz)]
+        n = arrs[0].shape[0]
+        scz = None if sigma_cz is None else np.ascontiguousarray(sigma_cz, dtype=np.float64)
+        check(self.lib.hm_set_catalog_sg(self.h, n, *[_dptr(a) for a in arrs],
+                                         _dptr(scz) if scz is not None else None))
+        self.n = n
+
     @property
     def info(self):
         i = _lib.hm_problem_info()

@@ -147,6 +147,27 @@ def test_logpost_grad_128_fp64(H):
     assert rel(gd.cpu().numpy(), rgd) < 1e-12
 
 
+def test_catalog_in_supergalactic_coordinates(H):
+    """hm_set_catalog_sg (SGL, SGB in degrees, the paper's data coordinates)
+    gives the problem that the unit vectors give."""
+    spec, cat, gp, op, w = make_case(H, 16, 200.0, 500, "fp64", 13)
+    r = cat["rhat"]
+    sgb = np.degrees(np.arcsin(np.clip(r[:, 2], -1, 1)))
+    sgl = np.degrees(np.arctan2(r[:, 1], r[:, 0])) % 360.0
+    gq = H.Problem(16, 200.0, spec.cosmo, spec.sigma_nl, "fp64",
+                   ("table", cat["prior_d0"], cat["prior_bin"], cat["prior_logdens"]))
+    gq.set_catalog_sg(sgl, sgb, cat["mu"], cat["sigma_mu"], cat["cz"])
+    d = torch.tensor(cat["d_init"], device="cuda")
+    wt = torch.tensor(w, device="cuda")
+    a = gp.logpost_grad(wt, d)
+    b = gq.logpost_grad(wt, d)
+    assert abs(a[0].item() - b[0].item()) <= 1e-12 * abs(a[0].item())
+    assert rel(b[1].cpu().numpy(), a[1].cpu().numpy()) < 1e-12
+    assert rel(b[2].cpu().numpy(), a[2].cpu().numpy()) < 1e-12
+    with pytest.raises(Exception, match="SGB"):
+        gq.set_catalog_sg(sgl[:3], np.array([0.0, 91.0, 0.0]), cat["mu"][:3], cat["sigma_mu"][:3], cat["cz"][:3])
+
+
 def test_empty_catalog_is_prior_only(H):
     p = H.Problem(16, 100.0, precision="fp64", prior=("power", 2.0, 0.5, 40.0))
     p.set_catalog(np.zeros((0, 3)), np.zeros(0), np.zeros(0), np.zeros(0))
