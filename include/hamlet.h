@@ -239,8 +239,9 @@ int hm_run_chain(hm_state* s, int32_t n_traj, int32_t n_leapfrog, const double* 
  * Device memory is allocated once, at creation (HM_ENOMEM if it does not
  * fit): about 5 grids + 6 half spectra per slot and ~700 B per point of
  * room.  Not available on a slotted state: hm_adapt_step_size (use the
- * per-job adaptation below), sigma_NL sampling and chain analytics
- * (HM_ESTATE). */
+ * per-job adaptation below), the all-chain sigma_NL switch (each job chooses
+ * at load) and chain analytics (HM_ESTATE).  hm_state_get_sigma_nl reports
+ * each loaded chain's sigma_NL. */
 int hm_slots_create(hm_problem* templ, int32_t n_slots, int64_t max_points, uint64_t seed, hm_state** out);
 /* Number of loaded chains and of slots. */
 int hm_slots_count(hm_state* s, int32_t* n_active_out, int32_t* n_slots_out);
@@ -251,12 +252,14 @@ int hm_slots_count(hm_state* s, int32_t* n_active_out, int32_t* n_slots_out);
  * trajectory counter 0, Philox chain word chain_id, step eps0.  With
  * adapt_target in (0, 1) the step adapts by dual averaging after every
  * trajectory (as hm_adapt_step_size) until hm_slots_adapt_end; 0 keeps it
- * fixed.  Psi and the gradient of the new chain are evaluated on `stream`.
+ * fixed.  With sigma_nl0 > 0 the job samples sigma_NL as a chain coordinate
+ * (as hm_state_sample_sigma_nl) starting there; 0 keeps the problem's
+ * value.  Psi and the gradient of the new chain are evaluated on `stream`.
  * *index_out receives the chain index.  Errors: HM_EINVAL (mismatched job,
  * catalogue larger than a slot, bad eps0 or target, non-finite d),
- * HM_ESTATE (every slot in use). */
+ * negative sigma_nl0), HM_ESTATE (every slot in use). */
 int hm_slots_load(hm_state* s, hm_problem* job, int32_t chain_id, const double* d_init_host, double eps0,
-                  double adapt_target, int32_t* index_out, void* stream);
+                  double adapt_target, double sigma_nl0, int32_t* index_out, void* stream);
 /* End the step adaptation of chain `index`: its step becomes the averaged
  * iterate, copied to *eps_out_host (may be NULL).  Synchronises the stream. */
 int hm_slots_adapt_end(hm_state* s, int32_t index, double* eps_out_host, void* stream);

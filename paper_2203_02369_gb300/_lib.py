@@ -83,7 +83,7 @@ SIGNATURES = [
                                 ct.POINTER(hm_trace), _P]),
     ("hm_slots_create", ct.c_int, [_P, ct.c_int32, ct.c_int64, ct.c_uint64, ct.POINTER(_P)]),
     ("hm_slots_count", ct.c_int, [_P, ct.POINTER(ct.c_int32), ct.POINTER(ct.c_int32)]),
-    ("hm_slots_load", ct.c_int, [_P, _P, ct.c_int32, c_double_p, ct.c_double, ct.c_double,
+    ("hm_slots_load", ct.c_int, [_P, _P, ct.c_int32, c_double_p, ct.c_double, ct.c_double, ct.c_double,
                                  ct.POINTER(ct.c_int32), _P]),
     ("hm_slots_adapt_end", ct.c_int, [_P, ct.c_int32, c_double_p, _P]),
     ("hm_slots_release", ct.c_int, [_P, ct.c_int32, ct.POINTER(ct.c_int32), _P]),

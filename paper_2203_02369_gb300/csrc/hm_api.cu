@@ -1328,8 +1328,9 @@ int hm_state_get_sigma_nl(hm_state* s, double* sigma_out_host, double* grad_out_
   HM_CUDA(cudaMemcpyAsync(cs.data(), s->cs.p, sizeof(ChainScal) * s->C, cudaMemcpyDeviceToHost, st));
   HM_CUDA(cudaStreamSynchronize(st));
   for (int c = 0; c < s->C; ++c) {
-    sigma_out_host[c] = s->sample_sig ? cs[c].sig : s->chain_prob[c]->desc.sigma_nl;
-    if (grad_out_host) grad_out_host[c] = s->sample_sig ? cs[c].g_sig : 0.0;
+    const bool smp = s->sample_sig && cs[c].sample_sig;
+    sigma_out_host[c] = smp ? cs[c].sig : s->chain_prob[c]->desc.sigma_nl;
+    if (grad_out_host) grad_out_host[c] = smp ? cs[c].g_sig : 0.0;
   }
   return HM_OK;
 }
@@ -1424,6 +1425,9 @@ int hm_slots_create(hm_problem* templ, int32_t n_slots, int64_t max_points, uint
   HM_CUDA(cudaMemset(s->kinb_p.p, 0, 8 * C * s->nparts_p));
   s->region_of.assign(C, -1);
   s->free_regions.clear();
+  // sigma_NL sampling is chosen per job at load: the sigma_NL kernels run on
+  // every trajectory and skip the chains that hold it fixed
+  s->sample_sig = true;
   for (int r = n_slots - 1; r >= 0; --r) s->free_regions.push_back(r);
   *out = s.release();
   return HM_OK;
@@ -1437,7 +1441,7 @@ int hm_slots_count(hm_state* s, int32_t* n_active_out, int32_t* n_slots_out) {
 }
 
 int hm_slots_load(hm_state* s, hm_problem* job, int32_t chain_id, const double* d_init_host, double eps0,
-                  double adapt_target, int32_t* index_out, void* stream) {
+                  double adapt_target, double sigma_nl0, int32_t* index_out, void* stream) {
   HM_TRY(slotted_ok(s));
   if (!job || !index_out) return fail(HM_EINVAL, "null argument");
   if (!same_field_model(job, s->p0))
@@ -1447,6 +1451,7 @@ int hm_slots_load(hm_state* s, hm_problem* job, int32_t chain_id, const double* 
   if (!(eps0 > 0) || !std::isfinite(eps0)) return fail(HM_EINVAL, "eps0 must be finite and > 0");
   if (adapt_target != 0.0 && !(adapt_target > 0.0 && adapt_target < 1.0))
     return fail(HM_EINVAL, "adapt_target must be 0 (off) or in (0, 1)");
+  if (!std::isfinite(sigma_nl0) || sigma_nl0 < 0.0) return fail(HM_EINVAL, "sigma_nl0 must be 0 (fixed) or > 0");
   if (s->C >= s->C_cap || s->free_regions.empty()) return fail(HM_ESTATE, "every slot is in use");
   if (job->n > 0) HM_TRY(check_finite(d_init_host, job->n, "d_init"));
   cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -1471,6 +1476,8 @@ int hm_slots_load(hm_state* s, hm_problem* job, int32_t chain_id, const double* 
   ChainScal x{};
   x.sample_d = 1;
   x.eps = eps0;
+  x.sample_sig = sigma_nl0 > 0.0 ? 1 : 0;
+  x.sig = sigma_nl0;
   HM_CUDA(cudaMemcpyAsync(s->cs.as<ChainScal>() + c, &x, sizeof(x), cudaMemcpyHostToDevice, st));
   const int id = chain_id;
   HM_CUDA(cudaMemcpyAsync(s->chain_id.as<int>() + c, &id, sizeof(int), cudaMemcpyHostToDevice, st));

@@ -380,12 +380,14 @@ class Slots:
         check(self.lib.hm_slots_count(self.h, ct.byref(a), ct.byref(n)))
         return a.value
 
-    def load(self, problem, d_init, chain_id, eps0, adapt_target=0.0):
-        """Load a job; returns its chain index."""
+    def load(self, problem, d_init, chain_id, eps0, adapt_target=0.0, sigma_nl0=0.0):
+        """Load a job; returns its chain index.  sigma_nl0 > 0: the job samples
+        sigma_NL starting there."""
         d = np.ascontiguousarray(d_init, dtype=np.float64)
         idx = ct.c_int32()
         check(self.lib.hm_slots_load(self.h, problem.h, int(chain_id), _dptr(d) if d.size else None,
-                                     float(eps0), float(adapt_target), ct.byref(idx), _stream()))
+                                     float(eps0), float(adapt_target), float(sigma_nl0), ct.byref(idx),
+                                     _stream()))
         assert idx.value == len(self.problems)
         self.problems.append(problem)
         return idx.value
@@ -427,6 +429,13 @@ class Slots:
         gd = torch.empty(self.problems[index].n, dtype=torch.float64, device=self.device)
         check(self.lib.hm_state_get_grad(self.h, int(index), _ptr(gw), _ptr(gd), _stream()))
         return gw, gd
+
+    def sigma_nl(self):
+        """(sigma_NL, dPsi/dsigma_NL) of every loaded chain."""
+        na = len(self.problems)
+        s, g = np.zeros(max(na, 1)), np.zeros(max(na, 1))
+        check(self.lib.hm_state_get_sigma_nl(self.h, _dptr(s), _dptr(g), _stream()))
+        return s[:na], g[:na]
 
     def scalars(self, index):
         psi, kin, traj = ct.c_double(), ct.c_double(), ct.c_int64()

@@ -48,6 +48,7 @@ class Job:
     arrival: float = 0.0            # seconds after the start of the run
     adapt_warmup: int = 0           # dual-averaging warm-up trajectories before the timed ones
     accept_target: float = 0.70
+    sample_sigma_nl: bool = False   # sigma_NL as a chain coordinate, starting at the spec's value
     # filled in by the loop
     admitted: float = float("nan")
     finished: float = float("nan")
@@ -115,6 +116,8 @@ class ServingLoop:
             cat = mock.make_catalog(job.spec)
             prob = Problem.from_mock(job.spec, cat, device=self.device)
             st = State(prob, [cat["d_init"]], seed=job.seed, chain_ids=[job.job_id])
+            if job.sample_sigma_nl:
+                st.sample_sigma_nl(True, job.spec.sigma_nl)
             eps = job.eps
             if job.adapt_warmup > 0:
                 # the job's own step size, tuned to the target acceptance
@@ -204,7 +207,8 @@ class SlotsBackend:
     def load(self, job):
         with torch.cuda.stream(self.stream):
             return self.slots.load(job._prob, job._cat["d_init"], job.job_id, job.eps,
-                                   job.accept_target if job.adapt_warmup > 0 else 0.0)
+                                   job.accept_target if job.adapt_warmup > 0 else 0.0,
+                                   job.spec.sigma_nl if job.sample_sigma_nl else 0.0)
 
     def run(self, n_traj):
         with torch.cuda.stream(self.stream):

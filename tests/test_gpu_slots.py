@@ -131,6 +131,30 @@ def test_slot_step_adaptation_matches_the_one_chain_adaptation(H):
     sl.close()
 
 
+def test_slot_job_sampling_sigma_nl_matches_its_alone_chain(H):
+    """A job that samples sigma_NL (eq. q) beside one that holds it fixed
+    draws the chain its one-chain state draws with sigma_NL sampled."""
+    a = _job(H, 14, n=450)
+    b = _job(H, 15, n=300)
+    s0 = 230.0
+    tmpl = H.Problem(16, 200.0, precision="fp64")
+    sl = H.Slots(tmpl, n_slots=2, max_points=500, seed=SEED)
+    sl.load(b[2], b[1]["d_init"], chain_id=8, eps0=EPS)
+    i = sl.load(a[2], a[1]["d_init"], chain_id=7, eps0=EPS, sigma_nl0=s0)
+    got = sl.run(4, L_STEPS)[:, i]
+    sig, gsig = sl.sigma_nl()
+    assert sig[1 - i] == a[0].sigma_nl or sig[1 - i] == b[0].sigma_nl   # the fixed job reports its problem's value
+    st = H.State(a[2], [a[1]["d_init"]], seed=SEED, chain_ids=[7])
+    st.sample_sigma_nl(True, s0)
+    ref = st.run_chain(4, L_STEPS, EPS, use_graph=True)[:, 0]
+    rs, rg = st.sigma_nl()
+    _same(got, ref)
+    assert abs(sig[i] - rs[0]) <= 1e-12 * rs[0]
+    assert sig[i] != s0                         # it moved
+    st.close()
+    sl.close()
+
+
 def test_slots_reject_mismatched_and_oversize_jobs(H):
     tmpl = H.Problem(16, 200.0, precision="fp64")
     sl = H.Slots(tmpl, n_slots=2, max_points=100, seed=1)
