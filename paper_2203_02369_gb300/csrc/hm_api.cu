@@ -868,6 +868,13 @@ int hm_philox(uint64_t seed, int64_t n, uint32_t c1, uint32_t c2, uint32_t c3, u
 // ---------------------------------------------------------------------------
 // chain states
 // ---------------------------------------------------------------------------
+// CTAs per chain of the trajectory-start field kernel (momentum draw, save,
+// half kick and drift): enough that a single chain fills the GPU, at most
+// one node pair per thread and 1024 blocks.
+static int field_parts(long long n3) {
+  return (int)std::min<long long>(1024, std::max<long long>(1, (n3 / 2 + 255) / 256));
+}
+
 static GradArgs state_args(hm_state* s) {
   GradArgs a{};
   a.prec = s->prec;
@@ -947,7 +954,7 @@ int hm_state_create_batch(hm_problem* const* problems, int32_t n_problems, int32
   s->ntot = tot;
   s->max_pts = maxp;
   s->pts_blocks = points_blocks(maxp);
-  s->nparts_f = (int)std::min<long long>(256, std::max<long long>(1, (s->n3 / 2 + 255) / 256));
+  s->nparts_f = field_parts(s->n3);
   s->nparts_p = std::max(1, std::min(64, (maxp / 2 + 255) / 256));
   const size_t C = n_chains, rs = s->rsz;
   HM_TRY(s->w.alloc(rs * C * s->n3));
@@ -1395,7 +1402,7 @@ int hm_slots_create(hm_problem* templ, int32_t n_slots, int64_t max_points, uint
   s->ntot = tot;
   s->max_pts = (int)max_points;
   s->pts_blocks = points_blocks(s->max_pts);
-  s->nparts_f = (int)std::min<long long>(256, std::max<long long>(1, (s->n3 / 2 + 255) / 256));
+  s->nparts_f = field_parts(s->n3);
   s->nparts_p = std::max(1, std::min(64, (s->max_pts / 2 + 255) / 256));
   const size_t C = n_slots, rs = s->rsz;
   DevBuf* grids[] = {&s->w, &s->pw, &s->gw, &s->w0, &s->gw0};
