@@ -4,7 +4,7 @@ import math
 
 import numpy as np
 import pytest
-from scipy import integrate, stats
+from scipy import integrate, optimize, special, stats
 
 from oracle import hamlet_oracle as O
 from paper_2203_02369_gb300 import mock
@@ -82,9 +82,31 @@ def test_parseval_and_hermitian():
 
 
 # --------------------------------------------------------- cosmology ----
+def tophat_j1(x):
+    """Top-hat window written independently of the oracle: 3 j1(x)/x with
+    scipy's spherical Bessel function (1 at x = 0)."""
+    x = np.asarray(x, dtype=np.float64)
+    out = np.ones_like(x)
+    m = x > 0
+    out[m] = 3.0 * special.spherical_jn(1, x[m]) / x[m]
+    return out
+
+
+def test_tophat_window_limits_zero_and_bessel_form():
+    # W(x) = 3 j1(x)/x: W -> 1 - x^2/10 as x -> 0, first zero where tan x = x
+    for x in (1e-3, 1e-2, 0.1):
+        assert abs(O.tophat_window(x) - (1.0 - x * x / 10.0 + x ** 4 / 280.0)) < 1e-9
+    x0 = optimize.brentq(lambda x: math.tan(x) - x, 4.0, 4.6)
+    assert abs(x0 - 4.493409457909064) < 1e-12
+    assert abs(O.tophat_window(x0)) < 1e-12
+    x = np.linspace(0.05, 40.0, 2001)
+    assert np.max(np.abs(O.tophat_window(x) - tophat_j1(x))) < 1e-12
+
+
 def test_power_spectrum_normalisation_independent_quadrature():
+    # sigma(8 Mpc/h) from adaptive quadrature with the Bessel-form window
     pk = O.PowerSpectrum(**COSMO)
-    f = lambda lnk: (lambda k: k ** 3 * pk(k) * O.tophat_window(k * 8.0) ** 2)(math.exp(lnk))
+    f = lambda lnk: (lambda k: k ** 3 * pk(k) * tophat_j1(k * 8.0) ** 2)(math.exp(lnk))
     val, _ = integrate.quad(f, math.log(1e-5), math.log(1e2), limit=4000)
     assert abs(math.sqrt(val / (2 * math.pi ** 2)) - 0.8) < 1e-8
 
@@ -112,6 +134,52 @@ def test_transfer_function_limits():
     k = np.logspace(-3, 0, 2000)
     kp = k[np.argmax(pk(k))]
     assert 0.01 < kp < 0.03
+
+
+def _q_nobaryon(k, omega_m, h, T_cmb):
+    # without baryons alpha_Gamma = 1 and Gamma_eff = omega_m h on every scale
+    return k * (T_cmb / 2.7) ** 2 / (omega_m * h)
+
+
+def test_transfer_without_baryons_depends_on_k_through_q_only():
+    # EH98: with omega_b = 0 the shape parameter is omega_m h, so T is one
+    # function of q = k theta^2 / (omega_m h) for any (omega_m, h, T_cmb)
+    k = np.logspace(-4, 2, 61)
+    Ta = O.eh_nowiggle_transfer(k, 0.3, 0.0, 0.7, 2.7255)
+    for om, h, tc in ((0.2, 0.7, 2.7255), (0.3, 0.5, 2.7255), (0.45, 0.8, 2.9)):
+        kb = k * (om * h) / (0.3 * 0.7) * (2.7255 / tc) ** 2
+        Tb = O.eh_nowiggle_transfer(kb, om, 0.0, h, tc)
+        assert np.max(np.abs(Tb / Ta - 1)) < 1e-12
+    # baryons suppress small-scale power (alpha_Gamma < 1)
+    assert O.eh_nowiggle_transfer(np.array([1.0]), 0.3, 0.05, 0.7, 2.7255)[0] < \
+        O.eh_nowiggle_transfer(np.array([1.0]), 0.3, 0.0, 0.7, 2.7255)[0]
+
+
+def test_transfer_small_and_large_q_asymptotes():
+    om, h, tc = 0.3, 0.7, 2.7255
+    # q -> infinity: T -> ln(1.8 q) / (14.2 q^2) (logarithmic CDM tail)
+    for k in (1e5, 1e6):
+        q = _q_nobaryon(k, om, h, tc)
+        T = O.eh_nowiggle_transfer(np.array([k]), om, 0.0, h, tc)[0]
+        assert abs(T * q * q * 14.2 / math.log(1.8 * q) - 1) < 2e-6
+    # q -> 0: 1 - T = C0(0) q^2 / L0(0) with C0(0) = 14.2 + 731, L0(0) = ln(2e) = 1 + ln 2,
+    # and d/dq ln[(1 - T)/q^2] -> -731*62.5/745.2 - (1.8/(2e))/(1 + ln 2)
+    lead = 745.2 / (1.0 + math.log(2.0))
+    slope = -731.0 * 62.5 / 745.2 - (1.8 / (2.0 * math.e)) / (1.0 + math.log(2.0))
+    q1, q2 = 1e-6, 2e-6
+    r = []
+    for q in (q1, q2):
+        k = q * om * h / (tc / 2.7) ** 2
+        T = O.eh_nowiggle_transfer(np.array([k]), om, 0.0, h, tc)[0]
+        r.append((1.0 - T) / (q * q))
+    assert abs(r[0] / lead - 1) < 2e-4
+    qa, qb = 1e-4, 2e-4
+    ra = []
+    for q in (qa, qb):
+        k = q * om * h / (tc / 2.7) ** 2
+        T = O.eh_nowiggle_transfer(np.array([k]), om, 0.0, h, tc)[0]
+        ra.append(math.log((1.0 - T) / (q * q)))
+    assert abs((ra[1] - ra[0]) / (qb - qa) / slope - 1) < 2e-2
 
 
 # ---------------------------------------------------- point functions ----
@@ -239,19 +307,50 @@ def test_linear_continuity_per_mode():
     assert err < 1e-9 * np.max(np.abs(p.aHf * dk))
 
 
+def _mode_k(N, L):
+    # |k| of every DFT mode, from integer mode numbers in (-N/2, N/2]
+    n = np.array([i if i <= N // 2 else i - N for i in range(N)], dtype=np.float64)
+    return 2.0 * np.pi / L * np.sqrt(n[:, None, None] ** 2 + n[None, :, None] ** 2 + n[None, None, :] ** 2)
+
+
+def _impulse_response(p, window=None):
+    # the colouring map is a convolution, so E_w[mean_x delta(x)^2] over white
+    # fields w is the squared norm of its response to a unit impulse
+    e0 = np.zeros((p.N,) * 3)
+    e0[0, 0, 0] = 1.0
+    dk = O.delta_k(p, e0)
+    if window is not None:
+        dk = dk * window
+    return np.fft.ifftn(dk).real
+
+
 def test_colouring_variance():
-    # <delta(x)^2> = sum_k P(k) / V over draws of the whitened field
+    # <delta(x)^2> = (1/V) sum_{k != 0} P(|k|), P taken from the power spectrum
+    # itself at the mode wavenumbers (eq. prior-k with its variance per mode)
+    for N, L in ((8, 200.0), (16, 500.0)):
+        p, _ = tiny_problem(N=N, L=L)
+        k = _mode_k(N, L)
+        expect = np.sum(p.pk(k[k > 0])) / L ** 3
+        got = np.sum(_impulse_response(p) ** 2)
+        assert abs(got / expect - 1) < 1e-12
+    # and the sample variance over white fields agrees within its MC error
     p, _ = tiny_problem(N=8, L=200.0)
-    amp = p.colour_amplitude()
-    expect = np.sum(amp ** 2 * p.delta ** 3) / p.L ** 3
-    acc = 0.0
-    nd = 300
-    for s in range(nd):
-        w = mock.white_field(8, 1000 + s)
-        dl = np.fft.ifftn(O.delta_k(p, w)).real
-        acc += np.mean(dl ** 2)
-    got = acc / nd
-    assert abs(got / expect - 1) < 0.05
+    k = _mode_k(8, 200.0)
+    expect = np.sum(p.pk(k[k > 0])) / 200.0 ** 3
+    acc = np.mean([np.mean(np.fft.ifftn(O.delta_k(p, mock.white_field(8, 1000 + s))).real ** 2)
+                   for s in range(300)])
+    assert abs(acc / expect - 1) < 0.05
+
+
+def test_colouring_reproduces_sigma8_on_a_resolved_grid():
+    # a field coloured on a grid that resolves the 8 Mpc/h top-hat and holds
+    # its large scales has, smoothed with that top-hat, the variance sigma8^2
+    # of the continuum definition (0.9 % short at 64^3 in 400 Mpc/h: the
+    # modes below the fundamental are missing)
+    N, L = 64, 400.0
+    p, _ = tiny_problem(N=N, L=L)
+    var = np.sum(_impulse_response(p, tophat_j1(8.0 * _mode_k(N, L))) ** 2)
+    assert abs(var / 0.8 ** 2 - 1) < 0.015
 
 
 def test_velocity_field_is_real():
