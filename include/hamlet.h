@@ -44,7 +44,7 @@ enum {
 };
 
 enum { HM_FP32 = 0, HM_FP64 = 1 };
-enum { HM_PRIOR_TABLE = 0, HM_PRIOR_POWER = 1 };
+enum { HM_PRIOR_TABLE = 0, HM_PRIOR_POWER = 1, HM_PRIOR_DZ = 2 };
 
 typedef struct hm_problem hm_problem;
 typedef struct hm_state hm_state;
@@ -58,11 +58,18 @@ typedef struct hm_problem_desc {
   double L;              /* box side, Mpc/h */
   double observer[3];    /* observer position; used when observer_set != 0 */
   int32_t observer_set;  /* 0: observer at the box centre (L/2, L/2, L/2) */
-  int32_t prior_kind;    /* HM_PRIOR_TABLE or HM_PRIOR_POWER (eq. D) */
+  int32_t prior_kind;    /* HM_PRIOR_DZ, HM_PRIOR_TABLE or HM_PRIOR_POWER (eq. D) */
   double omega_m, omega_b, h, n_s, sigma8, T_cmb; /* P(k): Eisenstein-Hu no-wiggle */
   double f_growth;       /* linear growth rate; <= 0 means omega_m^0.55 */
   double sigma_nl;       /* non-linear velocity dispersion sigma_NL, km/s (eq. kappa) */
-  /* HM_PRIOR_TABLE: eq. D's histogram as ln pi_D at the bin centres
+  /* HM_PRIOR_DZ (section "Priors", eq. D from eq. e:dz), also taken for
+   * HM_PRIOR_TABLE with prior_nbins = 0 and no table, so it is the default
+   * of a zeroed description: every hm_set_catalog builds the histogram of
+   * the redshift distances d_z of the catalogue's observed cz (as
+   * hm_dz_prior_table) with bins of prior_bin (<= 0: 5 Mpc/h) on
+   * [0, max d_z + prior_pad) (prior_pad <= 0: 3 sigma_v/H0), and the prior
+   * is that table (d0 = 0), read as below.
+   * HM_PRIOR_TABLE: eq. D's histogram as ln pi_D at the bin centres
    * d0 + (b + 1/2) bin, interpolated linearly between centres (flat in the
    * outer half bins); support [d0, d0 + nbins * bin), -inf outside */
   double prior_d0, prior_bin;
@@ -73,6 +80,7 @@ typedef struct hm_problem_desc {
   double prior_alpha, prior_dmin, prior_dmax;
   int32_t device;        /* CUDA device ordinal */
   int32_t pad1;
+  double prior_pad;      /* HM_PRIOR_DZ: support beyond the largest d_z, Mpc/h */
 } hm_problem_desc;
 
 /* Derived constants of a problem (host copy). */
@@ -111,8 +119,11 @@ int hm_problem_get_info(const hm_problem* p, hm_problem_info* out);
  * distance modulus mu with error sigma_mu, redshift cz with error sigma_cz).
  * rhat_host: n x 3 unit vectors (row-major), the direction r_i of eq. lvr;
  * cz_host in km/s (z = cz/c); sigma_cz_host may be NULL (zeros).  Replaces a
- * previous catalogue.  Errors: HM_EINVAL (n < 0, non-finite value,
- * sigma_mu <= 0, |rhat| != 1 beyond 1e-6), HM_ENOMEM. */
+ * previous catalogue; with the HM_PRIOR_DZ prior it also rebuilds the
+ * distance prior from these redshifts (states and slots made from an
+ * earlier catalogue keep that catalogue and its table).  Errors: HM_EINVAL
+ * (n < 0, non-finite value, sigma_mu <= 0, |rhat| != 1 beyond 1e-6),
+ * HM_ENOMEM. */
 int hm_set_catalog(hm_problem* p, int64_t n, const double* rhat_host, const double* mu_host,
                    const double* sigma_mu_host, const double* cz_host, const double* sigma_cz_host);
 
@@ -140,20 +151,23 @@ int hm_logpost_grad(hm_problem* p, const void* w_dev, const double* d_dev, doubl
                     void* grad_w_dev, double* grad_d_dev, void* stream);
 
 /* hm_logpost_grad for callers that cannot let the library allocate device
- * memory (code running inside another framework's memory pool, work
- * recorded into a stream capture, hosts that budget device memory up
- * front).  The paper has no counterpart; this is a deployment variant.
- * Same arguments, outputs and error behaviour as hm_logpost_grad, and the
- * same kernels, all launched on `stream`; it never calls cudaMalloc,
- * cudaFree or any other allocating routine.  Scratch comes from one static
- * 4 MiB device array that every GPU loading this library keeps until the
- * process exits; a problem needing more (any N > 32; on a 32^3 grid more
- * than about 19,000 points at FP32 or 8,800 at FP64) is rejected with
- * HM_EINVAL and a message naming the sizes.  The first call on a device looks up the
- * array's device address with that device current; make that first call
- * before any stream capture.  Every call shares the one array (each call
- * clears what must start at zero), so calls whose work overlaps on the GPU
- * race: serialise them on one stream or with events. */
+ * memory: code running inside another framework's memory pool, which has to
+ * account for every device byte itself, and hosts that budget device memory
+ * up front and allow no allocation (nor the device synchronisation that
+ * cudaMalloc/cudaFree may cause) once they run.  The paper has no
+ * counterpart; this is a deployment variant.  Same arguments, outputs and
+ * error behaviour as hm_logpost_grad, and the same kernels, all launched on
+ * `stream`; it never calls cudaMalloc, cudaFree or any other allocating
+ * routine.  Scratch comes from one static 4 MiB device array that every GPU
+ * loading this library keeps until the process exits; a problem needing
+ * more (any N > 32; on a 32^3 grid more than about 19,000 points at FP32 or
+ * 8,800 at FP64) is rejected with HM_EINVAL and a message naming the sizes.
+ * The first call on a device looks up the array's device address with that
+ * device current (once per device, also when host threads make their first
+ * calls at the same time); make that first call before any stream capture.
+ * Every call shares the one array and clears what must start at zero, so
+ * calls whose work overlaps on the GPU race: serialise them on one stream or
+ * with events. */
 int hm_logpost_grad_noalloc(hm_problem* p, const void* w_dev, const double* d_dev, double* psi_dev,
                             void* grad_w_dev, double* grad_d_dev, void* stream);
 
@@ -362,6 +376,15 @@ const char* hm_kernel_kind_name(int32_t kind);
  * is returned (HM_EINVAL in the latter case). */
 int hm_dz_prior_table(double omega_m, int64_t n, const double* cz_host, double bin_width, double pad,
                       int32_t max_bins, double* logdens_out, int32_t* nbins_out);
+
+/* The problem's distance-prior table (eq. D) as the device reads it: ln pi_D
+ * at the bin centres d0 + (b + 1/2) bin for b < *nbins_out (host copies;
+ * d0_out, bin_out and logdens_out may be NULL; with logdens_out NULL only
+ * the sizes are returned).  For HM_PRIOR_DZ this is the histogram built by
+ * the last hm_set_catalog (0 bins before any catalogue).  Errors: HM_ESTATE
+ * for a power-law prior, HM_EINVAL when max_bins is too small. */
+int hm_problem_prior_table(const hm_problem* p, int32_t max_bins, double* logdens_out, int32_t* nbins_out,
+                           double* d0_out, double* bin_out);
 
 /* Raw Philox-4x32-10 blocks for counters (q, c1, c2, c3), q = 0..n-1, key
  * seed: out_dev receives 4 n uint32 words. */

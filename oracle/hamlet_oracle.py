@@ -256,7 +256,10 @@ def kappa2_prime(d, sigma_cz, omega_m):
 class Problem:
     """Everything the posterior depends on besides (w, d).
 
-    prior: ("table", d0, bin_width, logdens array) or ("power", alpha, dmin, dmax).
+    prior: ("dz", bin_width, pad) -- eq. D built from the catalogue's observed
+    redshifts by eq. e:dz (dz_prior_table; bin_width <= 0 means 5 Mpc/h,
+    pad <= 0 means 3 sigma_v/H0), stored as the equivalent table;
+    ("table", d0, bin_width, logdens array) or ("power", alpha, dmin, dmax).
     """
 
     def __init__(self, N, L, cosmo, sigma_nl, rhat, mu, sigma_mu, cz, sigma_cz,
@@ -281,6 +284,11 @@ class Problem:
         self.cz = np.asarray(cz, float)
         self.z = self.cz / C_KMS
         self.sigma_cz = np.asarray(sigma_cz, float)
+        if prior[0] == "dz":
+            bw = prior[1] if prior[1] > 0 else 5.0
+            pad = prior[2] if prior[2] > 0 else 3.0 * self.sigma_v / H0
+            prior = ("table", 0.0, bw, dz_prior_table(self.cz, self.omega_m, bw, pad)) if self.cz.size else \
+                ("table", 0.0, bw, np.zeros(1))
         self.prior = prior
         self.n = self.mu.shape[0]
         self._D = None
@@ -813,9 +821,10 @@ def wiener_filter(prob, d):
 
 
 def problem_from_catalog(spec_N, spec_L, cosmo, sigma_nl, cat, prior=None):
-    """Convenience: build a Problem from a mock catalogue dict."""
+    """Convenience: build a Problem from a mock catalogue dict; the distance
+    prior defaults to eq. D from the catalogue's redshifts (section "Priors")."""
     if prior is None:
-        prior = ("table", cat["prior_d0"], cat["prior_bin"], cat["prior_logdens"])
+        prior = ("dz", 0.0, 0.0)
     return Problem(spec_N, spec_L, cosmo, sigma_nl, cat["rhat"], cat["mu"], cat["sigma_mu"],
                    cat["cz"], cat["sigma_cz"], prior)
 

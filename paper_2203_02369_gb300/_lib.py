@@ -26,6 +26,7 @@ class hm_problem_desc(ct.Structure):
         ("prior_logdens_host", c_double_p),
         ("prior_alpha", ct.c_double), ("prior_dmin", ct.c_double), ("prior_dmax", ct.c_double),
         ("device", ct.c_int32), ("pad1", ct.c_int32),
+        ("prior_pad", ct.c_double),
     ]
 
 
@@ -48,7 +49,7 @@ class hm_trace(ct.Structure):
 
 HM_OK, HM_EINVAL, HM_ENOMEM, HM_ECUDA, HM_EDOMAIN, HM_ESTATE = 0, -1, -2, -3, -4, -5
 HM_FP32, HM_FP64 = 0, 1
-HM_PRIOR_TABLE, HM_PRIOR_POWER = 0, 1
+HM_PRIOR_TABLE, HM_PRIOR_POWER, HM_PRIOR_DZ = 0, 1, 2
 
 # (name, restype, argtypes) of every exported entry point
 _P = ct.c_void_p
@@ -63,6 +64,8 @@ SIGNATURES = [
     ("hm_logpost_grad", ct.c_int, [_P, _P, _P, _P, _P, _P, _P]),
     ("hm_logpost_grad_noalloc", ct.c_int, [_P, _P, _P, _P, _P, _P, _P]),
     ("hm_problem_last_status", ct.c_int, [_P, _P, ct.POINTER(ct.c_int32)]),
+    ("hm_problem_prior_table", ct.c_int, [_P, ct.c_int32, c_double_p, ct.POINTER(ct.c_int32), c_double_p,
+                                          c_double_p]),
     ("hm_velocity_field", ct.c_int, [_P, _P, _P, _P]),
     ("hm_fft_r2c", ct.c_int, [_P, _P, _P, ct.c_int32, _P]),
     ("hm_fft_c2r", ct.c_int, [_P, _P, _P, ct.c_int32, _P]),

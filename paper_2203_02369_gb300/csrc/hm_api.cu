@@ -9,6 +9,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <memory>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -271,6 +272,12 @@ struct hm_problem {
   long long n3 = 0, nspec = 0;
   DevBuf tw, amp, ampd, prior_logdens;   // ampd: colouring sqrt(P/Delta^3)/N^3 per n^2
   std::vector<double> prior_host;
+  // eq. D from the observed redshifts: rebuilt by every hm_set_catalog; the
+  // tables of earlier catalogues stay allocated (states and slots made from
+  // them keep reading theirs) until the problem is destroyed
+  bool prior_dz = false;
+  double dz_bin = 0, dz_pad = 0;
+  std::vector<std::unique_ptr<DevBuf>> prior_retired;
   // catalogue
   long long n = 0;
   DevBuf rx, ry, rz, mu, smu, zobs, scz;
@@ -502,6 +509,36 @@ static int check_finite(const double* x, long long n, const char* what) {
   return HM_OK;
 }
 
+// eq. D's histogram from eq. e:dz: d_z of each cz/c (flat LCDM, composite
+// Simpson with 64 intervals on [0, z]), bins of bin_width on [0, max d_z +
+// pad), count + 0.5 per bin, normalised to a density; ln density per bin.
+static std::vector<double> dz_histogram(double omega_m, long long n, const double* cz, double bin_width,
+                                        double pad) {
+  auto dz = [&](double z) {
+    const int m = 64;
+    double s = 0.0;
+    for (int i = 0; i <= m; ++i) {
+      const double x = z * i / m;
+      const double f = 1.0 / std::sqrt(omega_m * (1.0 + x) * (1.0 + x) * (1.0 + x) + 1.0 - omega_m);
+      s += ((i == 0 || i == m) ? 1.0 : ((i & 1) ? 4.0 : 2.0)) * f;
+    }
+    return kC / kH0 * (z / m) / 3.0 * s;
+  };
+  std::vector<double> d(n);
+  double dmax = 0.0;
+  for (long long i = 0; i < n; ++i) {
+    d[i] = dz(std::max(cz[i], 0.0) / kC);
+    dmax = std::max(dmax, d[i]);
+  }
+  const long long nb = (long long)std::ceil((dmax + pad) / bin_width);
+  std::vector<double> cnt(nb, 0.0), out(nb);
+  for (long long i = 0; i < n; ++i) cnt[std::min<long long>((long long)(d[i] / bin_width), nb - 1)] += 1.0;
+  double tot = 0.0;
+  for (long long b = 0; b < nb; ++b) tot += cnt[b] + 0.5;
+  for (long long b = 0; b < nb; ++b) out[b] = std::log((cnt[b] + 0.5) / (tot * bin_width));
+  return out;
+}
+
 int hm_init_problem(const hm_problem_desc* desc, hm_problem** out) {
   if (!desc || !out) return fail(HM_EINVAL, "null argument");
   *out = nullptr;
@@ -512,7 +549,13 @@ int hm_init_problem(const hm_problem_desc* desc, hm_problem** out) {
   if (!(d.L > 0) || !(d.omega_m > 0) || !(d.omega_b > 0) || !(d.h > 0) || !(d.sigma8 > 0) ||
       !(d.T_cmb > 0) || !std::isfinite(d.n_s) || !(d.sigma_nl >= 0))
     return fail(HM_EINVAL, "bad cosmology or box parameters");
-  if (d.prior_kind == HM_PRIOR_TABLE) {
+  // a table kind without a table is the default: eq. D from the redshifts
+  const bool dz_prior = d.prior_kind == HM_PRIOR_DZ ||
+                        (d.prior_kind == HM_PRIOR_TABLE && d.prior_nbins == 0 && !d.prior_logdens_host);
+  if (dz_prior) {
+    if (d.prior_bin < 0 || !std::isfinite(d.prior_bin) || d.prior_pad < 0 || !std::isfinite(d.prior_pad))
+      return fail(HM_EINVAL, "redshift-distance prior needs prior_bin >= 0 and prior_pad >= 0");
+  } else if (d.prior_kind == HM_PRIOR_TABLE) {
     if (d.prior_nbins <= 0 || !d.prior_logdens_host || !(d.prior_bin > 0))
       return fail(HM_EINVAL, "table prior needs prior_nbins > 0, prior_bin > 0 and prior_logdens_host");
   } else if (d.prior_kind == HM_PRIOR_POWER) {
@@ -580,7 +623,16 @@ int hm_init_problem(const hm_problem_desc* desc, hm_problem** out) {
     HM_TRY(p->tw.alloc(twd.size() * 8));
     HM_CUDA(cudaMemcpy(p->tw.p, twd.data(), twd.size() * 8, cudaMemcpyHostToDevice));
   }
-  if (d.prior_kind == HM_PRIOR_TABLE) {
+  if (dz_prior) {
+    // built by hm_set_catalog; the device sees a table (d0 = 0) once a catalogue is set
+    p->prior_dz = true;
+    p->dz_bin = d.prior_bin > 0 ? d.prior_bin : 5.0;
+    p->dz_pad = d.prior_pad > 0 ? d.prior_pad : 3.0 * p->sigma_v / kH0;
+    p->desc.prior_kind = HM_PRIOR_TABLE;
+    p->desc.prior_d0 = 0.0;
+    p->desc.prior_bin = p->dz_bin;
+    p->desc.prior_nbins = 0;
+  } else if (d.prior_kind == HM_PRIOR_TABLE) {
     p->prior_host.assign(d.prior_logdens_host, d.prior_logdens_host + d.prior_nbins);
     HM_TRY(p->prior_logdens.alloc(p->prior_host.size() * 8));
     HM_CUDA(cudaMemcpy(p->prior_logdens.p, p->prior_host.data(), p->prior_host.size() * 8, cudaMemcpyHostToDevice));
@@ -652,7 +704,38 @@ int hm_set_catalog(hm_problem* p, int64_t n, const double* rhat, const double* m
   HM_TRY(upload(p->smu, ismu2.data(), n));   // the device keeps 1/sigma_mu^2
   HM_TRY(upload(p->zobs, z.data(), n));
   HM_TRY(upload(p->scz, sc.data(), n));
+  if (p->prior_dz) {
+    if (p->prior_logdens.p) {   // states made from the previous catalogue keep reading its table
+      p->prior_retired.push_back(std::make_unique<DevBuf>());
+      std::swap(p->prior_retired.back()->p, p->prior_logdens.p);
+      std::swap(p->prior_retired.back()->bytes, p->prior_logdens.bytes);
+    }
+    p->prior_host.clear();
+    p->desc.prior_nbins = 0;
+    if (n > 0) {
+      p->prior_host = dz_histogram(p->desc.omega_m, n, cz, p->dz_bin, p->dz_pad);
+      if (p->prior_host.size() > (size_t)(1 << 24)) return fail(HM_EINVAL, "redshift-distance histogram too long");
+      HM_TRY(p->prior_logdens.alloc(p->prior_host.size() * 8));
+      HM_CUDA(cudaMemcpy(p->prior_logdens.p, p->prior_host.data(), p->prior_host.size() * 8,
+                         cudaMemcpyHostToDevice));
+      p->desc.prior_nbins = (int32_t)p->prior_host.size();
+    }
+  }
   p->n = n;
+  p->ws_points = -1;   // the standalone workspace takes the new catalogue's parameters
+  return HM_OK;
+}
+
+int hm_problem_prior_table(const hm_problem* p, int32_t max_bins, double* logdens_out, int32_t* nbins_out,
+                           double* d0_out, double* bin_out) {
+  if (!p || !nbins_out) return fail(HM_EINVAL, "null argument");
+  if (p->desc.prior_kind != HM_PRIOR_TABLE) return fail(HM_ESTATE, "the problem's distance prior is not a table");
+  *nbins_out = (int32_t)p->prior_host.size();
+  if (d0_out) *d0_out = p->desc.prior_d0;
+  if (bin_out) *bin_out = p->desc.prior_bin;
+  if (!logdens_out) return HM_OK;
+  if ((size_t)max_bins < p->prior_host.size()) return fail(HM_EINVAL, "max_bins too small (see nbins_out)");
+  std::copy(p->prior_host.begin(), p->prior_host.end(), logdens_out);
   return HM_OK;
 }
 
@@ -831,31 +914,11 @@ int hm_dz_prior_table(double omega_m, int64_t n, const double* cz_host, double b
   if (n <= 0 || !cz_host || !nbins_out) return fail(HM_EINVAL, "need n > 0 redshifts and nbins_out");
   if (!(bin_width > 0) || !(pad >= 0) || !(omega_m > 0)) return fail(HM_EINVAL, "bad bin width, pad or omega_m");
   HM_TRY(check_finite(cz_host, n, "cz"));
-  // eq. e:dz by composite Simpson, 64 intervals on [0, z]
-  auto dz = [&](double z) {
-    const int m = 64;
-    double s = 0.0;
-    for (int i = 0; i <= m; ++i) {
-      const double x = z * i / m;
-      const double f = 1.0 / std::sqrt(omega_m * (1.0 + x) * (1.0 + x) * (1.0 + x) + 1.0 - omega_m);
-      s += ((i == 0 || i == m) ? 1.0 : ((i & 1) ? 4.0 : 2.0)) * f;
-    }
-    return kC / kH0 * (z / m) / 3.0 * s;
-  };
-  std::vector<double> d(n);
-  double dmax = 0.0;
-  for (long long i = 0; i < n; ++i) {
-    d[i] = dz(std::max(cz_host[i], 0.0) / kC);
-    dmax = std::max(dmax, d[i]);
-  }
-  const long long nb = (long long)std::ceil((dmax + pad) / bin_width);
-  *nbins_out = (int32_t)nb;
-  if (nb > max_bins || !logdens_out) return nb > max_bins ? fail(HM_EINVAL, "max_bins too small (see nbins_out)") : HM_OK;
-  std::vector<double> cnt(nb, 0.0);
-  for (long long i = 0; i < n; ++i) cnt[std::min<long long>((long long)(d[i] / bin_width), nb - 1)] += 1.0;
-  double tot = 0.0;
-  for (long long b = 0; b < nb; ++b) tot += cnt[b] + 0.5;
-  for (long long b = 0; b < nb; ++b) logdens_out[b] = std::log((cnt[b] + 0.5) / (tot * bin_width));
+  const std::vector<double> t = dz_histogram(omega_m, n, cz_host, bin_width, pad);
+  *nbins_out = (int32_t)t.size();
+  if ((long long)t.size() > max_bins || !logdens_out)
+    return (long long)t.size() > max_bins ? fail(HM_EINVAL, "max_bins too small (see nbins_out)") : HM_OK;
+  std::copy(t.begin(), t.end(), logdens_out);
   return HM_OK;
 }
 
@@ -869,8 +932,8 @@ int hm_philox(uint64_t seed, int64_t n, uint32_t c1, uint32_t c2, uint32_t c3, u
 // chain states
 // ---------------------------------------------------------------------------
 // CTAs per chain of the trajectory-start field kernel (momentum draw, save,
-// half kick and drift): enough that a single chain fills the GPU, at most
-// one node pair per thread and 1024 blocks.
+// half kick and drift): enough that a single chain fills the GPU, no more
+// threads than node pairs and at most 1024 blocks per chain.
 static int field_parts(long long n3) {
   return (int)std::min<long long>(1024, std::max<long long>(1, (n3 / 2 + 255) / 256));
 }
@@ -1814,17 +1877,34 @@ const char* hm_kernel_kind_name(int32_t kind) {
 // Posterior gradient without any device allocation.
 //
 // Some callers cannot let a library allocate device memory: code that runs
-// inside another framework's allocator or memory pool, code replayed from a
-// captured stream where an allocation would be illegal, or embedded hosts
-// that budget every byte up front.  hm_logpost_grad_noalloc serves them by
-// taking its scratch from one statically sized device array that every GPU
-// loading this library holds until the process exits.  It launches the same
-// kernels as hm_logpost_grad, all on the caller's stream, and never calls
-// cudaMalloc, cudaFree or any other allocating routine.
+// inside another framework's allocator or memory pool, which must account for
+// every device byte itself, and hosts that budget device memory up front and
+// allow no allocation once they run (cudaMalloc and cudaFree may also
+// synchronise the device, which such hosts cannot afford mid-run).
+// hm_logpost_grad_noalloc serves them by taking its scratch from one
+// statically sized device array that every GPU loading this library holds
+// until the process exits.  It launches the same kernels as hm_logpost_grad,
+// all on the caller's stream, and never calls cudaMalloc, cudaFree or any
+// other allocating routine.
 // ---------------------------------------------------------------------------
 constexpr size_t kNoAllocScratchBytes = 4u << 20;   // 4 MiB per device
+constexpr int kNoAllocMaxDevices = 64;
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
-static void* g_noalloc_base[64];                     // device address of the array, per device
+// Device address of the array, looked up once per device with that device
+// current (host code cannot use the symbol itself as a device pointer).
+static std::once_flag g_noalloc_once[kNoAllocMaxDevices];
+static void* g_noalloc_base[kNoAllocMaxDevices];
+
+// The per-call constants, passed by value, and the state that must start at
+// zero on every call (chain scalars, chain word, bucket counts).
+__global__ void k_noalloc_init(PointParams P, PointParams* pp, ChainScal* cs, int* cid, int* cnt, int ncnt) {
+  if (threadIdx.x == 0) {
+    *pp = P;
+    *cs = ChainScal{};
+    *cid = 0;
+  }
+  for (int i = threadIdx.x; i < ncnt; i += blockDim.x) cnt[i] = 0;
+}
 
 namespace {
 struct NoAllocLayout {
@@ -1870,7 +1950,8 @@ extern "C" int hm_logpost_grad_noalloc(hm_problem* p, const void* w_dev, const d
   if (!p || !w_dev || !psi_dev || !grad_w_dev) return fail(HM_EINVAL, "null argument");
   if (p->n > 0 && (!d_dev || !grad_d_dev)) return fail(HM_EINVAL, "null distance argument");
   if (!p->rx.p) return fail(HM_ESTATE, "no catalogue set");
-  if (p->device < 0 || p->device >= 64) return fail(HM_EINVAL, "device ordinal out of range for the static scratch");
+  if (p->device < 0 || p->device >= kNoAllocMaxDevices)
+    return fail(HM_EINVAL, "device ordinal out of range for the static scratch");
   const NoAllocLayout L = noalloc_layout(p);
   if (L.total > kNoAllocScratchBytes)
     return fail(HM_EINVAL, "problem too large for the no-allocation path: needs " + std::to_string(L.total) +
@@ -1879,22 +1960,25 @@ extern "C" int hm_logpost_grad_noalloc(hm_problem* p, const void* w_dev, const d
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   HM_CUDA(cudaSetDevice(p->device));
   // once per device, with that device current: the array's device address
-  if (!g_noalloc_base[p->device]) {
-    void* base = nullptr;
-    HM_CUDA(cudaGetSymbolAddress(&base, g_noalloc_scratch));
-    g_noalloc_base[p->device] = base;
+  // (host threads making their first call at the same time wait for one
+  // lookup; a failed lookup is retried by the next call)
+  cudaError_t look = cudaSuccess;
+  try {
+    std::call_once(g_noalloc_once[p->device], [&] {
+      void* base = nullptr;
+      look = cudaGetSymbolAddress(&base, g_noalloc_scratch);
+      if (look != cudaSuccess) throw look;
+      g_noalloc_base[p->device] = base;
+    });
+  } catch (cudaError_t e) {
+    return fail(HM_ECUDA, std::string("cudaGetSymbolAddress of the static scratch: ") + cudaGetErrorString(e));
   }
   char* b = static_cast<char*>(g_noalloc_base[p->device]);
   const int NB = p->N * plane_split(p->N);
-  // per-call constants (copied from host stack values; a pageable source is
-  // staged before cudaMemcpyAsync returns) and the state that must start at zero
-  const PointParams P = point_params(p, 0);
-  const ChainScal S{};
-  const int zero_id = 0;
-  HM_CUDA(cudaMemcpyAsync(b + L.pp, &P, sizeof(P), cudaMemcpyHostToDevice, st));
-  HM_CUDA(cudaMemcpyAsync(b + L.cs, &S, sizeof(S), cudaMemcpyHostToDevice, st));
-  HM_CUDA(cudaMemcpyAsync(b + L.cid, &zero_id, sizeof(zero_id), cudaMemcpyHostToDevice, st));
-  HM_CUDA(cudaMemsetAsync(b + L.cnt, 0, 4 * 2 * (size_t)NB, st));
+  k_noalloc_init<<<1, 64, 0, st>>>(point_params(p, 0), reinterpret_cast<PointParams*>(b + L.pp),
+                                   reinterpret_cast<ChainScal*>(b + L.cs), reinterpret_cast<int*>(b + L.cid),
+                                   reinterpret_cast<int*>(b + L.cnt), 2 * NB);
+  HM_CUDA(cudaGetLastError());
   PointArrays pa{};
   pa.rx = p->rx.as<double>();
   pa.ry = p->ry.as<double>();

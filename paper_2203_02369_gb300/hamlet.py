@@ -34,7 +34,9 @@ def _dptr(a):
 class Problem:
     """One reconstruction problem: grid, cosmology, catalogue, distance prior.
 
-    prior: ("table", d0, bin_width, logdens) or ("power", alpha, dmin, dmax).
+    prior: None or ("dz", bin_width, pad): eq. D from the redshifts of each
+    catalogue set (section "Priors"; bin_width <= 0: 5 Mpc/h, pad <= 0:
+    3 sigma_v/H0); ("table", d0, bin_width, logdens); ("power", alpha, dmin, dmax).
     """
 
     def __init__(self, N, L, cosmo=None, sigma_nl=250.0, precision="fp32", prior=None,
@@ -58,9 +60,13 @@ class Problem:
         d.T_cmb = c.get("T_cmb", 2.7255)
         d.f_growth = c.get("f_growth", -1.0)
         d.sigma_nl = float(sigma_nl)
-        prior = prior or ("power", 2.0, 0.5, 0.45 * L)
+        prior = prior or ("dz", 0.0, 0.0)
         self._prior_keep = None
-        if prior[0] == "table":
+        if prior[0] == "dz":
+            d.prior_kind = _lib.HM_PRIOR_DZ
+            d.prior_bin = float(prior[1])
+            d.prior_pad = float(prior[2])
+        elif prior[0] == "table":
             d.prior_kind = _lib.HM_PRIOR_TABLE
             d.prior_d0 = float(prior[1])
             d.prior_bin = float(prior[2])
@@ -84,8 +90,9 @@ class Problem:
 
     @classmethod
     def from_mock(cls, spec: MockSpec, cat: dict, device=0, prior=None):
-        p = cls(spec.N, spec.L, spec.cosmo, spec.sigma_nl, spec.precision,
-                prior or ("table", cat["prior_d0"], cat["prior_bin"], cat["prior_logdens"]),
+        """The mock's problem; the distance prior defaults to eq. D built from
+        its redshifts with the spec's bin width."""
+        p = cls(spec.N, spec.L, spec.cosmo, spec.sigma_nl, spec.precision, prior or ("dz", spec.prior_bin, 0.0),
                 device=device)
         p.set_catalog(cat["rhat"], cat["mu"], cat["sigma_mu"], cat["cz"], cat["sigma_cz"])
         return p
@@ -153,6 +160,15 @@ class Problem:
                                                _stream()))
         return psi, gw, gd
 
+    def prior_table(self):
+        """(d0, bin width, ln pi_D at the bin centres) of the distance prior
+        as the device reads it."""
+        nb, d0, bw = ct.c_int32(), ct.c_double(), ct.c_double()
+        check(self.lib.hm_problem_prior_table(self.h, 0, None, ct.byref(nb), ct.byref(d0), ct.byref(bw)))
+        t = np.zeros(max(nb.value, 1))
+        check(self.lib.hm_problem_prior_table(self.h, nb.value, _dptr(t), ct.byref(nb), None, None))
+        return d0.value, bw.value, t[:nb.value].copy()
+
     def last_status(self):
         v = ct.c_int32()
         check(self.lib.hm_problem_last_status(self.h, _stream(), ct.byref(v)))
@@ -214,6 +230,9 @@ class State:
         p0 = self.problems[0]
         self.N, self.dtype, self.device = p0.N, p0.dtype, p0.device
         self._an_radii = None
+        self.seed = int(seed)
+        self.chain_ids = list(chain_ids) if chain_ids is not None else list(range(nch))
+        self._sig_on = False
 
     def close(self):
         if self.h:
@@ -277,7 +296,68 @@ class State:
         check(self.lib.hm_state_profile_read(self.h, 64, ms, ln, ct.byref(nk)))
         return {self.lib.hm_kernel_kind_name(k).decode(): (ms[k], ln[k]) for k in range(nk.value)}
 
+    # -- checkpoint / resume ------------------------------------------------
+    # A chain is resumed exactly by its position (w, d; sigma_NL when it is
+    # sampled) and its trajectory counter: the momenta are drawn afresh at the
+    # start of every trajectory from Philox counters (element pair,
+    # trajectory, chain word, tag) under the state's key, so the continued
+    # chain draws the numbers the uninterrupted one would have drawn.
+    # File layout (little endian): 8-byte magic, int32 version, N, precision
+    # (0 FP32, 1 FP64), sigma_NL sampled flag; int64 n points, trajectory
+    # counter, Philox key, chain word; float64 sigma_NL; then w (N^3 values of
+    # the field precision) and d (n float64).
+    CHECKPOINT_MAGIC = b"HMCHAIN\x01"
+    _HDR = "<8siiiiqqqqd"
+
+    def save(self, path, chain=0):
+        """Write chain `chain`'s resumable state to a host file."""
+        import struct
+        g = self.get(chain)
+        traj = self.scalars(chain)["traj"]
+        sig = float(self.sigma_nl()[0][chain]) if self._sig_on else 0.0
+        prec = 0 if self.dtype == torch.float32 else 1
+        hdr = struct.pack(self._HDR, self.CHECKPOINT_MAGIC, 1, self.N, prec, int(self._sig_on), self._n(chain),
+                          int(traj), self.seed, int(self.chain_ids[chain]), sig)
+        with open(path, "wb") as fh:
+            fh.write(hdr)
+            fh.write(g["w"].cpu().numpy().tobytes())
+            fh.write(g["d"].cpu().numpy().astype(np.float64).tobytes())
+
+    def restore(self, path, chain=0):
+        """Load a state written by save() into chain `chain` (same grid,
+        precision, catalogue size, Philox key and chain word), set its
+        trajectory counter and re-evaluate Psi and the gradient there."""
+        import struct
+        with open(path, "rb") as fh:
+            raw = fh.read()
+        hs = struct.calcsize(self._HDR)
+        magic, ver, N, prec, sig_on, n, traj, seed, cid, sig = struct.unpack(self._HDR, raw[:hs])
+        if magic != self.CHECKPOINT_MAGIC or ver != 1:
+            raise HamletError(-1, f"{path}: not a chain checkpoint")
+        mine = 0 if self.dtype == torch.float32 else 1
+        if (N, prec, n) != (self.N, mine, self._n(chain)):
+            raise HamletError(-1, f"{path}: grid/precision/points {(N, prec, n)} differ from the chain's "
+                                  f"{(self.N, mine, self._n(chain))}")
+        if (seed, cid) != (self.seed, int(self.chain_ids[chain])):
+            raise HamletError(-1, f"{path}: Philox key/chain word {(seed, cid)} differ from the chain's "
+                                  f"{(self.seed, int(self.chain_ids[chain]))}: it would not continue its stream")
+        esz = 4 if prec == 0 else 8
+        nw = N ** 3 * esz
+        if len(raw) != hs + nw + 8 * n:
+            raise HamletError(-1, f"{path}: truncated checkpoint")
+        w = np.frombuffer(raw, dtype=np.float32 if prec == 0 else np.float64, count=N ** 3, offset=hs)
+        d = np.frombuffer(raw, dtype=np.float64, count=n, offset=hs + nw)
+        self.set(chain, w=torch.tensor(w.reshape((N,) * 3).copy()), d=torch.tensor(d.copy()))
+        self.set_traj(chain, traj)
+        if sig_on:
+            cur = self.sigma_nl()[0] if self._sig_on else np.full(self.C, sig)
+            cur[chain] = sig
+            self.sample_sigma_nl(True, cur)
+        else:
+            self.refresh()
+
     def sample_sigma_nl(self, enable=True, sigma0=None):
+        self._sig_on = bool(enable)
         s0 = None if sigma0 is None else np.ascontiguousarray(
             np.broadcast_to(np.asarray(sigma0, dtype=np.float64), (self.C,)))
         check(self.lib.hm_state_sample_sigma_nl(self.h, int(bool(enable)), _dptr(s0) if s0 is not None else None,

@@ -8,6 +8,8 @@
  *        double sigma_nl, double prior_d0, double prior_bin, int32 nbins,
  *        int32 pad, double logdens[nbins], double rhat[3n], double mu[n],
  *        double sigma_mu[n], double cz[n], double w[N^3], double d[n]
+ *        (nbins = 0: the default distance prior, eq. D built by the library
+ *        from the redshifts, bins of prior_bin or 5 Mpc/h when <= 0)
  * output: double psi, double grad_w[N^3], double grad_d[n],
  *         double H_new[2], int32 accept[2], int32 rc
  * usage:  hamlet_client in.bin out.bin
@@ -53,7 +55,7 @@ int main(int argc, char** argv) {
       rd(f, &d0, 8, 1) || rd(f, &bin, 8, 1) || rd(f, &nbins, 4, 1) || rd(f, &pad, 4, 1))
     return 1;
   const size_t n3 = (size_t)N * N * N;
-  double* logd = malloc(8 * (size_t)nbins);
+  double* logd = malloc(8 * (size_t)(nbins > 0 ? nbins : 1));
   double* rhat = malloc(8 * 3 * (size_t)n);
   double* mu = malloc(8 * (size_t)n);
   double* smu = malloc(8 * (size_t)n);
@@ -82,7 +84,7 @@ int main(int argc, char** argv) {
   desc.prior_d0 = d0;
   desc.prior_bin = bin;
   desc.prior_nbins = nbins;
-  desc.prior_logdens_host = logd;
+  desc.prior_logdens_host = nbins > 0 ? logd : NULL;
   desc.device = 0;
   hm_problem* p = NULL;
   CK(hm_init_problem(&desc, &p));

@@ -58,8 +58,15 @@ def test_invalid_problem_rejected_before_any_device_call():
     d.T_cmb = 2.7255
     d.n_s = 0.96
     d.sigma_nl = 150.0
-    d.prior_kind = _lib.HM_PRIOR_TABLE   # table without data
+    d.prior_kind = _lib.HM_PRIOR_TABLE   # a table of 5 bins without its data
+    d.prior_nbins = 5
+    d.prior_bin = 5.0
     assert lib.hm_init_problem(ct.byref(d), ct.byref(h)) == _lib.HM_EINVAL
+    d.prior_nbins = 0                    # the redshift-distance prior with a negative pad
+    d.prior_kind = _lib.HM_PRIOR_DZ
+    d.prior_pad = -1.0
+    assert lib.hm_init_problem(ct.byref(d), ct.byref(h)) == _lib.HM_EINVAL
+    assert b"prior_pad" in lib.hm_last_error()
     assert lib.hm_set_catalog(None, 0, None, None, None, None, None) == _lib.HM_EINVAL
     assert lib.hm_run_chain(None, 1, 1, None, 1, 0, None, None) == _lib.HM_EINVAL
 

@@ -42,6 +42,7 @@ def test_c_client_matches_oracle_and_binding(tmp_path):
     torch = pytest.importorskip("torch")
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
+    from _parity import check, check_scalar
     from oracle import hamlet_oracle as O
     from paper_2203_02369_gb300 import mock
     from paper_2203_02369_gb300.hamlet import Problem
@@ -51,13 +52,12 @@ def test_c_client_matches_oracle_and_binding(tmp_path):
     w = mock.white_field(16, 5)
     d = cat["d_init"]
     n = d.shape[0]
-    ld = np.ascontiguousarray(cat["prior_logdens"], dtype=np.float64)
     inp = tmp_path / "in.bin"
     with open(inp, "wb") as fh:
-        fh.write(struct.pack("<iiqdddd", 16, 1, n, spec.L, spec.sigma_nl, float(cat["prior_d0"]),
-                             float(cat["prior_bin"])))
-        fh.write(struct.pack("<ii", ld.shape[0], 0))
-        for a in (ld, cat["rhat"], cat["mu"], cat["sigma_mu"], cat["cz"], w, d):
+        # nbins = 0: the default distance prior, eq. D from the redshifts
+        fh.write(struct.pack("<iiqdddd", 16, 1, n, spec.L, spec.sigma_nl, 0.0, 0.0))
+        fh.write(struct.pack("<ii", 0, 0))
+        for a in (cat["rhat"], cat["mu"], cat["sigma_mu"], cat["cz"], w, d):
             fh.write(np.ascontiguousarray(a, dtype=np.float64).tobytes())
     out = tmp_path / "out.bin"
     r = subprocess.run([exe, str(inp), str(out)], capture_output=True, text=True, timeout=300)
@@ -70,9 +70,9 @@ def test_c_client_matches_oracle_and_binding(tmp_path):
     # the FP64 oracle
     op = O.problem_from_catalog(16, spec.L, mock.spec_dict(spec)["cosmo"], spec.sigma_nl, cat)
     rpsi, rgw, rgd = O.logpost_grad(op, w, d)
-    assert abs(psi - rpsi) <= 1e-12 * abs(rpsi)
-    assert np.linalg.norm(gw - rgw.ravel()) <= 1e-12 * np.linalg.norm(rgw)
-    assert np.linalg.norm(gd - rgd) <= 1e-12 * np.linalg.norm(rgd)
+    check_scalar("C client psi", psi, rpsi, 1e-12)
+    check("C client grad_w", gw, rgw, 1e-12)
+    check("C client grad_d", gd, rgd, 1e-12)
     _, _, recs = O.run_chain(op, np.zeros((16, 16, 16)), d, seed=3, chain=0, traj0=0, n_traj=2, eps=0.03,
                              n_steps=10)
     for t in range(2):
@@ -81,3 +81,5 @@ def test_c_client_matches_oracle_and_binding(tmp_path):
     gp = Problem.from_mock(spec, cat)
     bpsi, bgw, bgd = gp.logpost_grad(torch.tensor(w, device="cuda"), torch.tensor(d, device="cuda"))
     assert abs(psi - bpsi.item()) <= 1e-12 * abs(rpsi)
+    check("C client vs binding grad_w", gw, bgw, 1e-12)
+    check("C client vs binding grad_d", gd, bgd, 1e-12)

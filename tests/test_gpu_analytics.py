@@ -7,6 +7,7 @@ import numpy as np
 import pytest
 import torch
 
+from _parity import check
 from oracle import hamlet_oracle as O
 from paper_2203_02369_gb300 import mock
 
@@ -34,9 +35,8 @@ def _case(H, N, L, n, prec, seed):
     spec = mock.MockSpec(N=N, L=L, n_points=n, r_max=0.32 * L, mask_deg=0.0, sigma_mu=(0.2, 0.45),
                          sigma_nl=250.0, seed=seed, precision=prec)
     cat = mock.make_catalog(spec)
-    prior = ("table", cat["prior_d0"], cat["prior_bin"], cat["prior_logdens"])
-    gp = H.Problem.from_mock(spec, cat, prior=prior)
-    op = O.problem_from_catalog(N, L, mock.spec_dict(spec)["cosmo"], spec.sigma_nl, cat, prior=prior)
+    gp = H.Problem.from_mock(spec, cat)
+    op = O.problem_from_catalog(N, L, mock.spec_dict(spec)["cosmo"], spec.sigma_nl, cat)
     return cat, gp, op
 
 
@@ -75,17 +75,17 @@ def test_chain_analytics_vs_oracle(H, N, L, n, prec, n_traj, eps, n_steps, tol):
     states = _oracle_states(op, cat["d_init"], n_traj, eps, n_steps)
     # the two chains took the same decisions (else the comparison is moot)
     g = st.get(0)
-    assert rel(g["w"].cpu().numpy(), states[-1]) < (1e-10 if prec == "fp64" else 1e-4)
+    check(f"analytics chain w {prec}", g["w"], states[-1], 1e-10 if prec == "fp64" else 1e-4)
     assert tr[:, 0]["accept"].sum() > 0
     out = st.analytics_read(0)
     md, vd, mv, vv, met, sm, sv = _oracle_analytics(op, states)
     assert out["n_samples"] == n_traj
-    assert rel(out["mean_delta"].cpu().numpy(), md) < tol
-    assert rel(out["var_delta"].cpu().numpy(), vd) < 10 * tol
-    assert rel(out["mean_vr"].cpu().numpy(), mv) < tol
-    assert rel(out["var_vr"].cpu().numpy(), vv) < 10 * tol
+    check(f"mean delta {prec}", out["mean_delta"], md, tol)
+    check(f"var delta {prec}", out["var_delta"], vd, 10 * tol)
+    check(f"mean v_r {prec}", out["mean_vr"], mv, tol)
+    check(f"var v_r {prec}", out["var_vr"], vv, 10 * tol)
     assert out["metric"].shape == met.shape
-    assert rel(out["metric"], met) < 10 * tol
+    check(f"convergence metric {prec}", out["metric"], met, 10 * tol)
     sph = out["sphere"]
     assert sph.shape == (len(RADII), 5, 2)
     # sphere means are compared against the scale of the quantity (the

@@ -141,9 +141,15 @@ def test_slot_job_sampling_sigma_nl_matches_its_alone_chain(H):
     sl = H.Slots(tmpl, n_slots=2, max_points=500, seed=SEED)
     sl.load(b[2], b[1]["d_init"], chain_id=8, eps0=EPS)
     i = sl.load(a[2], a[1]["d_init"], chain_id=7, eps0=EPS, sigma_nl0=s0)
-    got = sl.run(4, L_STEPS)[:, i]
+    tr = sl.run(4, L_STEPS)
+    got = tr[:, i]
     sig, gsig = sl.sigma_nl()
-    assert sig[1 - i] == a[0].sigma_nl or sig[1 - i] == b[0].sigma_nl   # the fixed job reports its problem's value
+    # the fixed job reports its problem's value and no gradient, and draws its
+    # one-chain (fixed sigma_NL) chain
+    assert sig[1 - i] == b[0].sigma_nl
+    assert gsig[1 - i] == 0.0
+    ref_b, _, _ = _alone(H, b[2], b[1], 8, 4)
+    _same(tr[:, 1 - i], ref_b)
     st = H.State(a[2], [a[1]["d_init"]], seed=SEED, chain_ids=[7])
     st.sample_sigma_nl(True, s0)
     ref = st.run_chain(4, L_STEPS, EPS, use_graph=True)[:, 0]

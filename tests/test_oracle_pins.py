@@ -587,6 +587,28 @@ def test_dz_prior_table_counts_and_normalisation():
 
 
 # ------------------------------------------------------ sampled sigma_NL ----
+def test_dz_prior_kind_is_the_histogram_of_the_redshift_distances():
+    # ("dz", bin, pad): eq. D from the catalogue's own cz (section "Priors");
+    # default bin 5 Mpc/h and pad 3 sigma_v/H0
+    p, _ = tiny_problem(N=8, L=400.0, n=300, prior=("dz", 0.0, 0.0))
+    _, d0, bw, t = p.prior
+    assert (d0, bw) == (0.0, 5.0)
+    assert np.array_equal(t, O.dz_prior_table(p.cz, 0.3, 5.0, 3.0 * p.sigma_v / O.H0))
+    q, _ = tiny_problem(N=8, L=400.0, n=300, prior=("dz", 4.0, 12.0))
+    assert np.array_equal(q.prior[3], O.dz_prior_table(q.cz, 0.3, 4.0, 12.0))
+
+
+@pytest.mark.parametrize("name", sorted(mock.PRESETS))
+def test_preset_start_distances_inside_the_dz_prior_support(name):
+    # the chains start at cz/H0, which is inside [0, max d_z + pad): d_z < cz/H0
+    # by less than the pad at these redshifts
+    spec = mock.PRESETS[name]
+    cat = mock.make_catalog(spec)
+    op = O.problem_from_catalog(spec.N, spec.L, mock.spec_dict(spec)["cosmo"], spec.sigma_nl, cat)
+    lp, _ = O.log_prior_d(op, cat["d_init"])
+    assert np.all(np.isfinite(lp))
+
+
 def test_sigma_nl_gradient_central_differences_and_consistency():
     p, d = tiny_problem(N=8, L=80.0, n=40, sigma_cz=50.0)
     rng = np.random.default_rng(17)

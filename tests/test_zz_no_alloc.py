@@ -1,9 +1,10 @@
 """The no-allocation gradient entry point against the ordinary one.
 
 hm_logpost_grad_noalloc exists for callers that cannot let the library
-allocate device memory (inside another framework's memory pool, inside a
-stream capture, on hosts that budget device memory up front); it takes its
-scratch from one static device array.  This file is collected last on
+allocate device memory (code inside another framework's memory pool, which
+accounts for every device byte itself; hosts that budget device memory up
+front and allow no allocation once they run); it takes its scratch from one
+static device array.  This file is collected last on
 purpose, so that a run stopping at its first failure has already run every
 other test.  It must pass alone in a fresh process and after the others.
 """
