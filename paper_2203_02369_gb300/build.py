@@ -19,7 +19,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(BUILD, "libhamlet.so")
 
-SOURCES = ["hm_api.cu", "hm_fft_kernels.cu", "hm_fft_cluster.cu", "hm_points.cu", "hm_hmc.cu", "hm_analytics.cu"]
+SOURCES = ["hm_api.cu", "hm_fft_kernels.cu", "hm_fft_256.cu", "hm_points.cu", "hm_hmc.cu", "hm_analytics.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "-Xcompiler", "-ffp-contract=off",

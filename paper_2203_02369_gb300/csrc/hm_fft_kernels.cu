@@ -824,7 +824,8 @@ static cudaError_t pencil_t(const void* in, long long in_stride, void* out, long
 
 // Supported grids: N in {8, 16, 32, 64, 128} at both precisions (one x-plane
 // of the half spectrum fits one CTA's shared memory), and N = 256 at FP32
-// (plane passes as 8-CTA clusters, hm_fft_cluster.cu).
+// (plane passes as a z pass over row slabs and a y pass over column tiles,
+// hm_fft_256.cu).
 bool fft_supported(int prec, int N) {
   return N == 8 || N == 16 || N == 32 || N == 64 || N == 128 || (N == 256 && prec == 0);
 }
@@ -893,14 +894,14 @@ cudaError_t fft_prepare(int prec, int N) {
   if (N == 256) {
     if (prec != 0) return cudaErrorInvalidValue;
     cudaError_t e = prepare_pencil_t<float, 256>();
-    return e != cudaSuccess ? e : plane_cl_prepare();
+    return e != cudaSuccess ? e : plane256_prepare();
   }
   HM_DISPATCH_N(prec, N, (prepare_t<T, NN>()), (prepare_t<T, NN>()));
 }
 
 cudaError_t launch_plane_r2c(int prec, int N, const void* in, long long in_stride, void* out,
                              long long out_stride, int count, const void* tw, cudaStream_t st) {
-  if (N == 256) return prec == 0 ? launch_plane_r2c_cl(in, in_stride, out, out_stride, count, tw, nullptr, st)
+  if (N == 256) return prec == 0 ? launch_plane_r2c_256(in, in_stride, out, out_stride, count, tw, nullptr, st)
                                  : cudaErrorInvalidValue;
   PlanePoints none{};
   HM_DISPATCH_N(prec, N, (plane_r2c_t<T, NN, false>(in, in_stride, out, out_stride, count, tw, none, st)),
@@ -909,7 +910,7 @@ cudaError_t launch_plane_r2c(int prec, int N, const void* in, long long in_strid
 
 cudaError_t launch_plane_r2c_scatter(int prec, int N, const PlanePoints& pts, void* out, long long out_stride,
                                      int count, const void* tw, cudaStream_t st) {
-  if (N == 256) return prec == 0 ? launch_plane_r2c_cl(nullptr, 0, out, out_stride, count, tw, &pts, st)
+  if (N == 256) return prec == 0 ? launch_plane_r2c_256(nullptr, 0, out, out_stride, count, tw, &pts, st)
                                  : cudaErrorInvalidValue;
   HM_DISPATCH_N(prec, N, (plane_r2c_t<T, NN, true>(nullptr, 0, out, out_stride, count, tw, pts, st)),
                 (plane_r2c_t<T, NN, true>(nullptr, 0, out, out_stride, count, tw, pts, st)));
@@ -919,7 +920,7 @@ cudaError_t launch_plane_c2r(int prec, int N, const void* in, long long in_strid
                              long long out_stride, int count, const void* tw, const FieldEpi* epi,
                              cudaStream_t st, void* next_spec) {
   if (N == 256)
-    return prec == 0 ? launch_plane_c2r_cl(epi ? C2R_EPI : C2R_STORE, in, in_stride, out, out_stride, count, tw, epi,
+    return prec == 0 ? launch_plane_c2r_256(epi ? C2R_EPI : C2R_STORE, in, in_stride, out, out_stride, count, tw, epi,
                                            nullptr, next_spec, st)
                      : cudaErrorInvalidValue;
   PlanePoints none{};
@@ -934,7 +935,7 @@ cudaError_t launch_plane_c2r(int prec, int N, const void* in, long long in_strid
 cudaError_t launch_plane_c2r_gather(int prec, int N, const void* in, long long in_stride,
                                     const PlanePoints& pts, int count, const void* tw, cudaStream_t st) {
   if (N == 256)
-    return prec == 0 ? launch_plane_c2r_cl(C2R_GATHER, in, in_stride, nullptr, 0, count, tw, nullptr, &pts, nullptr, st)
+    return prec == 0 ? launch_plane_c2r_256(C2R_GATHER, in, in_stride, nullptr, 0, count, tw, nullptr, &pts, nullptr, st)
                      : cudaErrorInvalidValue;
   HM_DISPATCH_N(prec, N, (plane_c2r_t<T, NN, C2R_GATHER>(in, in_stride, nullptr, 0, count, tw, nullptr, pts, st)),
                 (plane_c2r_t<T, NN, C2R_GATHER>(in, in_stride, nullptr, 0, count, tw, nullptr, pts, st)));

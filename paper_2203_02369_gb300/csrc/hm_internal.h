@@ -58,6 +58,9 @@ struct PointParams {
   double sigma_nl2;      // sigma_NL^2
   double ik2_nl, logk2_nl;  // 1/sigma_NL^2 and ln sigma_NL^2 (kappa^2 of a point with sigma_cz = 0)
   double minv_d;         // (sigma_v/H0)^2, inverse mass of a distance
+  double k3;             // 3 Omega_m H0 / c (zbar = c23 (1 - sqrt(1 - k3 d)))
+  double c23;            // 2 / (3 Omega_m)
+  double inv_h;          // 1 / h (luminosity distance in Mpc: d (1 + zbar) / h)
   int N;
   int prior_kind;
   int prior_nbins;
@@ -128,6 +131,7 @@ struct PointArrays {
   const double* ry;
   const double* rz;
   const double* mu;
+  const double* xr;      // 10^((mu - 25)/5): the luminosity distance (Mpc) of the observed modulus
   const double* ismu2;   // 1 / sigma_mu^2 per point
   const double* zobs;
   const double* scz;
@@ -142,7 +146,8 @@ struct PointArrays {
   int* off;       // [C][NB+1] bucket starts in the global bucket order
   void* rec;      // PtRec<T> [ntot] in bucket order
   void* part;     // T [12][ntot]: per (side, component) u and du partials, bucket order
-  double* lk;     // [6][ntot] terms of the point likelihood that depend on d only
+  double* lk;     // terms of the point likelihood that depend on d only: [6][ntot] doubles
+                  // on the FP64 path; on the FP32 path [ntot] doubles then [5][ntot] floats
   long long ntot;
 };
 
@@ -184,15 +189,16 @@ cudaError_t launch_pencil(int prec, int N, int mode, const void* in, long long i
                           long long out_stride, int count, const void* tw, const void* amp,
                           cudaStream_t st, const int* plane_off = nullptr);
 bool fft_supported(int prec, int N);
-// N = 256 plane passes (thread-block clusters, FP32): pts == nullptr loads
-// real grids, else scatters the bucketed residuals; mode is C2R_STORE (0),
-// C2R_EPI (1) or C2R_GATHER (2).
-cudaError_t plane_cl_prepare();
-cudaError_t launch_plane_r2c_cl(const void* in, long long in_stride, void* out, long long out_stride, int count,
-                                const void* tw, const PlanePoints* pts, cudaStream_t st);
-cudaError_t launch_plane_c2r_cl(int mode, const void* in, long long in_stride, void* out, long long out_stride,
-                                int count, const void* tw, const FieldEpi* epi, const PlanePoints* pts,
-                                void* next, cudaStream_t st);
+// N = 256 plane passes (FP32): a z pass over row slabs and a y pass over
+// column tiles (hm_fft_256.cu).  pts == nullptr loads real grids, else
+// scatters the bucketed residuals; mode is C2R_STORE (0), C2R_EPI (1) or
+// C2R_GATHER (2).  The inverse runs its y pass in place on `in`.
+cudaError_t plane256_prepare();
+cudaError_t launch_plane_r2c_256(const void* in, long long in_stride, void* out, long long out_stride, int count,
+                                 const void* tw, const PlanePoints* pts, cudaStream_t st);
+cudaError_t launch_plane_c2r_256(int mode, const void* in, long long in_stride, void* out, long long out_stride,
+                                 int count, const void* tw, const FieldEpi* epi, const PlanePoints* pts,
+                                 void* next, cudaStream_t st);
 // Raise the dynamic shared-memory limit of every FFT kernel for (prec, N) on
 // the current device; call once per device before any launch or capture.
 cudaError_t fft_prepare(int prec, int N);
