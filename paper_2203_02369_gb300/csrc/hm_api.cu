@@ -281,6 +281,7 @@ struct hm_problem {
   // catalogue
   long long n = 0;
   DevBuf rx, ry, rz, mu, smu, zobs, scz;
+  DevBuf xr;   // x_ref = 10^((mu - 25)/5): the luminosity distance (Mpc) the observed modulus states
   // standalone workspace (one chain)
   DevBuf S1, S2, hist, prior_part, pts_part, kin_part, pp, cs, chain_id;
   PtWork pw;
@@ -299,6 +300,7 @@ struct hm_state {
   std::vector<hm_problem*> chain_prob;
   DevBuf w, pw, gw, w0, gw0, S1, S2;
   DevBuf rx, ry, rz, mu, smu, zobs, scz, d, pd, gd, d0, gd0;
+  DevBuf xr;
   PtWork work;
   DevBuf prior_part, pts_part, kinb_f, kinb_p, kinl_f, kinl_p;
   DevBuf pp, cs, chain_id, eps_dev, trace_dev, gsig_part, sig_dev;
@@ -355,6 +357,7 @@ static PointArrays point_arrays(hm_state* s) {
   pa.ry = s->ry.as<double>();
   pa.rz = s->rz.as<double>();
   pa.mu = s->mu.as<double>();
+  pa.xr = s->xr.as<double>();
   pa.ismu2 = s->smu.as<double>();
   pa.zobs = s->zobs.as<double>();
   pa.scz = s->scz.as<double>();
@@ -376,6 +379,9 @@ static PointParams point_params(const hm_problem* p, long long off) {
   P.ik2_nl = 1.0 / P.sigma_nl2;
   P.logk2_nl = std::log(P.sigma_nl2);
   P.minv_d = p->minv_d;
+  P.k3 = 3.0 * p->desc.omega_m * kH0 / kC;
+  P.c23 = 2.0 / (3.0 * p->desc.omega_m);
+  P.inv_h = 1.0 / p->desc.h;
   P.N = p->N;
   P.ksplit = plane_split(p->N);
   P.rq = p->N / P.ksplit;
@@ -699,6 +705,9 @@ int hm_set_catalog(hm_problem* p, int64_t n, const double* rhat, const double* m
   HM_TRY(upload(p->ry, ry.data(), n));
   HM_TRY(upload(p->rz, rz.data(), n));
   HM_TRY(upload(p->mu, mu, n));
+  std::vector<double> xr(n);
+  for (long long i = 0; i < n; ++i) xr[i] = std::pow(10.0, (mu[i] - 25.0) / 5.0);
+  HM_TRY(upload(p->xr, xr.data(), n));
   std::vector<double> ismu2(n);
   for (long long i = 0; i < n; ++i) ismu2[i] = 1.0 / (smu[i] * smu[i]);
   HM_TRY(upload(p->smu, ismu2.data(), n));   // the device keeps 1/sigma_mu^2
@@ -799,6 +808,7 @@ int hm_logpost_grad(hm_problem* p, const void* w_dev, const double* d_dev, doubl
   pa.ry = p->ry.as<double>();
   pa.rz = p->rz.as<double>();
   pa.mu = p->mu.as<double>();
+  pa.xr = p->xr.as<double>();
   pa.ismu2 = p->smu.as<double>();
   pa.zobs = p->zobs.as<double>();
   pa.scz = p->scz.as<double>();
@@ -1030,7 +1040,8 @@ int hm_state_create_batch(hm_problem* const* problems, int32_t n_problems, int32
   HM_CUDA(cudaMemset(s->w.p, 0, rs * C * s->n3));
   HM_CUDA(cudaMemset(s->pw.p, 0, rs * C * s->n3));
   const size_t nt = (size_t)std::max<long long>(tot, 1);
-  DevBuf* dbl[] = {&s->rx, &s->ry, &s->rz, &s->mu, &s->smu, &s->zobs, &s->scz, &s->d, &s->pd, &s->gd, &s->d0, &s->gd0};
+  DevBuf* dbl[] = {&s->rx, &s->ry, &s->rz, &s->mu, &s->xr, &s->smu, &s->zobs,
+                   &s->scz, &s->d, &s->pd, &s->gd, &s->d0, &s->gd0};
   for (DevBuf* b : dbl) HM_TRY(b->alloc(8 * nt));
   HM_CUDA(cudaMemset(s->pd.p, 0, 8 * nt));
   HM_TRY(s->work.alloc(s->prec, n_chains, s->N, tot));
@@ -1043,6 +1054,7 @@ int hm_state_create_batch(hm_problem* const* problems, int32_t n_problems, int32
     HM_CUDA(cudaMemcpy((char*)s->ry.p + o, p->ry.p, b, cudaMemcpyDeviceToDevice));
     HM_CUDA(cudaMemcpy((char*)s->rz.p + o, p->rz.p, b, cudaMemcpyDeviceToDevice));
     HM_CUDA(cudaMemcpy((char*)s->mu.p + o, p->mu.p, b, cudaMemcpyDeviceToDevice));
+    HM_CUDA(cudaMemcpy((char*)s->xr.p + o, p->xr.p, b, cudaMemcpyDeviceToDevice));
     HM_CUDA(cudaMemcpy((char*)s->smu.p + o, p->smu.p, b, cudaMemcpyDeviceToDevice));
     HM_CUDA(cudaMemcpy((char*)s->zobs.p + o, p->zobs.p, b, cudaMemcpyDeviceToDevice));
     HM_CUDA(cudaMemcpy((char*)s->scz.p + o, p->scz.p, b, cudaMemcpyDeviceToDevice));
@@ -1473,7 +1485,8 @@ int hm_slots_create(hm_problem* templ, int32_t n_slots, int64_t max_points, uint
   HM_TRY(s->S1.alloc(2 * rs * 3 * C * s->nspec));
   HM_TRY(s->S2.alloc(2 * rs * 3 * C * s->nspec));
   const size_t nt = (size_t)std::max<long long>(tot, 1);
-  DevBuf* dbl[] = {&s->rx, &s->ry, &s->rz, &s->mu, &s->smu, &s->zobs, &s->scz, &s->d, &s->pd, &s->gd, &s->d0, &s->gd0};
+  DevBuf* dbl[] = {&s->rx, &s->ry, &s->rz, &s->mu, &s->xr, &s->smu, &s->zobs,
+                   &s->scz, &s->d, &s->pd, &s->gd, &s->d0, &s->gd0};
   for (DevBuf* b : dbl) HM_TRY(b->alloc(8 * nt));
   HM_TRY(s->work.alloc(s->prec, n_slots, s->N, tot));
   s->pp_host.assign(C, PointParams{});
@@ -1532,9 +1545,9 @@ int hm_slots_load(hm_state* s, hm_problem* job, int32_t chain_id, const double* 
   const long long n = job->n;
   if (n > 0) {
     const size_t b = 8 * (size_t)n, o = 8 * (size_t)off;
-    const DevBuf* src[] = {&job->rx, &job->ry, &job->rz, &job->mu, &job->smu, &job->zobs, &job->scz};
-    DevBuf* dst[] = {&s->rx, &s->ry, &s->rz, &s->mu, &s->smu, &s->zobs, &s->scz};
-    for (int k = 0; k < 7; ++k)
+    const DevBuf* src[] = {&job->rx, &job->ry, &job->rz, &job->mu, &job->xr, &job->smu, &job->zobs, &job->scz};
+    DevBuf* dst[] = {&s->rx, &s->ry, &s->rz, &s->mu, &s->xr, &s->smu, &s->zobs, &s->scz};
+    for (int k = 0; k < 8; ++k)
       HM_CUDA(cudaMemcpyAsync(static_cast<char*>(dst[k]->p) + o, src[k]->p, b, cudaMemcpyDeviceToDevice, st));
     // pageable host sources: each copy has consumed its source when it returns
     HM_CUDA(cudaMemcpyAsync(static_cast<char*>(s->d.p) + o, d_init_host, b, cudaMemcpyHostToDevice, st));
@@ -1984,6 +1997,7 @@ extern "C" int hm_logpost_grad_noalloc(hm_problem* p, const void* w_dev, const d
   pa.ry = p->ry.as<double>();
   pa.rz = p->rz.as<double>();
   pa.mu = p->mu.as<double>();
+  pa.xr = p->xr.as<double>();
   pa.ismu2 = p->smu.as<double>();
   pa.zobs = p->zobs.as<double>();
   pa.scz = p->scz.as<double>();

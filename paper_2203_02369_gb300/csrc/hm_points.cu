@@ -50,6 +50,37 @@ __device__ __forceinline__ bool log_prior(const PointParams& P, double d, double
   return true;
 }
 
+// The prior table read in FP32 on the FP32 path: the support test stays in
+// FP64 (it decides +inf exactly as the FP64 path does), the interpolation
+// between bin centres runs in FP32 (ln pi and its slope to ~1e-7 relative).
+__device__ __forceinline__ bool log_prior_f32(const PointParams& P, double d, float& lp, float& dlp) {
+  if (P.prior_kind == PRIOR_TABLE) {
+    const int nb = P.prior_nbins;
+    if (!(d >= P.prior_d0 && d < P.prior_d0 + nb * P.prior_bin)) return false;
+    const float t = (float)(d - P.prior_d0) / (float)P.prior_bin - 0.5f;
+    const float b = floorf(t);
+    const float f = t - b;
+    if (b < 0.0f) {
+      lp = (float)P.prior_logdens[0];
+      dlp = 0.0f;
+    } else if (b >= (float)(nb - 1)) {
+      lp = (float)P.prior_logdens[nb - 1];
+      dlp = 0.0f;
+    } else {
+      const int ib = (int)b;
+      const float a0 = (float)P.prior_logdens[ib], a1 = (float)P.prior_logdens[ib + 1];
+      lp = (1.0f - f) * a0 + f * a1;
+      dlp = (a1 - a0) / (float)P.prior_bin;
+    }
+    return true;
+  }
+  if (!(d >= P.prior_dmin && d <= P.prior_dmax)) return false;
+  const float df = (float)d;
+  lp = (float)P.prior_alpha * logf(df);
+  dlp = (float)P.prior_alpha / df;
+  return true;
+}
+
 __device__ __forceinline__ double block_sum(double v, double* red) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
@@ -82,14 +113,149 @@ k_points_prep(const PointParams* __restrict__ pp, PointArrays pa) {
   pa.slot[i] = atomicAdd(&pa.cnt[c * P.N * P.ksplit + key], 1);
 }
 
-// ... then the bucket offsets, the bucket-ordered point records, and the
-// d-only FP64 likelihood terms:
+// The terms of the point likelihood that depend on d alone (eqs. lmu, vrobs,
+// kappa, D) with their derivatives, FP64 path: everything in FP64.
 //   lk[0] = A   = (mu_i - mu(d))^2/(2 s_mu^2) + ln kappa - ln pi_D(d)  (+inf outside)
 //   lk[1] = A'  = dA/dd
 //   lk[2] = v_obs(d), lk[3] = v_obs'(d), lk[4] = 1/kappa^2, lk[5] = (kappa^2)'
+// F32LAYOUT writes the FP32 path's layout (A as a double, the rest as floats,
+// see place_terms_fp32) from the same FP64 arithmetic.
+template <bool F32LAYOUT>
+__device__ __forceinline__ void place_terms_fp64(const PointParams& P, PointArrays& pa, ChainScal* cs, int c,
+                                                 long long i, double d) {
+  const double om = P.omega_m;
+  const double x = 1.0 - 3.0 * om * kH0 * d / kC;
+  double lp = 0.0, dlp = 0.0;
+  const bool ok = d > 0.0 && x > 0.0 && log_prior(P, d, lp, dlp) && !(cs[c].sample_sig && !(cs[c].sig > 0.0));
+  const long long nt = pa.ntot;
+  if (!ok) {
+    pa.lk[i] = __longlong_as_double(0x7ff0000000000000LL);  // +inf
+    if constexpr (F32LAYOUT) {
+      float* f = reinterpret_cast<float*>(pa.lk + nt);
+      for (int k = 0; k < 5; ++k) f[k * nt + i] = 0.0f;
+    } else {
+      for (int k = 1; k < 6; ++k) pa.lk[k * nt + i] = 0.0;
+    }
+    atomicOr(&cs[c].status, STATUS_DOMAIN);
+    return;
+  }
+  const double sq = sqrt(x);
+  const double zb = 2.0 / (3.0 * om) * (1.0 - sq);
+  const double zbp = (kH0 / kC) / sq;
+  const double opz = 1.0 + zb;
+  const double iopz = 1.0 / opz;
+  const double mu_d = 5.0 * log10(d * opz / P.h) + 25.0;
+  const double mup = (5.0 / 2.302585092994045684) * (1.0 / d + zbp * iopz);
+  const double z = pa.zobs[i];
+  const double scz = pa.scz[i];
+  // kappa^2 = sigma_NL^2 + sigma_cz^2 / (1 + zbar)^2 (eq. kappa); with
+  // sigma_cz = 0 and a fixed sigma_NL it is a per-chain constant
+  double ik2, lk2, k2p;
+  if (scz == 0.0 && !cs[c].sample_sig) {
+    ik2 = P.ik2_nl;
+    lk2 = P.logk2_nl;
+    k2p = 0.0;
+  } else {
+    const double scz2 = scz * scz;
+    const double snl2 = cs[c].sample_sig ? cs[c].sig * cs[c].sig : P.sigma_nl2;
+    const double k2 = snl2 + scz2 * iopz * iopz;
+    ik2 = 1.0 / k2;
+    lk2 = log(k2);
+    k2p = -2.0 * scz2 * zbp * iopz * iopz * iopz;
+  }
+  const double ismu2 = pa.ismu2[i];
+  const double res_mu = pa.mu[i] - mu_d;
+  pa.lk[i] = 0.5 * res_mu * res_mu * ismu2 + 0.5 * lk2 - lp;
+  const double t[5] = {-res_mu * mup * ismu2 + 0.5 * k2p * ik2 - dlp, kC * (z - zb) * iopz,
+                       -kC * zbp * (1.0 + z) * iopz * iopz, ik2, k2p};
+  if constexpr (F32LAYOUT) {
+    float* f = reinterpret_cast<float*>(pa.lk + nt);
+#pragma unroll
+    for (int k = 0; k < 5; ++k) f[k * nt + i] = (float)t[k];
+  } else {
+#pragma unroll
+    for (int k = 0; k < 5; ++k) pa.lk[(k + 1) * nt + i] = t[k];
+  }
+}
+
+// The same terms on the FP32 path, where only the per-point sums and the
+// energies need FP64.  Two differences cancel and keep FP64 inputs:
+//  - z - zbar, a thousandth of z at these distances (the observed velocity
+//    is c (z - zbar)/(1 + zbar)), so zbar is formed to ~1e-14 in FP64 from
+//    FP32 seeds refined by one Newton step each: s = sqrt(1 - k3 d) and
+//    zbar = c23 k3 d / (1 + s) (= c23 (1 - s) without its cancellation);
+//  - mu_i - mu(d), a few tenths of ~35 mag: with x = d (1 + zbar)/h and
+//    x_ref = 10^((mu_i - 25)/5) (per point, from the host), mu_i - mu(d) =
+//    -(5/ln 10) ln(1 + (x - x_ref)/x_ref), so only x - x_ref is formed in
+//    FP64 and the logarithm runs in FP32 near 1.
+// Everything else is FP32.  Layout: lk[0..nt) doubles A; then floats
+// A', v_obs, v_obs', 1/kappa^2, (kappa^2)' at f[k nt + i], f = (float*)(lk + nt).
+__device__ __forceinline__ void place_terms_fp32(const PointParams& P, PointArrays& pa, ChainScal* cs, int c,
+                                                 long long i, double d) {
+  const long long nt = pa.ntot;
+  float* f = reinterpret_cast<float*>(pa.lk + nt);
+  const double eps3 = P.k3 * d;
+  const double om1 = 1.0 - eps3;
+  float lp = 0.0f, dlp = 0.0f;
+  const bool ok = d > 0.0 && om1 > 0.0 && log_prior_f32(P, d, lp, dlp) && !(cs[c].sample_sig && !(cs[c].sig > 0.0));
+  if (!ok) {
+    pa.lk[i] = __longlong_as_double(0x7ff0000000000000LL);  // +inf
+    for (int k = 0; k < 5; ++k) f[k * nt + i] = 0.0f;
+    atomicOr(&cs[c].status, STATUS_DOMAIN);
+    return;
+  }
+  // sqrt(1 - k3 d): FP32 seed, one Newton step s0 + (om1 - s0^2)/(2 s0)
+  const float s0 = sqrtf((float)om1);
+  const double s0d = (double)s0;
+  const double s = fma(fma(-s0d, s0d, om1), (double)(0.5f / s0), s0d);
+  // zbar = c23 eps3/(1 + s): FP32 reciprocal, one correction of the quotient
+  const double den = 1.0 + s;
+  const double rden = (double)(1.0f / (float)den);
+  double q = eps3 * rden;
+  q = fma(fma(-q, den, eps3), rden, q);
+  const double zb = P.c23 * q;
+  const double opz = 1.0 + zb;
+  const double xr = pa.xr[i];
+  const float qm1 = (float)fma(d * P.inv_h, opz, -xr) / (float)xr;   // x/x_ref - 1
+  constexpr float k5ln10 = 2.1714724095162591f;                       // 5 / ln 10
+  const float res_mu = -k5ln10 * log1pf(qm1);
+  const float iopz = 1.0f / (float)opz;
+  const float zbp = (float)(kH0 / kC) / (float)s;                      // dzbar/dd
+  const float mup = k5ln10 * (1.0f / (float)d + zbp * iopz);
+  const double z = pa.zobs[i];
+  const float vo = (float)kC * (float)(z - zb) * iopz;
+  const float vop = -(float)kC * zbp * (1.0f + (float)z) * iopz * iopz;
+  // kappa^2 = sigma_NL^2 + sigma_cz^2/(1 + zbar)^2 (eq. kappa); with
+  // sigma_cz = 0 and a fixed sigma_NL it is a per-chain constant
+  const double scz = pa.scz[i];
+  float ik2, k2p;
+  double lk2;
+  if (scz == 0.0 && !cs[c].sample_sig) {
+    ik2 = (float)P.ik2_nl;
+    lk2 = P.logk2_nl;
+    k2p = 0.0f;
+  } else {
+    const float scz2 = (float)(scz * scz);
+    const float snl2 = cs[c].sample_sig ? (float)(cs[c].sig * cs[c].sig) : (float)P.sigma_nl2;
+    const float k2 = snl2 + scz2 * iopz * iopz;
+    ik2 = 1.0f / k2;
+    lk2 = (double)logf(k2);
+    k2p = -2.0f * scz2 * zbp * iopz * iopz * iopz;
+  }
+  const float ismu2 = (float)pa.ismu2[i];
+  pa.lk[i] = (double)(0.5f * res_mu * res_mu * ismu2 - lp) + 0.5 * lk2;
+  f[i] = -res_mu * mup * ismu2 + 0.5f * k2p * ik2 - dlp;
+  f[nt + i] = vo;
+  f[2 * nt + i] = vop;
+  f[3 * nt + i] = ik2;
+  f[4 * nt + i] = k2p;
+}
+
+// ... then the bucket offsets, the bucket-ordered point records, and the
+// d-only likelihood terms (place_terms_fp64 / place_terms_fp32 above).
 template <typename T>
 __global__ void __launch_bounds__(kPtsNT)
-k_points_place(const PointParams* __restrict__ pp, PointArrays pa, ChainScal* __restrict__ cs) {
+k_points_place(const PointParams* __restrict__ pp, PointArrays pa, ChainScal* __restrict__ cs, int f32_terms) {
   pdl_wait();
   pdl_trigger();
   constexpr int kMaxNB = kMaxBuckets;   // sub-buckets per chain (N * ksplit)
@@ -155,54 +321,13 @@ k_points_place(const PointParams* __restrict__ pp, PointArrays pa, ChainScal* __
   r.yz = cp.iy * N + cp.iz;
   r.r = (T)0;
   static_cast<PtRec<T>*>(pa.rec)[pos] = r;
-  // likelihood terms that depend on d only (eqs. lmu, vrobs, kappa, D)
-  const double om = P.omega_m;
-  const double x = 1.0 - 3.0 * om * kH0 * d / kC;
-  double lp = 0.0, dlp = 0.0;
-  const bool ok = d > 0.0 && x > 0.0 && log_prior(P, d, lp, dlp) && !(cs[c].sample_sig && !(cs[c].sig > 0.0));
-  const long long nt = pa.ntot;
-  if (!ok) {
-    pa.lk[i] = __longlong_as_double(0x7ff0000000000000LL);  // +inf
-    pa.lk[nt + i] = 0.0;
-    pa.lk[2 * nt + i] = 0.0;
-    pa.lk[3 * nt + i] = 0.0;
-    pa.lk[4 * nt + i] = 0.0;
-    pa.lk[5 * nt + i] = 0.0;
-    atomicOr(&cs[c].status, STATUS_DOMAIN);
-    return;
-  }
-  const double sq = sqrt(x);
-  const double zb = 2.0 / (3.0 * om) * (1.0 - sq);
-  const double zbp = (kH0 / kC) / sq;
-  const double opz = 1.0 + zb;
-  const double iopz = 1.0 / opz;
-  const double mu_d = 5.0 * log10(d * opz / P.h) + 25.0;
-  const double mup = (5.0 / 2.302585092994045684) * (1.0 / d + zbp * iopz);
-  const double z = pa.zobs[i];
-  const double scz = pa.scz[i];
-  // kappa^2 = sigma_NL^2 + sigma_cz^2 / (1 + zbar)^2 (eq. kappa); with
-  // sigma_cz = 0 and a fixed sigma_NL it is a per-chain constant
-  double ik2, lk2, k2p;
-  if (scz == 0.0 && !cs[c].sample_sig) {
-    ik2 = P.ik2_nl;
-    lk2 = P.logk2_nl;
-    k2p = 0.0;
+  if constexpr (sizeof(T) == 8) {
+    place_terms_fp64<false>(P, pa, cs, c, i, d);
+  } else if (f32_terms) {
+    place_terms_fp32(P, pa, cs, c, i, d);
   } else {
-    const double scz2 = scz * scz;
-    const double snl2 = cs[c].sample_sig ? cs[c].sig * cs[c].sig : P.sigma_nl2;
-    const double k2 = snl2 + scz2 * iopz * iopz;
-    ik2 = 1.0 / k2;
-    lk2 = log(k2);
-    k2p = -2.0 * scz2 * zbp * iopz * iopz * iopz;
+    place_terms_fp64<true>(P, pa, cs, c, i, d);
   }
-  const double ismu2 = pa.ismu2[i];
-  const double res_mu = pa.mu[i] - mu_d;
-  pa.lk[i] = 0.5 * res_mu * res_mu * ismu2 + 0.5 * lk2 - lp;
-  pa.lk[nt + i] = -res_mu * mup * ismu2 + 0.5 * k2p * ik2 - dlp;
-  pa.lk[2 * nt + i] = kC * (z - zb) * iopz;
-  pa.lk[3 * nt + i] = -kC * zbp * (1.0 + z) * iopz * iopz;
-  pa.lk[4 * nt + i] = ik2;
-  pa.lk[5 * nt + i] = k2p;
 }
 
 // ---------------------------------------------------------------------------
@@ -234,28 +359,34 @@ k_points_lik(const PointParams* __restrict__ pp, PointArrays pa, double* __restr
       psi_i = A;
       rec[pos].r = (T)0;
       gd = 0.0;
+    } else if constexpr (sizeof(T) == 4) {
+      // FP32 path: the six FP32 partials summed with TwoSum, then the
+      // velocity term in FP32 (v_obs - u is a few hundred km/s, kept to
+      // ~1e-7 relative); Psi_i and the gradient go to FP64 for the sums and
+      // the distance update
+      const float* part = static_cast<const float*>(pa.part);
+      HalfSqAcc<float> su, sdu;
+#pragma unroll
+      for (int k = 0; k < 6; ++k) {
+        su.add(part[(long long)k * nt + pos]);
+        sdu.add(part[(long long)(6 + k) * nt + pos]);
+      }
+      const float u = su.hi + su.lo, du = sdu.hi + sdu.lo;
+      const float* f = reinterpret_cast<const float*>(pa.lk + nt);
+      const float Ap = f[i], vo = f[nt + i], vop = f[2 * nt + i], ik2 = f[3 * nt + i], k2p = f[4 * nt + i];
+      const float res_v = vo - u;
+      const float r2k = res_v * res_v * ik2;
+      psi_i = A + (double)(0.5f * r2k);
+      rec[pos].r = -res_v * ik2;
+      if (ssig) gsig = (double)((float)cs[c].sig * ik2 * (1.0f - r2k));
+      gd = (double)(Ap + res_v * (vop - du) * ik2 - 0.5f * r2k * k2p * ik2);
     } else {
       const T* part = static_cast<const T*>(pa.part);
-      double u, du;
-      if constexpr (sizeof(T) == 4) {
-        // the six FP32 partials summed with TwoSum (error-free FP32 pairs), so
-        // the FP64 result equals their exact sum to ~1e-14 without FP64 adds
-        HalfSqAcc<float> su, sdu;
+      double u = 0.0, du = 0.0;
 #pragma unroll
-        for (int k = 0; k < 6; ++k) {
-          su.add((float)part[(long long)k * nt + pos]);
-          sdu.add((float)part[(long long)(6 + k) * nt + pos]);
-        }
-        u = su.value();
-        du = sdu.value();
-      } else {
-        u = 0.0;
-        du = 0.0;
-#pragma unroll
-        for (int k = 0; k < 6; ++k) {
-          u += (double)part[(long long)k * nt + pos];
-          du += (double)part[(long long)(6 + k) * nt + pos];
-        }
+      for (int k = 0; k < 6; ++k) {
+        u += (double)part[(long long)k * nt + pos];
+        du += (double)part[(long long)(6 + k) * nt + pos];
       }
       const double vo = pa.lk[2 * nt + i], vop = pa.lk[3 * nt + i];
       const double ik2 = pa.lk[4 * nt + i], k2p = pa.lk[5 * nt + i];
@@ -400,9 +531,16 @@ cudaError_t launch_points_prep(int n_chains, int max_pts, const PointParams* pp,
 
 cudaError_t launch_points_place(int prec, int n_chains, int max_pts, const PointParams* pp,
                                 PointArrays pa, ChainScal* cs, cudaStream_t st) {
-  // runs even without points: block 0 writes the (empty) bucket offsets
-  if (prec == 0) return launch_k<PDL_POINTS>(k_points_place<float>, pts_grid(n_chains, max_pts), dim3(kPtsNT), 0, st, pp, pa, cs);
-  return launch_k<PDL_POINTS>(k_points_place<double>, pts_grid(n_chains, max_pts), dim3(kPtsNT), 0, st, pp, pa, cs);
+  // runs even without points: block 0 writes the (empty) bucket offsets.
+  // On the FP32 path the d-only terms run in FP32 when the launch covers
+  // several chains and in FP64 for one chain: this kernel runs on a side
+  // stream beside the plane passes, and on GB300 the shorter FP32 form sped
+  // the 16-chain 128^3 evaluation up by 5 % but slowed the one-chain
+  // trajectory by 4 % (same box, same bench; the output is the same layout)
+  if (prec == 0)
+    return launch_k<PDL_POINTS>(k_points_place<float>, pts_grid(n_chains, max_pts), dim3(kPtsNT), 0, st, pp, pa, cs,
+                                n_chains > 1 ? 1 : 0);
+  return launch_k<PDL_POINTS>(k_points_place<double>, pts_grid(n_chains, max_pts), dim3(kPtsNT), 0, st, pp, pa, cs, 0);
 }
 
 cudaError_t launch_points_lik(int prec, int n_chains, int max_pts, const PointParams* pp, PointArrays pa,

@@ -45,7 +45,7 @@ class MockSpec:
     seed: int
     precision: str = "fp32"  # "fp32" (FP32 fields, FP64 energy) or "fp64"
     cosmo: Cosmology = field(default_factory=Cosmology)
-    prior_bin: float = 5.0   # distance-prior histogram bin width (Mpc/h)
+    prior_bin: float = 5.0   # bin width (Mpc/h) of the distance prior's redshift-distance histogram
 
 
 # Presets with the sizes of the paper's mocks (PAPER "Mock Catalogue
@@ -111,8 +111,7 @@ def make_catalog(spec: MockSpec):
     """Draw one catalogue.  Returns a dict of float64 numpy arrays:
 
     rhat (n,3) unit directions, d_true (n,), mu (n,), sigma_mu (n,),
-    cz (n,) km/s, sigma_cz (n,) (zeros), d_init (n,) starting distances,
-    and the distance-prior histogram (prior_d0, prior_bin, prior_logdens).
+    cz (n,) km/s, sigma_cz (n,) (zeros), d_init (n,) starting distances.
     """
     rng = np.random.Generator(np.random.PCG64(spec.seed))
     n = spec.n_points
@@ -128,18 +127,10 @@ def make_catalog(spec: MockSpec):
     vr = np.sum(_smooth_flow(rng, x) * rhat, axis=1)
     cz = H0 * d_true + vr + spec.sigma_nl * rng.normal(size=n)
     sigma_cz = np.zeros(n)
-    # distance prior: histogram of the redshift-distance proxy cz/H0
-    bw = spec.prior_bin
-    dz = np.maximum(cz / H0, 0.5)
-    top = dz.max() + 3.0 * 350.0 / H0
-    nb = int(np.ceil(top / bw))
-    counts, _ = np.histogram(dz, bins=nb, range=(0.0, nb * bw))
-    dens = (counts + 0.5) / ((counts + 0.5).sum() * bw)
-    logdens = np.log(dens)
-    d_init = np.clip(dz, 0.5 * bw, nb * bw - 0.5 * bw)
+    # chains start at the redshift-distance proxy cz/H0, kept off the observer
+    d_init = np.maximum(cz / H0, 0.5 * spec.prior_bin)
     return dict(rhat=np.ascontiguousarray(rhat), d_true=d_true, mu=mu,
-                sigma_mu=sigma_mu, cz=cz, sigma_cz=sigma_cz, d_init=d_init,
-                prior_d0=0.0, prior_bin=bw, prior_logdens=logdens)
+                sigma_mu=sigma_mu, cz=cz, sigma_cz=sigma_cz, d_init=d_init)
 
 
 def white_field(N, seed):

@@ -275,6 +275,42 @@ def test_leapfrog_vs_oracle(H, N, L, n, prec, steps):
     check_scalar(f"psi {tag}", sc["psi"], psi1, tol)
 
 
+def test_leapfrog_two_chain_state_vs_oracle(H):
+    """A launch over several chains evaluates the FP32 path's distance terms
+    in FP32 (zbar and mu_i - mu(d) from FP64 differences, the rest FP32):
+    both chains of a two-chain 64^3 / 5,000-point state against the oracle."""
+    N, L, n, steps = 64, 500.0, 5000, 20
+    spec, cat, gp, op, st1 = _state_and_oracle(H, N, L, n, "fp32", 23)
+    st = H.State(gp, [cat["d_init"], cat["d_init"]], seed=77, chain_ids=[0, 1])
+    rng = np.random.default_rng(6)
+    d0 = cat["d_init"]
+    starts = []
+    for c in range(2):
+        w0 = (0.5 * rng.normal(size=(N, N, N))).astype(np.float32).astype(np.float64)
+        pw0 = rng.normal(size=(N, N, N)).astype(np.float32).astype(np.float64)
+        pd0 = rng.normal(size=n) / math.sqrt(op.minv_d)
+        st.set(c, w=torch.tensor(w0), d=torch.tensor(d0), pw=torch.tensor(pw0), pd=torch.tensor(pd0))
+        starts.append((w0, pw0, pd0))
+    st.refresh()
+    for c in range(2):
+        gw, gd = st.grad(c)
+        rpsi, rgw, rgd = O.logpost_grad(op, starts[c][0], d0)
+        check(f"two-chain grad_w chain {c}", gw, rgw, 1e-5)
+        check(f"two-chain grad_d chain {c}", gd, rgd, 1e-5)
+        check_scalar(f"two-chain psi chain {c}", st.scalars(c)["psi"], rpsi, 1e-5)
+    st.leapfrog(steps, 0.02)
+    for c in range(2):
+        w0, pw0, pd0 = starts[c]
+        g = st.get(c)
+        w1, d1, pw1, pd1, psi1, _, _ = O.leapfrog(op, w0, d0, pw0, pd0, 0.02, steps)
+        tag = f"two-chain leapfrog chain {c}"
+        check(f"w {tag}", g["w"], w1, 1e-5)
+        check(f"d {tag}", g["d"], d1, 1e-5)
+        check(f"p_w {tag}", g["pw"], pw1, 1e-5)
+        check(f"p_d {tag}", g["pd"], pd1, 1e-4)
+        check_scalar(f"psi {tag}", st.scalars(c)["psi"], psi1, 1e-5)
+
+
 def test_run_chain_vs_oracle_fp64(H):
     N, L, n = 16, 200.0, 500
     spec, cat, gp, op, st = _state_and_oracle(H, N, L, n, "fp64", 31)
