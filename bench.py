@@ -59,6 +59,8 @@ def parse():
     ap.add_argument("--accept-target", type=float, default=0.70,
                     help="acceptance the batched and served chains' step sizes are tuned to (dual averaging)")
     ap.add_argument("--tune-eps", action="store_true", help="print acceptance for a sweep of eps and exit")
+    ap.add_argument("--workload", default="grid128_30000pts", choices=["grid128_30000pts", "grid64_5000pts"],
+                    help="plain-chain preset (the headline is the 128^3 one; 64^3 for profiling the small grid)")
     return ap.parse_args()
 
 
@@ -214,24 +216,26 @@ def ncu_traffic(kind):
 # --------------------------------------------------------------------------
 # reference arm: the FP64 oracle on the host cores
 # --------------------------------------------------------------------------
-def oracle_problem():
+def oracle_problem(preset="grid128_30000pts"):
     from oracle import hamlet_oracle as O
-    spec = mock.PRESETS["grid128_30000pts"]
+    spec = mock.PRESETS[preset]
     cat = mock.make_catalog(spec)
     op = O.problem_from_catalog(spec.N, spec.L, mock.spec_dict(spec)["cosmo"], spec.sigma_nl, cat)
     return O, spec, cat, op
 
 
-def run_oracle_steps(n_steps, eps):
+def run_oracle_steps(n_steps, eps, preset="grid128_30000pts"):
     """n_steps oracle leapfrog steps (one gradient evaluation each) from the
-    mock start state; returns (seconds, evaluations)."""
-    O, spec, cat, op = oracle_problem()
+    mock start state; returns (seconds, evaluations, seconds of each step)."""
+    O, spec, cat, op = oracle_problem(preset)
     w = np.zeros((spec.N,) * 3)
     d = cat["d_init"].copy()
     pw, pd = O.draw_momenta(op, 2, 0, 0)
     psi, gw, gd = O.logpost_grad(op, w, d)
+    each = []
     t0 = time.perf_counter()
     for _ in range(n_steps):
+        t1 = time.perf_counter()
         pw -= 0.5 * eps * gw
         pd -= 0.5 * eps * gd
         w += eps * pw
@@ -239,7 +243,45 @@ def run_oracle_steps(n_steps, eps):
         psi, gw, gd = O.logpost_grad(op, w, d)
         pw -= 0.5 * eps * gw
         pd -= 0.5 * eps * gd
-    return time.perf_counter() - t0, n_steps
+        each.append(time.perf_counter() - t1)
+    return time.perf_counter() - t0, n_steps, each
+
+
+def _oracle_worker(args):
+    n_steps, eps = args
+    _, _, each = run_oracle_steps(n_steps, eps)
+    return each
+
+
+def run_oracle_all_cores(n_per_core, eps):
+    """The oracle as it stands on every host core at once: one process per
+    core (spawned, so no process inherits a CUDA context), each running
+    n_per_core leapfrog steps of the 128^3 workload on its own copy;
+    returns (evaluations/s over the wall time of the timed steps, cores)."""
+    import multiprocessing as mp
+    cores = os.cpu_count() or 1
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(cores) as pool:
+        pool.map(_oracle_worker, [(1, eps)] * cores)          # import, problem set-up, page-in
+        t0 = time.perf_counter()
+        res = pool.map(_oracle_worker, [(n_per_core, eps)] * cores)
+        wall = time.perf_counter() - t0
+    n = sum(len(r) for r in res)
+    return n / wall, cores, n, wall
+
+
+def cpu_baseline_leg(eps):
+    """The oracle timed on the host: all cores (the reported value), and one
+    core at 128^3 and 64^3 (median of 5 evaluations each)."""
+    val, cores, n, wall = run_oracle_all_cores(2, eps)
+    _, _, e128 = run_oracle_steps(5, eps)
+    _, _, e64 = run_oracle_steps(5, eps, preset="grid64_5000pts")
+    return {"value": val, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{n} oracle leapfrog steps (one gradient evaluation each) of this workload, numpy FP64, "
+                      f"{cores} processes of one thread each (independent copies), {wall:.1f} s wall",
+            "single_core_s_per_eval_median": {"grid128_30000pts": float(np.median(e128)),
+                                              "grid64_5000pts": float(np.median(e64))},
+            "single_core_grad_evals_per_s_128": 1.0 / float(np.median(e128))}
 
 
 def replica_aggregate(my_ms, units_per_rank, ws, device="cpu"):
@@ -259,18 +301,17 @@ def reference_arm(args):
     ws, rank, _ = dist_env()
     if rank != 0:
         return
-    # warm-up (import, FFT plans, page-in) then the timed steps
-    run_oracle_steps(max(1, min(args.warmup, 2)), args.eps)
-    secs, ev = run_oracle_steps(args.steps, args.eps)
-    val = ev / secs
+    # every step: one oracle leapfrog step on each host core at once (after
+    # a warm-up step per core for imports, problem set-up and page-in)
+    val, cores, n, wall = run_oracle_all_cores(args.steps, args.eps)
     line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * wall / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
             "config": {"workload": WORKLOAD, "grid": 128, "box": 500.0, "points": 30000,
-                       "step": "one oracle leapfrog step (one gradient evaluation)"},
-            "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": f"{args.steps} oracle leapfrog steps (numpy FP64, 1 thread)"},
+                       "step": f"one oracle leapfrog step (one gradient evaluation) on each of {cores} host cores"},
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"{n} oracle leapfrog steps (numpy FP64), {cores} processes of one thread"},
             "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -456,38 +497,41 @@ def run_batched_same(prob, d_init, eps, L, use_graph, n_chains=16, K=20, M=60):
                         "60-trajectory burn-in"}
 
 
-def run_serving(eps, L, target, grids=(64, 128, 256), n_range=(1e3, 1e5), n_jobs=12):
+def run_serving(eps, L, target, grids=(64, 128, 256), n_range=(1e3, 1e5), n_jobs=60, n_timed=50, grid_slots=None):
     """Poisson stream of reconstruction jobs (64^3 / 128^3 at 500 Mpc/h,
     256^3 at 1000 Mpc/h), all arriving within a fraction of a second so that
     the GPU is saturated.  Served by continuous batching (one slotted state
-    per grid, up to 8 jobs advancing in the same launches) and, for
-    reference, the same jobs one at a time.  Each job draws the same chain in
-    both runs (same seed and chain word per job, per-job step tuned by the
-    same dual averaging), so acceptance and accuracy are equal by
-    construction."""
+    per grid, up to 8 jobs advancing in the same launches; grid_slots caps a
+    grid's batch) and, for reference, the same jobs one at a time.  Each job
+    draws the same chain in both runs (same seed and chain word per job,
+    per-job step tuned by the same dual averaging), so acceptance and
+    accuracy are equal by construction."""
     from paper_2203_02369_gb300.serve import BatchedServingLoop, ServingLoop, poisson_jobs
-    n_warm, n_timed, seed = 20, 12, 7
+    n_warm, seed = 20, 7
     rate = 200.0   # arrivals per second: above both loops' service rates, so both run saturated
 
     def jobs():
         return poisson_jobs(n_jobs, rate_per_s=rate, seed=seed, n_traj=n_timed, grids=grids, n_range=n_range, eps=eps,
                             adapt_warmup=n_warm, accept_target=target)
-    served = BatchedServingLoop(max_slots=8, max_points=int(n_range[1]), seed=seed).run(jobs())
+    served = BatchedServingLoop(max_slots=8, max_points=int(n_range[1]), seed=seed,
+                                grid_slots=grid_slots).run(jobs())
     plain = ServingLoop(max_slots=1).run(jobs())
     served["plain_one_at_a_time"] = {k: plain[k] for k in ("makespan_s", "grad_evals_per_s", "ess_per_s",
                                                            "trajectory_latency_ms", "job_latency_s",
                                                            "grad_evals_per_s_incl_warmup",
                                                            "seconds_per_effective_sample", "accept_rate",
-                                                           "errors")}
+                                                           "errors", "by_grid")}
     served["speedup_vs_plain_evals"] = served["grad_evals_per_s"] / plain["grad_evals_per_s"]
     if served.get("ess_per_s") and plain.get("ess_per_s"):
         served["speedup_vs_plain_ess"] = served["ess_per_s"] / plain["ess_per_s"]
     gs = "/".join(str(x) for x in grids)
+    pol = ", ".join(f"{k}^3 at most {v}" for k, v in sorted((grid_slots or {}).items()))
     served["workload"] = (f"{n_jobs} jobs, Poisson arrivals at {rate:.0f}/s, grids {gs}, {n_range[0]:.0e}-{n_range[1]:.0e} points; "
                           f"each job tunes its step by dual averaging ({n_warm} trajectories, target acceptance "
                           f"{target}) and then runs {n_timed} trajectories x {L} steps (the timed ones); served = "
-                          "continuous batching over slotted states (up to 8 jobs per grid in one launch), plain = "
-                          "the same jobs one at a time, each in its own one-chain state")
+                          "continuous batching over slotted states (up to 8 jobs per grid in one launch"
+                          + (f"; {pol}" if pol else "") + "), plain = the same jobs one at a time, each in its own "
+                          "one-chain state")
     return served
 
 
@@ -506,7 +550,7 @@ def main():
         torch.cuda.set_device(local)
         dist.init_process_group("nccl", init_method="env://")
     dev = torch.cuda.current_device()
-    spec = mock.PRESETS["grid128_30000pts"]
+    spec = mock.PRESETS[args.workload]
     cat = mock.make_catalog(spec)
     prob = Problem.from_mock(spec, cat, device=dev)
     state = State(prob, [cat["d_init"]], seed=1000 + rank, chain_ids=[rank])
@@ -597,7 +641,7 @@ def main():
         # one trajectory at a time, each timed on the device; after each, 64
         # fixed field entries and 64 fixed distances are read (outside the
         # timed intervals) for per-coordinate ESS
-        M = 400
+        M = 2000   # the 128^3 configuration's 2,000 trajectories
         rng = np.random.default_rng(123)
         n_field = spec.N ** 3
         wi = torch.tensor(rng.choice(n_field, 64, replace=False), device=dev)
@@ -700,10 +744,7 @@ def main():
     # CPU baseline: the oracle on a bounded sample, rank 0, N = 1 only
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        secs, nev = run_oracle_steps(6, args.eps)
-        cpu = {"value": nev / secs, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": f"{nev} oracle leapfrog steps (one gradient evaluation each) of this workload, "
-                         "numpy FP64, 1 thread"}
+        cpu = cpu_baseline_leg(args.eps)
 
     batched = None
     if not args.no_batched:
@@ -721,15 +762,19 @@ def main():
 
     serving = None
     if not args.no_serve and ws == 1:
-        serving = run_serving(args.eps, L, args.accept_target)
+        # the paper-scale serving mix; 256^3 chains fill the GPU alone, so their
+        # group batches at most two
+        serving = run_serving(args.eps, L, args.accept_target, grid_slots={256: 2})
         serving["grid_128_only"] = run_serving(args.eps, L, args.accept_target, grids=(128,), n_range=(3e3, 3e4),
-                                               n_jobs=48)
+                                               n_jobs=48, n_timed=12)
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": max_ms / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-                "config": {"workload": WORKLOAD, "grid": N, "box": spec.L, "points": n,
+                "config": {"workload": WORKLOAD if args.workload == "grid128_30000pts" else
+                           f"plain HMC: {N}^3 grid, L={spec.L:g} Mpc/h, {n} points, 1 chain, {L} leapfrog steps/trajectory",
+                           "grid": N, "box": spec.L, "points": n,
                            "leapfrog_steps": L, "eps": args.eps, "chains_per_gpu": 1,
                            "parallelism": f"replicas{ws}" if ws > 1 else "single",
                            "l2": "flushed (512 MiB write) before every timed step",

@@ -254,12 +254,19 @@ class BatchedServingLoop:
     trajectories (at most max_batch_traj) as the loaded job closest to an
     event (end of its warm-up or of its run) still needs, so the host's
     bookkeeping is paid once per call; the trajectory latency recorded is
-    the call's time divided by its trajectories."""
+    the call's time divided by its trajectories.
+
+    grid_slots maps a grid size N to the most jobs its group batches (the
+    rest wait for a slot): a grid whose single chain already fills the GPU
+    gains little from sharing launches and pays for it in trajectory
+    latency, so it can be held to one or two slots while small grids batch
+    up to max_slots."""
 
     def __init__(self, max_slots=8, max_points=100_000, reserve_bytes=2 << 30, device=0, use_graph=True,
                  keep_state=False, seed=0, backend_factory=None, prepare=None, free_bytes=None, prep_threads=2,
-                 max_batch_traj=4):
+                 max_batch_traj=4, grid_slots=None):
         self.max_batch_traj = max(1, int(max_batch_traj))
+        self.grid_slots = dict(grid_slots or {})
         self.max_slots = max_slots
         self.max_points = max_points
         self.reserve = reserve_bytes
@@ -368,7 +375,8 @@ class BatchedServingLoop:
         sp = job.spec
         per = slots_footprint_bytes(sp.N, 1, self.max_points, sp.precision)
         room = self.free_bytes() - self.reserve - (16 << 20)
-        n = min(self.max_slots, int(room // per)) if room > 0 else 0
+        cap = min(self.max_slots, int(self.grid_slots.get(sp.N, self.max_slots)))
+        n = min(cap, int(room // per)) if room > 0 else 0
         if n < 1:
             return None
         g = {"backend": self.backend_factory(job, n), "ready": collections.deque(), "slots": n, "stop": False}
@@ -450,6 +458,21 @@ class BatchedServingLoop:
             return job
 
 
+def latency_by_grid(jobs):
+    """Trajectory and job latency percentiles of the jobs of each grid size."""
+    out = {}
+    for N in sorted({j.spec.N for j in jobs}):
+        js = [j for j in jobs if j.spec.N == N and not j.error]
+        lat = np.array([x for j in js for x in j.traj_latency])
+        jl = np.array([j.finished - j.arrival for j in js])
+        out[str(N)] = {"jobs": len(js),
+                       "trajectory_latency_ms": {"p50": float(np.percentile(lat, 50) * 1e3) if lat.size else None,
+                                                 "p99": float(np.percentile(lat, 99) * 1e3) if lat.size else None},
+                       "job_latency_s": {"p50": float(np.percentile(jl, 50)) if jl.size else None,
+                                         "p99": float(np.percentile(jl, 99)) if jl.size else None}}
+    return out
+
+
 def summarize(jobs, makespan):
     lat = np.array([x for j in jobs for x in j.traj_latency]) if jobs else np.zeros(0)
     job_lat = np.array([j.finished - j.arrival for j in jobs])
@@ -473,6 +496,7 @@ def summarize(jobs, makespan):
         "job_latency_s": {"p50": float(np.percentile(job_lat, 50)) if job_lat.size else None,
                           "p99": float(np.percentile(job_lat, 99)) if job_lat.size else None},
         "accept_rate": float(acc.mean()) if acc.size else None,
+        "by_grid": latency_by_grid(jobs),
     }
 
 

@@ -230,3 +230,18 @@ def test_batched_device_failure_fails_that_groups_jobs_only():
     assert errs == {0, 1}
     assert all("injected device failure" in jobs[k].error for k in (0, 1))
     assert len(jobs[2].traj_latency) == 3 and all(len(jobs[k].traj_latency) == 4 for k in (3, 4))
+
+
+def test_batched_grid_slot_policy_and_latency_by_grid():
+    # a grid held to one slot serves its jobs one after another while another
+    # grid batches; the stats report latency per grid
+    loop = _bloop(max_slots=4, grid_slots={128: 1})
+    jobs = [_job(k, N=128 if k % 2 else 64, arrival=0.0, n_traj=5) for k in range(6)]
+    stats = loop.run(jobs)
+    assert stats["jobs"] == 6 and not stats["errors"]
+    by = {be.key[0]: be for be in FakeSlots.instances}
+    assert by[128].n_slots == 1 and max(len(r) for r in by[128].runs) == 1
+    assert by[64].n_slots == 4 and max(len(r) for r in by[64].runs) == 3
+    assert set(stats["by_grid"]) == {"64", "128"}
+    assert stats["by_grid"]["128"]["jobs"] == 3
+    assert stats["by_grid"]["64"]["trajectory_latency_ms"]["p50"] > 0
