@@ -497,7 +497,8 @@ def run_batched_same(prob, d_init, eps, L, use_graph, n_chains=16, K=20, M=60):
                         "60-trajectory burn-in"}
 
 
-def run_serving(eps, L, target, grids=(64, 128, 256), n_range=(1e3, 1e5), n_jobs=60, n_timed=50, grid_slots=None):
+def run_serving(eps, L, target, grids=(64, 128, 256), n_range=(1e3, 1e5), n_jobs=60, n_timed=50, grid_slots=None,
+                grid_priority=None):
     """Poisson stream of reconstruction jobs (64^3 / 128^3 at 500 Mpc/h,
     256^3 at 1000 Mpc/h), all arriving within a fraction of a second so that
     the GPU is saturated.  Served by continuous batching (one slotted state
@@ -514,7 +515,7 @@ def run_serving(eps, L, target, grids=(64, 128, 256), n_range=(1e3, 1e5), n_jobs
         return poisson_jobs(n_jobs, rate_per_s=rate, seed=seed, n_traj=n_timed, grids=grids, n_range=n_range, eps=eps,
                             adapt_warmup=n_warm, accept_target=target)
     served = BatchedServingLoop(max_slots=8, max_points=int(n_range[1]), seed=seed,
-                                grid_slots=grid_slots).run(jobs())
+                                grid_slots=grid_slots, grid_priority=grid_priority).run(jobs())
     plain = ServingLoop(max_slots=1).run(jobs())
     served["plain_one_at_a_time"] = {k: plain[k] for k in ("makespan_s", "grad_evals_per_s", "ess_per_s",
                                                            "trajectory_latency_ms", "job_latency_s",
@@ -525,7 +526,8 @@ def run_serving(eps, L, target, grids=(64, 128, 256), n_range=(1e3, 1e5), n_jobs
     if served.get("ess_per_s") and plain.get("ess_per_s"):
         served["speedup_vs_plain_ess"] = served["ess_per_s"] / plain["ess_per_s"]
     gs = "/".join(str(x) for x in grids)
-    pol = ", ".join(f"{k}^3 at most {v}" for k, v in sorted((grid_slots or {}).items()))
+    pol = ", ".join([f"{k}^3 at most {v}" for k, v in sorted((grid_slots or {}).items())] +
+                    [f"{k}^3 stream priority {v}" for k, v in sorted((grid_priority or {}).items())])
     served["workload"] = (f"{n_jobs} jobs, Poisson arrivals at {rate:.0f}/s, grids {gs}, {n_range[0]:.0e}-{n_range[1]:.0e} points; "
                           f"each job tunes its step by dual averaging ({n_warm} trajectories, target acceptance "
                           f"{target}) and then runs {n_timed} trajectories x {L} steps (the timed ones); served = "
@@ -763,8 +765,9 @@ def main():
     serving = None
     if not args.no_serve and ws == 1:
         # the paper-scale serving mix; 256^3 chains fill the GPU alone, so their
-        # group batches at most two
-        serving = run_serving(args.eps, L, args.accept_target, grid_slots={256: 2})
+        # group batches at most two, and the smaller grids' groups run on
+        # higher-priority streams
+        serving = run_serving(args.eps, L, args.accept_target, grid_slots={256: 2}, grid_priority={64: -2, 128: -1})
         serving["grid_128_only"] = run_serving(args.eps, L, args.accept_target, grids=(128,), n_range=(3e3, 3e4),
                                                n_jobs=48, n_timed=12)
 

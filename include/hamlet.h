@@ -386,6 +386,15 @@ int hm_dz_prior_table(double omega_m, int64_t n, const double* cz_host, double b
 int hm_problem_prior_table(const hm_problem* p, int32_t max_bins, double* logdens_out, int32_t* nbins_out,
                            double* d0_out, double* bin_out);
 
+/* Number of bounded device waits that gave up on `device` since the library
+ * loaded (the x pass at FP32 N = 256 waits for tensor copies of its next
+ * tile; a wait that never completes is abandoned after a fixed number
+ * of polls, the CTA returns and the count grows).  0 in correct operation; a
+ * positive count means the results since then are not to be trusted.
+ * reset != 0 clears it.  Synchronises the device.  Not from the paper: a
+ * fault check of this implementation. */
+int hm_device_wait_timeouts(int32_t device, int32_t reset, int32_t* count_out);
+
 /* Raw Philox-4x32-10 blocks for counters (q, c1, c2, c3), q = 0..n-1, key
  * seed: out_dev receives 4 n uint32 words. */
 int hm_philox(uint64_t seed, int64_t n, uint32_t c1, uint32_t c2, uint32_t c3, uint32_t* out_dev,

@@ -64,6 +64,7 @@ SIGNATURES = [
     ("hm_logpost_grad", ct.c_int, [_P, _P, _P, _P, _P, _P, _P]),
     ("hm_logpost_grad_noalloc", ct.c_int, [_P, _P, _P, _P, _P, _P, _P]),
     ("hm_problem_last_status", ct.c_int, [_P, _P, ct.POINTER(ct.c_int32)]),
+    ("hm_device_wait_timeouts", ct.c_int, [ct.c_int32, ct.c_int32, ct.POINTER(ct.c_int32)]),
     ("hm_problem_prior_table", ct.c_int, [_P, ct.c_int32, c_double_p, ct.POINTER(ct.c_int32), c_double_p,
                                           c_double_p]),
     ("hm_velocity_field", ct.c_int, [_P, _P, _P, _P]),

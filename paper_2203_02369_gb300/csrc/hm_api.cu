@@ -919,6 +919,15 @@ int hm_cells(hm_problem* p, const double* d_dev, int32_t* cell_dev, int32_t* per
   return HM_OK;
 }
 
+int hm_device_wait_timeouts(int32_t device, int32_t reset, int32_t* count_out) {
+  if (!count_out) return fail(HM_EINVAL, "null argument");
+  HM_CUDA(cudaSetDevice(device));
+  const int v = fft_tma_wait_timeouts(reset != 0);
+  if (v < 0) return fail(HM_ECUDA, "reading the wait counter failed");
+  *count_out = v;
+  return HM_OK;
+}
+
 int hm_dz_prior_table(double omega_m, int64_t n, const double* cz_host, double bin_width, double pad,
                       int32_t max_bins, double* logdens_out, int32_t* nbins_out) {
   if (n <= 0 || !cz_host || !nbins_out) return fail(HM_EINVAL, "need n > 0 redshifts and nbins_out");

@@ -189,6 +189,10 @@ cudaError_t launch_pencil(int prec, int N, int mode, const void* in, long long i
                           long long out_stride, int count, const void* tw, const void* amp,
                           cudaStream_t st, const int* plane_off = nullptr);
 bool fft_supported(int prec, int N);
+// Bounded waits on tensor copies that gave up in the TMA-staged pencil pass
+// (FP32, N = 256) on the current device since load (0 in correct
+// operation); reset clears it.
+int fft_tma_wait_timeouts(bool reset);
 // N = 256 plane passes (FP32): a z pass over row slabs and a y pass over
 // column tiles (hm_fft_256.cu).  pts == nullptr loads real grids, else
 // scatters the bucketed residuals; mode is C2R_STORE (0), C2R_EPI (1) or

@@ -194,9 +194,11 @@ def group_key(job):
 class SlotsBackend:
     """One slotted state on its own CUDA stream (the device side of a group)."""
 
-    def __init__(self, job, n_slots, max_points, seed, device=0, use_graph=True):
+    def __init__(self, job, n_slots, max_points, seed, device=0, use_graph=True, priority=0):
         torch.cuda.set_device(device)
-        self.stream = torch.cuda.Stream(device=device)
+        # a lower number is a higher priority: the device schedules the CTAs
+        # of this group's pending kernels ahead of lower-priority streams
+        self.stream = torch.cuda.Stream(device=device, priority=int(priority))
         sp = job.spec
         self.n_leapfrog = job.n_leapfrog
         self.use_graph = use_graph
@@ -260,13 +262,16 @@ class BatchedServingLoop:
     rest wait for a slot): a grid whose single chain already fills the GPU
     gains little from sharing launches and pays for it in trajectory
     latency, so it can be held to one or two slots while small grids batch
-    up to max_slots."""
+    up to max_slots.  grid_priority maps N to its group's CUDA stream
+    priority (lower is higher): short small-grid trajectories need not wait
+    behind the CTAs of a large grid's kernels."""
 
     def __init__(self, max_slots=8, max_points=100_000, reserve_bytes=2 << 30, device=0, use_graph=True,
                  keep_state=False, seed=0, backend_factory=None, prepare=None, free_bytes=None, prep_threads=2,
-                 max_batch_traj=4, grid_slots=None):
+                 max_batch_traj=4, grid_slots=None, grid_priority=None):
         self.max_batch_traj = max(1, int(max_batch_traj))
         self.grid_slots = dict(grid_slots or {})
+        self.grid_priority = dict(grid_priority or {})
         self.max_slots = max_slots
         self.max_points = max_points
         self.reserve = reserve_bytes
@@ -274,7 +279,8 @@ class BatchedServingLoop:
         self.keep_state = keep_state
         self.seed = seed
         self.backend_factory = backend_factory or (
-            lambda job, n: SlotsBackend(job, n, max_points, seed, device=device, use_graph=use_graph))
+            lambda job, n: SlotsBackend(job, n, max_points, seed, device=device, use_graph=use_graph,
+                                        priority=self.grid_priority.get(job.spec.N, 0)))
         self.prepare = prepare or (lambda job: _prepare_job(job, device))
         self.free_bytes = free_bytes or (lambda: torch.cuda.mem_get_info(self.device)[0])
         self.prep_threads = prep_threads

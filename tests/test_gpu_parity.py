@@ -484,3 +484,19 @@ def test_logpost_grad_256_cluster_planes(H):
     assert abs(tr[0, 0]["H_new"] - recs[0]["H_new"]) <= 1e-5 * abs(recs[0]["H_new"])
     tr = st.run_chain(2, 5, 0.01, use_graph=True)
     assert np.all(np.isfinite(tr[:, 0]["H_new"]))
+
+
+def test_no_bounded_device_wait_gave_up(H):
+    """The x pass at FP32 N = 256 waits for tensor copies with a bounded
+    poll; after the transforms, gradients and chains above (and one more
+    128^3 and 256^3 velocity field here) none may have given up."""
+    import ctypes as ct
+    for N, L in ((128, 500.0), (256, 1000.0)):
+        p = H.Problem(N, L, precision="fp32")
+        p.set_catalog(np.zeros((0, 3)), np.zeros(0), np.zeros(0), np.zeros(0))
+        v = p.velocity_field(torch.tensor(mock.white_field(N, 3), dtype=torch.float32, device="cuda"))
+        assert torch.isfinite(v).all()
+    torch.cuda.synchronize()
+    n = ct.c_int32(-1)
+    assert p.lib.hm_device_wait_timeouts(0, 0, ct.byref(n)) == 0
+    assert n.value == 0
