@@ -55,6 +55,7 @@ def parse():
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--batched-only", action="store_true", help="run only the 32-chain batched measurement")
     ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--no-256", action="store_true", help="skip the 256^3 one-chain measurement")
     ap.add_argument("--no-fft-ref", action="store_true", help="skip the cuFFT reference timing")
     ap.add_argument("--accept-target", type=float, default=0.70,
                     help="acceptance the batched and served chains' step sizes are tuned to (dual averaging)")
@@ -421,6 +422,54 @@ def run_batched(args, eps, L, use_graph):
     return out
 
 
+def run_grid256(L, eps=0.01, K=5):
+    """One chain at 256^3 (box 1000 Mpc/h, 1e5 points, r^2 to 160 Mpc/h, the
+    serving mix's large grid; its working set is far beyond L2): ms per
+    gradient evaluation over K trajectories (CUDA events), and per kernel
+    kind the mean launch time (profiled pass) and its algorithmic GB/s."""
+    import torch
+    from paper_2203_02369_gb300.hamlet import Problem, State
+    spec = mock.MockSpec(N=256, L=1000.0, n_points=100000, r_max=160.0, mask_deg=10.0, sigma_mu=(0.2, 0.45),
+                         sigma_nl=250.0, seed=1007)
+    cat = mock.make_catalog(spec)
+    prob = Problem.from_mock(spec, cat)
+    st = State(prob, [cat["d_init"]], seed=5)
+    st.run_chain(3, L, eps, use_graph=True, trace=False)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    tr = st.run_chain(K, L, eps, use_graph=True, trace=True)
+    b.record()
+    torch.cuda.synchronize()
+    ms_eval = a.elapsed_time(b) / (K * L)
+    st.profile(True)
+    st.run_chain(1, L, eps, use_graph=True, trace=False)
+    st.profile(True)
+    for _ in range(3):
+        st.run_chain(1, L, eps, use_graph=True, trace=False)
+        st.profile_collect()
+    prof = st.profile_read()
+    st.profile(False)
+    fo = occupied_plane_fraction(prob, st.get(0)["d"])
+    ab = algorithmic_bytes(256, spec.n_points, fo=fo)
+    peak = measured_peaks()[0].get("hbm_gbs", 6800.0)
+    kern = {}
+    for k, (ms, n) in prof.items():
+        if not n:
+            continue
+        us = 1e3 * ms / n
+        gbs = ab.get(k, 0) / (us * 1e-6) / 1e9 if ab.get(k) else None
+        kern[k] = {"us_per_launch": us, "gbs_algorithmic": gbs, "frac": gbs / peak if gbs else None}
+    st.close()
+    prob.close()
+    return {"workload": "256^3 grid, L=1000 Mpc/h, 1e5 points (r^2 to 160 Mpc/h), 1 chain, 20 leapfrog steps, eps 0.01",
+            "ms_per_eval": ms_eval, "grad_evals_per_s": 1e3 / ms_eval, "accept_rate": float(tr["accept"].mean()),
+            "occupied_plane_fraction": fo, "kernels": kern,
+            "note": "plane kinds are two kernels at 256^3 (z pass over row slabs, y pass over column tiles; the "
+                    "gradient epilogue adds the y pass of the drifted field); algorithmic bytes as at 128^3, so "
+                    "the extra read and write of the spectra by the two-pass form count as overhead"}
+
+
 def run_fft_reference(prob, dev, reps=30):
     """The library's 3D r2c/c2r transforms (plane pass + x pencil) against
     cuFFT (torch.fft, unnormalised both ways) on the same 128^3 FP32 grids,
@@ -762,6 +811,10 @@ def main():
             same["plain_accept_rate"] = ess_info["accept_rate"]
         batched["same_workload"] = same
 
+    grid256 = None
+    if not args.no_256 and ws == 1:
+        grid256 = run_grid256(L)
+
     serving = None
     if not args.no_serve and ws == 1:
         # the paper-scale serving mix; 256^3 chains fill the GPU alone, so their
@@ -786,7 +839,8 @@ def main():
                 "gpu_launches": int(sum(v[1] * KERNELS_PER_PAIR.get(k, 1) for k, v in prof.items())),
                 "clocks": clk, "roofline": roofline, "model_roofline": model_roof, "kernels": kernels,
                 "ess": ess_info,
-                "e2e": e2e, "cpu_baseline": cpu, "batched": batched, "serving": serving, "fft_reference": fft_ref,
+                "e2e": e2e, "cpu_baseline": cpu, "batched": batched, "grid_256": grid256, "serving": serving,
+                "fft_reference": fft_ref,
                 "wall_s_timed": t_wall}
         print(json.dumps(line), flush=True)
     if ws > 1:

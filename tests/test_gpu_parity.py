@@ -461,9 +461,10 @@ def test_sampled_sigma_nl_gradient_and_leapfrog_vs_oracle(H):
     assert np.all(np.isfinite(tr[:, 0]["H_new"]))
 
 
-def test_logpost_grad_256_cluster_planes(H):
-    """256^3 (box 1000 Mpc/h), 2e4 points: the 8-CTA cluster plane passes,
-    the posterior gradient and one trajectory against the oracle's."""
+def test_logpost_grad_256_two_pass_planes(H):
+    """256^3 (box 1000 Mpc/h), 2e4 points: the z-pass / y-pass plane passes
+    and the TMA-staged x pass, the posterior gradient, the velocity field and
+    one trajectory against the oracle's."""
     spec = mock.MockSpec(N=256, L=1000.0, n_points=20000, r_max=300.0, mask_deg=10.0, sigma_mu=(0.2, 0.45),
                          sigma_nl=250.0, seed=81)
     cat = mock.make_catalog(spec)
