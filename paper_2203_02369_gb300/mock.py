@@ -48,8 +48,8 @@ class MockSpec:
     prior_bin: float = 5.0   # bin width (Mpc/h) of the distance prior's redshift-distance histogram
 
 
-# Presets with the sizes of the paper's mocks (PAPER "Mock Catalogue
-# construction") as fixed for this build's workloads.
+# Presets with the sizes of the paper's mocks (section "Mock Catalogue
+# construction"), the rest fixed for these workloads.
 PRESETS = {
     "grid16_500pts_fp64": MockSpec(N=16, L=200.0, n_points=500, r_max=80.0, mask_deg=0.0,
                         sigma_mu=(0.2, 0.2), sigma_nl=150.0, seed=0, precision="fp64"),
