@@ -281,7 +281,7 @@ struct hm_problem {
   // catalogue
   long long n = 0;
   DevBuf rx, ry, rz, mu, smu, zobs, scz;
-  DevBuf xr;   // x_ref = 10^((mu - 25)/5): the luminosity distance (Mpc) the observed modulus states
+  DevBuf xr;   // XRef per point: the FP32 path's constants of its distance terms
   // standalone workspace (one chain)
   DevBuf S1, S2, hist, prior_part, pts_part, kin_part, pp, cs, chain_id;
   PtWork pw;
@@ -357,7 +357,7 @@ static PointArrays point_arrays(hm_state* s) {
   pa.ry = s->ry.as<double>();
   pa.rz = s->rz.as<double>();
   pa.mu = s->mu.as<double>();
-  pa.xr = s->xr.as<double>();
+  pa.xr = s->xr.as<XRef>();
   pa.ismu2 = s->smu.as<double>();
   pa.zobs = s->zobs.as<double>();
   pa.scz = s->scz.as<double>();
@@ -373,6 +373,12 @@ static PointParams point_params(const hm_problem* p, long long off) {
   for (int j = 0; j < 3; ++j) P.obs[j] = p->obs[j];
   P.delta = p->delta;
   P.inv_delta = 1.0 / p->delta;
+  for (int j = 0; j < 3; ++j) {
+    P.obs_hi[j] = (float)P.obs[j];
+    P.obs_lo[j] = (float)(P.obs[j] - (double)P.obs_hi[j]);
+  }
+  P.inv_delta_hi = (float)P.inv_delta;
+  P.inv_delta_lo = (float)(P.inv_delta - (double)P.inv_delta_hi);
   P.omega_m = p->desc.omega_m;
   P.h = p->desc.h;
   P.sigma_nl2 = p->desc.sigma_nl * p->desc.sigma_nl;
@@ -382,6 +388,9 @@ static PointParams point_params(const hm_problem* p, long long off) {
   P.k3 = 3.0 * p->desc.omega_m * kH0 / kC;
   P.c23 = 2.0 / (3.0 * p->desc.omega_m);
   P.inv_h = 1.0 / p->desc.h;
+  P.c23k3_f = (float)(P.c23 * P.k3);
+  P.inv_h_f = (float)P.inv_h;
+  P.k3_f = (float)P.k3;
   P.N = p->N;
   P.ksplit = plane_split(p->N);
   P.rq = p->N / P.ksplit;
@@ -671,6 +680,40 @@ int hm_problem_get_info(const hm_problem* p, hm_problem_info* out) {
   return HM_OK;
 }
 
+// The FP32 path's per-point constants (see XRef), in FP64 on the host.
+static XRef xref_of(double omega_m, double h, double mu, double z) {
+  const double k3 = 3.0 * omega_m * kH0 / kC, c23 = 2.0 / (3.0 * omega_m), dmax = 0.999 / k3;
+  auto s_of = [&](double d) { return std::sqrt(1.0 - k3 * d); };
+  auto zbar = [&](double d) { return c23 * k3 * d / (1.0 + s_of(d)); };   // c23 (1 - s) without cancellation
+  auto x_of = [&](double d) { return d * (1.0 + zbar(d)) / h; };
+  auto split = [](double v, float& hi, float& lo) {
+    hi = (float)v;
+    lo = (float)(v - (double)hi);
+  };
+  XRef r{};
+  // d_z in closed form: s(d_z) = 1 - z/c23 (clamped where no distance has this zbar)
+  double dz = (1.0 - (1.0 - z / c23) * (1.0 - z / c23)) / k3;
+  if (!(dz < dmax)) dz = dmax;
+  split(dz, r.dz_hi, r.dz_lo);
+  r.s_z = (float)s_of(dz);
+  r.e_z = (float)(z - zbar(dz));
+  // d_ref by Newton on x(d) = x_ref (x increases with d), clamped to (0, dmax]
+  const double xref = std::pow(10.0, (mu - 25.0) / 5.0);
+  double dr = std::min(std::max(h * xref, 1e-6), dmax);
+  for (int it = 0; it < 60; ++it) {
+    const double sd = s_of(dr);
+    const double g = x_of(dr) - xref;
+    const double gp = (1.0 + zbar(dr) + dr * 0.5 * c23 * k3 / sd) / h;
+    const double dn = std::min(std::max(dr - g / gp, 1e-6), dmax);
+    if (dn == dr) break;
+    dr = dn;
+  }
+  split(dr, r.dr_hi, r.dr_lo);
+  r.s_ref = (float)s_of(dr);
+  r.e_ref = (float)(x_of(dr) - xref);
+  return r;
+}
+
 static int upload(DevBuf& b, const double* src, long long n) {
   HM_TRY(b.alloc(sizeof(double) * (size_t)std::max<long long>(n, 1)));
   if (n > 0) HM_CUDA(cudaMemcpy(b.p, src, sizeof(double) * n, cudaMemcpyHostToDevice));
@@ -705,9 +748,10 @@ int hm_set_catalog(hm_problem* p, int64_t n, const double* rhat, const double* m
   HM_TRY(upload(p->ry, ry.data(), n));
   HM_TRY(upload(p->rz, rz.data(), n));
   HM_TRY(upload(p->mu, mu, n));
-  std::vector<double> xr(n);
-  for (long long i = 0; i < n; ++i) xr[i] = std::pow(10.0, (mu[i] - 25.0) / 5.0);
-  HM_TRY(upload(p->xr, xr.data(), n));
+  std::vector<XRef> xr((size_t)std::max<long long>(n, 1));
+  for (long long i = 0; i < n; ++i) xr[i] = xref_of(p->desc.omega_m, p->desc.h, mu[i], z[i]);
+  static_assert(sizeof(XRef) == 4 * sizeof(double), "XRef is uploaded as four doubles");
+  HM_TRY(upload(p->xr, reinterpret_cast<const double*>(xr.data()), 4 * n));
   std::vector<double> ismu2(n);
   for (long long i = 0; i < n; ++i) ismu2[i] = 1.0 / (smu[i] * smu[i]);
   HM_TRY(upload(p->smu, ismu2.data(), n));   // the device keeps 1/sigma_mu^2
@@ -808,7 +852,7 @@ int hm_logpost_grad(hm_problem* p, const void* w_dev, const double* d_dev, doubl
   pa.ry = p->ry.as<double>();
   pa.rz = p->rz.as<double>();
   pa.mu = p->mu.as<double>();
-  pa.xr = p->xr.as<double>();
+  pa.xr = p->xr.as<XRef>();
   pa.ismu2 = p->smu.as<double>();
   pa.zobs = p->zobs.as<double>();
   pa.scz = p->scz.as<double>();
@@ -1049,9 +1093,10 @@ int hm_state_create_batch(hm_problem* const* problems, int32_t n_problems, int32
   HM_CUDA(cudaMemset(s->w.p, 0, rs * C * s->n3));
   HM_CUDA(cudaMemset(s->pw.p, 0, rs * C * s->n3));
   const size_t nt = (size_t)std::max<long long>(tot, 1);
-  DevBuf* dbl[] = {&s->rx, &s->ry, &s->rz, &s->mu, &s->xr, &s->smu, &s->zobs,
+  DevBuf* dbl[] = {&s->rx, &s->ry, &s->rz, &s->mu, &s->smu, &s->zobs,
                    &s->scz, &s->d, &s->pd, &s->gd, &s->d0, &s->gd0};
   for (DevBuf* b : dbl) HM_TRY(b->alloc(8 * nt));
+  HM_TRY(s->xr.alloc(sizeof(XRef) * nt));
   HM_CUDA(cudaMemset(s->pd.p, 0, 8 * nt));
   HM_TRY(s->work.alloc(s->prec, n_chains, s->N, tot));
   for (int c = 0; c < n_chains; ++c) {
@@ -1063,7 +1108,7 @@ int hm_state_create_batch(hm_problem* const* problems, int32_t n_problems, int32
     HM_CUDA(cudaMemcpy((char*)s->ry.p + o, p->ry.p, b, cudaMemcpyDeviceToDevice));
     HM_CUDA(cudaMemcpy((char*)s->rz.p + o, p->rz.p, b, cudaMemcpyDeviceToDevice));
     HM_CUDA(cudaMemcpy((char*)s->mu.p + o, p->mu.p, b, cudaMemcpyDeviceToDevice));
-    HM_CUDA(cudaMemcpy((char*)s->xr.p + o, p->xr.p, b, cudaMemcpyDeviceToDevice));
+    HM_CUDA(cudaMemcpy((char*)s->xr.p + 4 * o, p->xr.p, 4 * b, cudaMemcpyDeviceToDevice));
     HM_CUDA(cudaMemcpy((char*)s->smu.p + o, p->smu.p, b, cudaMemcpyDeviceToDevice));
     HM_CUDA(cudaMemcpy((char*)s->zobs.p + o, p->zobs.p, b, cudaMemcpyDeviceToDevice));
     HM_CUDA(cudaMemcpy((char*)s->scz.p + o, p->scz.p, b, cudaMemcpyDeviceToDevice));
@@ -1494,9 +1539,10 @@ int hm_slots_create(hm_problem* templ, int32_t n_slots, int64_t max_points, uint
   HM_TRY(s->S1.alloc(2 * rs * 3 * C * s->nspec));
   HM_TRY(s->S2.alloc(2 * rs * 3 * C * s->nspec));
   const size_t nt = (size_t)std::max<long long>(tot, 1);
-  DevBuf* dbl[] = {&s->rx, &s->ry, &s->rz, &s->mu, &s->xr, &s->smu, &s->zobs,
+  DevBuf* dbl[] = {&s->rx, &s->ry, &s->rz, &s->mu, &s->smu, &s->zobs,
                    &s->scz, &s->d, &s->pd, &s->gd, &s->d0, &s->gd0};
   for (DevBuf* b : dbl) HM_TRY(b->alloc(8 * nt));
+  HM_TRY(s->xr.alloc(sizeof(XRef) * nt));
   HM_TRY(s->work.alloc(s->prec, n_slots, s->N, tot));
   s->pp_host.assign(C, PointParams{});
   s->chain_prob.assign(C, nullptr);
@@ -1556,8 +1602,11 @@ int hm_slots_load(hm_state* s, hm_problem* job, int32_t chain_id, const double* 
     const size_t b = 8 * (size_t)n, o = 8 * (size_t)off;
     const DevBuf* src[] = {&job->rx, &job->ry, &job->rz, &job->mu, &job->xr, &job->smu, &job->zobs, &job->scz};
     DevBuf* dst[] = {&s->rx, &s->ry, &s->rz, &s->mu, &s->xr, &s->smu, &s->zobs, &s->scz};
-    for (int k = 0; k < 8; ++k)
-      HM_CUDA(cudaMemcpyAsync(static_cast<char*>(dst[k]->p) + o, src[k]->p, b, cudaMemcpyDeviceToDevice, st));
+    for (int k = 0; k < 8; ++k) {
+      const size_t m = dst[k] == &s->xr ? sizeof(XRef) / 8 : 1;   // xr: 32 B per point
+      HM_CUDA(cudaMemcpyAsync(static_cast<char*>(dst[k]->p) + m * o, src[k]->p, m * b, cudaMemcpyDeviceToDevice,
+                              st));
+    }
     // pageable host sources: each copy has consumed its source when it returns
     HM_CUDA(cudaMemcpyAsync(static_cast<char*>(s->d.p) + o, d_init_host, b, cudaMemcpyHostToDevice, st));
     HM_CUDA(cudaMemsetAsync(static_cast<char*>(s->pd.p) + o, 0, b, st));
@@ -2006,7 +2055,7 @@ extern "C" int hm_logpost_grad_noalloc(hm_problem* p, const void* w_dev, const d
   pa.ry = p->ry.as<double>();
   pa.rz = p->rz.as<double>();
   pa.mu = p->mu.as<double>();
-  pa.xr = p->xr.as<double>();
+  pa.xr = p->xr.as<XRef>();
   pa.ismu2 = p->smu.as<double>();
   pa.zobs = p->zobs.as<double>();
   pa.scz = p->scz.as<double>();

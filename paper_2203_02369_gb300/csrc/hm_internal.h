@@ -54,6 +54,8 @@ struct PointParams {
   double obs[3];
   double delta;          // grid spacing L/N
   double inv_delta;      // 1/delta (rounded once, on the host)
+  float obs_hi[3], obs_lo[3];          // obs and inv_delta as float pairs hi + lo
+  float inv_delta_hi, inv_delta_lo;    // (hi = the value rounded to float)
   double omega_m, h;
   double sigma_nl2;      // sigma_NL^2
   double ik2_nl, logk2_nl;  // 1/sigma_NL^2 and ln sigma_NL^2 (kappa^2 of a point with sigma_cz = 0)
@@ -61,6 +63,7 @@ struct PointParams {
   double k3;             // 3 Omega_m H0 / c (zbar = c23 (1 - sqrt(1 - k3 d)))
   double c23;            // 2 / (3 Omega_m)
   double inv_h;          // 1 / h (luminosity distance in Mpc: d (1 + zbar) / h)
+  float c23k3_f, inv_h_f, k3_f;   // c23 k3, 1/h and k3 rounded to float
   int N;
   int prior_kind;
   int prior_nbins;
@@ -118,6 +121,20 @@ struct FieldEpi {
 // One point as the plane passes see it, stored in x-plane bucket order:
 // fractional offsets in its cell, direction, (iy*N + iz) of the lower
 // corner, and the residual r = dPsi/du once the likelihood has run.
+// Per-point constants of the FP32 path's distance-only terms, formed in FP64
+// on the host when the catalogue is set.  With s(d) = sqrt(1 - k3 d) and
+// zbar(d) = c23 (1 - s(d)):
+//   d_z   solves zbar(d_z) = z (the observed redshift),
+//   d_ref solves d_ref (1 + zbar(d_ref))/h = x_ref = 10^((mu - 25)/5),
+// so that z - zbar(d) and x(d) - x_ref, the two differences that cancel,
+// follow from d - d_z and d - d_ref (float pairs) times smooth factors.
+struct XRef {
+  float dz_hi, dz_lo;    // d_z as hi + lo
+  float dr_hi, dr_lo;    // d_ref as hi + lo
+  float s_z, s_ref;      // s(d_z), s(d_ref)
+  float e_z, e_ref;      // residuals z - zbar(d_z) and x(d_ref) - x_ref
+};
+
 template <typename T> struct PtRec {
   T fx, fy, fz;
   T rx, ry, rz;
@@ -131,7 +148,7 @@ struct PointArrays {
   const double* ry;
   const double* rz;
   const double* mu;
-  const double* xr;      // 10^((mu - 25)/5): the luminosity distance (Mpc) of the observed modulus
+  const struct XRef* xr; // per-point constants of the FP32 path's distance terms
   const double* ismu2;   // 1 / sigma_mu^2 per point
   const double* zobs;
   const double* scz;

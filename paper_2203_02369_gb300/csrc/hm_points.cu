@@ -19,6 +19,23 @@ __device__ __forceinline__ CellPos cell_of(const PointParams& P, double d, doubl
   return c;
 }
 
+// The FP32 path's cells: the double-float screen (same indices, FP32
+// offsets), FP64 for a point the screen cannot decide.
+__device__ __forceinline__ CellPos cell_of_f32(const PointParams& P, double d, double rx, double ry, double rz) {
+  CellPos c;
+  float dh, dl, fx, fy, fz;
+  const float ih = P.inv_delta_hi, il = P.inv_delta_lo;
+  if (split_df(d, dh, dl) && cell_axis_df(P.obs_hi[0], P.obs_lo[0], dh, dl, rx, ih, il, P.N, c.ix, fx) &&
+      cell_axis_df(P.obs_hi[1], P.obs_lo[1], dh, dl, ry, ih, il, P.N, c.iy, fy) &&
+      cell_axis_df(P.obs_hi[2], P.obs_lo[2], dh, dl, rz, ih, il, P.N, c.iz, fz)) {
+    c.fx = fx;
+    c.fy = fy;
+    c.fz = fz;
+    return c;
+  }
+  return cell_of(P, d, rx, ry, rz);
+}
+
 // ln pi_D(d) and its derivative; returns false outside the support.  The
 // table (eq. D's histogram) gives ln pi at the bin centres d0 + (b + 1/2) bin,
 // interpolated linearly in between and flat in the outer half bins, so the
@@ -81,20 +98,6 @@ __device__ __forceinline__ bool log_prior_f32(const PointParams& P, double d, fl
   return true;
 }
 
-__device__ __forceinline__ double block_sum(double v, double* red) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  __syncthreads();
-  if (lane == 0) red[wid] = v;
-  __syncthreads();
-  double s = 0.0;
-  if (threadIdx.x == 0) {
-    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) s += red[i];
-  }
-  return s;
-}
-
 // ---------------------------------------------------------------------------
 // Bucketing by the x index of the lower CIC corner: counts (and the rank of
 // each point inside its bucket, in atomic order) ...
@@ -118,9 +121,6 @@ k_points_prep(const PointParams* __restrict__ pp, PointArrays pa) {
 //   lk[0] = A   = (mu_i - mu(d))^2/(2 s_mu^2) + ln kappa - ln pi_D(d)  (+inf outside)
 //   lk[1] = A'  = dA/dd
 //   lk[2] = v_obs(d), lk[3] = v_obs'(d), lk[4] = 1/kappa^2, lk[5] = (kappa^2)'
-// F32LAYOUT writes the FP32 path's layout (A as a double, the rest as floats,
-// see place_terms_fp32) from the same FP64 arithmetic.
-template <bool F32LAYOUT>
 __device__ __forceinline__ void place_terms_fp64(const PointParams& P, PointArrays& pa, ChainScal* cs, int c,
                                                  long long i, double d) {
   const double om = P.omega_m;
@@ -130,12 +130,7 @@ __device__ __forceinline__ void place_terms_fp64(const PointParams& P, PointArra
   const long long nt = pa.ntot;
   if (!ok) {
     pa.lk[i] = __longlong_as_double(0x7ff0000000000000LL);  // +inf
-    if constexpr (F32LAYOUT) {
-      float* f = reinterpret_cast<float*>(pa.lk + nt);
-      for (int k = 0; k < 5; ++k) f[k * nt + i] = 0.0f;
-    } else {
-      for (int k = 1; k < 6; ++k) pa.lk[k * nt + i] = 0.0;
-    }
+    for (int k = 1; k < 6; ++k) pa.lk[k * nt + i] = 0.0;
     atomicOr(&cs[c].status, STATUS_DOMAIN);
     return;
   }
@@ -168,34 +163,35 @@ __device__ __forceinline__ void place_terms_fp64(const PointParams& P, PointArra
   pa.lk[i] = 0.5 * res_mu * res_mu * ismu2 + 0.5 * lk2 - lp;
   const double t[5] = {-res_mu * mup * ismu2 + 0.5 * k2p * ik2 - dlp, kC * (z - zb) * iopz,
                        -kC * zbp * (1.0 + z) * iopz * iopz, ik2, k2p};
-  if constexpr (F32LAYOUT) {
-    float* f = reinterpret_cast<float*>(pa.lk + nt);
 #pragma unroll
-    for (int k = 0; k < 5; ++k) f[k * nt + i] = (float)t[k];
-  } else {
-#pragma unroll
-    for (int k = 0; k < 5; ++k) pa.lk[(k + 1) * nt + i] = t[k];
-  }
+  for (int k = 0; k < 5; ++k) pa.lk[(k + 1) * nt + i] = t[k];
 }
 
 // The same terms on the FP32 path, where only the per-point sums and the
-// energies need FP64.  Two differences cancel and keep FP64 inputs:
-//  - z - zbar, a thousandth of z at these distances (the observed velocity
-//    is c (z - zbar)/(1 + zbar)), so zbar is formed to ~1e-14 in FP64 from
-//    FP32 seeds refined by one Newton step each: s = sqrt(1 - k3 d) and
-//    zbar = c23 k3 d / (1 + s) (= c23 (1 - s) without its cancellation);
-//  - mu_i - mu(d), a few tenths of ~35 mag: with x = d (1 + zbar)/h and
-//    x_ref = 10^((mu_i - 25)/5) (per point, from the host), mu_i - mu(d) =
-//    -(5/ln 10) ln(1 + (x - x_ref)/x_ref), so only x - x_ref is formed in
-//    FP64 and the logarithm runs in FP32 near 1.
-// Everything else is FP32.  Layout: lk[0..nt) doubles A; then floats
-// A', v_obs, v_obs', 1/kappa^2, (kappa^2)' at f[k nt + i], f = (float*)(lk + nt).
+// energies need FP64.  Two differences cancel: z - zbar(d), a thousandth of
+// z at these distances (the observed velocity is c (z - zbar)/(1 + zbar)),
+// and mu_i - mu(d), a few tenths of ~35 mag.  With s = sqrt(1 - k3 d) and
+// the per-point constants of XRef (d_z: zbar(d_z) = z; d_ref: x(d_ref) =
+// x_ref, x(d) = d (1 + zbar)/h the luminosity distance in Mpc):
+//   z - zbar(d)  = e_z - c23 k3 (d - d_z)/(s + s_z),
+//   x(d) - x_ref = e_ref + (d - d_ref)/h [1 + zbar(d) + c23 k3 d_ref/(s + s_ref)],
+// (zbar(a) - zbar(b) = c23 (s_b - s_a) = c23 k3 (a - b)/(s_a + s_b)), and
+// mu_i - mu(d) = -(5/ln 10) ln(1 + (x - x_ref)/x_ref).  The two distance
+// differences are formed from float pairs (TwoSum), so every term runs in
+// FP32; the domain test and the sum A stay in FP64.  Layout: lk[0..nt)
+// doubles A; then floats A', v_obs, v_obs', 1/kappa^2, (kappa^2)' at
+// f[k nt + i], f = (float*)(lk + nt).
+__device__ __forceinline__ float diff_df(float ah, float al, float bh, float bl) {
+  float s, e;
+  two_sum_f(ah, -bh, s, e);
+  return __fadd_rn(s, __fadd_rn(e, __fsub_rn(al, bl)));
+}
+
 __device__ __forceinline__ void place_terms_fp32(const PointParams& P, PointArrays& pa, ChainScal* cs, int c,
                                                  long long i, double d) {
   const long long nt = pa.ntot;
   float* f = reinterpret_cast<float*>(pa.lk + nt);
-  const double eps3 = P.k3 * d;
-  const double om1 = 1.0 - eps3;
+  const double om1 = 1.0 - P.k3 * d;
   float lp = 0.0f, dlp = 0.0f;
   const bool ok = d > 0.0 && om1 > 0.0 && log_prior_f32(P, d, lp, dlp) && !(cs[c].sample_sig && !(cs[c].sig > 0.0));
   if (!ok) {
@@ -204,39 +200,37 @@ __device__ __forceinline__ void place_terms_fp32(const PointParams& P, PointArra
     atomicOr(&cs[c].status, STATUS_DOMAIN);
     return;
   }
-  // sqrt(1 - k3 d): FP32 seed, one Newton step s0 + (om1 - s0^2)/(2 s0)
-  const float s0 = sqrtf((float)om1);
-  const double s0d = (double)s0;
-  const double s = fma(fma(-s0d, s0d, om1), (double)(0.5f / s0), s0d);
-  // zbar = c23 eps3/(1 + s): FP32 reciprocal, one correction of the quotient
-  const double den = 1.0 + s;
-  const double rden = (double)(1.0f / (float)den);
-  double q = eps3 * rden;
-  q = fma(fma(-q, den, eps3), rden, q);
-  const double zb = P.c23 * q;
-  const double opz = 1.0 + zb;
-  const double xr = pa.xr[i];
-  const float qm1 = (float)fma(d * P.inv_h, opz, -xr) / (float)xr;   // x/x_ref - 1
+  const XRef xr = pa.xr[i];
+  float dh, dl;
+  split_df(d, dh, dl);            // 0 < d < 1/k3: always representable
+  const float df = __fadd_rn(dh, dl);
+  const float ck = P.c23k3_f;
+  const float s = sqrtf(__fmaf_rn(-P.k3_f, df, 1.0f));
+  const float zb = ck * df / (1.0f + s);          // c23 (1 - s) without cancellation
+  const float opz = 1.0f + zb;
+  const float iopz = 1.0f / opz;
+  const float zmzb = xr.e_z - ck * diff_df(dh, dl, xr.dz_hi, xr.dz_lo) / (s + xr.s_z);
+  const float dref = xr.dr_hi + xr.dr_lo;
+  const float xmxr = xr.e_ref + diff_df(dh, dl, xr.dr_hi, xr.dr_lo) * P.inv_h_f * (opz + ck * dref / (xr.s_ref + s));
+  const float xref = dref * (1.0f + ck * dref / (1.0f + xr.s_ref)) * P.inv_h_f - xr.e_ref;
   constexpr float k5ln10 = 2.1714724095162591f;                       // 5 / ln 10
-  const float res_mu = -k5ln10 * log1pf(qm1);
-  const float iopz = 1.0f / (float)opz;
-  const float zbp = (float)(kH0 / kC) / (float)s;                      // dzbar/dd
-  const float mup = k5ln10 * (1.0f / (float)d + zbp * iopz);
-  const double z = pa.zobs[i];
-  const float vo = (float)kC * (float)(z - zb) * iopz;
-  const float vop = -(float)kC * zbp * (1.0f + (float)z) * iopz * iopz;
+  const float res_mu = -k5ln10 * log1pf(xmxr / xref);
+  const float zbp = (float)(kH0 / kC) / s;                              // dzbar/dd
+  const float mup = k5ln10 * (1.0f / df + zbp * iopz);
+  const float vo = (float)kC * zmzb * iopz;
+  const float vop = -(float)kC * zbp * (1.0f + (zb + zmzb)) * iopz * iopz;
   // kappa^2 = sigma_NL^2 + sigma_cz^2/(1 + zbar)^2 (eq. kappa); with
   // sigma_cz = 0 and a fixed sigma_NL it is a per-chain constant
   const double scz = pa.scz[i];
   float ik2, k2p;
   double lk2;
-  if (scz == 0.0 && !cs[c].sample_sig) {
+  if ((__double_as_longlong(scz) << 1) == 0 && !cs[c].sample_sig) {
     ik2 = (float)P.ik2_nl;
     lk2 = P.logk2_nl;
     k2p = 0.0f;
   } else {
-    const float scz2 = (float)(scz * scz);
-    const float snl2 = cs[c].sample_sig ? (float)(cs[c].sig * cs[c].sig) : (float)P.sigma_nl2;
+    const float scz2 = (float)scz * (float)scz;
+    const float snl2 = cs[c].sample_sig ? (float)cs[c].sig * (float)cs[c].sig : (float)P.sigma_nl2;
     const float k2 = snl2 + scz2 * iopz * iopz;
     ik2 = 1.0f / k2;
     lk2 = (double)logf(k2);
@@ -255,7 +249,7 @@ __device__ __forceinline__ void place_terms_fp32(const PointParams& P, PointArra
 // d-only likelihood terms (place_terms_fp64 / place_terms_fp32 above).
 template <typename T>
 __global__ void __launch_bounds__(kPtsNT)
-k_points_place(const PointParams* __restrict__ pp, PointArrays pa, ChainScal* __restrict__ cs, int f32_terms) {
+k_points_place(const PointParams* __restrict__ pp, PointArrays pa, ChainScal* __restrict__ cs) {
   pdl_wait();
   pdl_trigger();
   constexpr int kMaxNB = kMaxBuckets;   // sub-buckets per chain (N * ksplit)
@@ -307,7 +301,7 @@ k_points_place(const PointParams* __restrict__ pp, PointArrays pa, ChainScal* __
   const long long i = P.pt_off + il;
   const double rx = pa.rx[i], ry = pa.ry[i], rz = pa.rz[i];
   const double d = pa.d[i];
-  const CellPos cp = cell_of(P, placeable(d), rx, ry, rz);
+  const CellPos cp = (sizeof(T) == 4) ? cell_of_f32(P, placeable(d), rx, ry, rz) : cell_of(P, placeable(d), rx, ry, rz);
   // the bucket and rank come from the counting pass (same arithmetic, same d)
   const int pos = (int)P.pt_off + excl[pa.cx[i]] + pa.slot[i];
   pa.pos[i] = pos;
@@ -322,11 +316,9 @@ k_points_place(const PointParams* __restrict__ pp, PointArrays pa, ChainScal* __
   r.r = (T)0;
   static_cast<PtRec<T>*>(pa.rec)[pos] = r;
   if constexpr (sizeof(T) == 8) {
-    place_terms_fp64<false>(P, pa, cs, c, i, d);
-  } else if (f32_terms) {
-    place_terms_fp32(P, pa, cs, c, i, d);
+    place_terms_fp64(P, pa, cs, c, i, d);
   } else {
-    place_terms_fp64<true>(P, pa, cs, c, i, d);
+    place_terms_fp32(P, pa, cs, c, i, d);
   }
 }
 
@@ -342,97 +334,145 @@ k_points_lik(const PointParams* __restrict__ pp, PointArrays pa, double* __restr
              double* __restrict__ gsig_part) {
   pdl_wait();
   pdl_trigger();
-  __shared__ double red[kPtsNT / 32];
+  __shared__ double red[3][kPtsNT / 32];
   const int c = blockIdx.y;
   const PointParams& P = pp[c];
+  const ChainScal& S = cs[c];
   const long long il = (long long)blockIdx.x * kPtsNT + threadIdx.x;
   double psi_i = 0.0, kin = 0.0, gsig = 0.0;
-  const bool ssig = cs[c].sample_sig != 0;
+  const bool ssig = S.sample_sig != 0;
   if (il < P.pt_n) {
     const long long i = P.pt_off + il;
     const long long nt = pa.ntot;
+    // every load that depends on i alone goes out before the first store
+    // (the arrays are not restrict-qualified, so the compiler keeps loads
+    // after stores in program order): one round of latency for all of them,
+    // then the partials at the bucket position
+    const bool upd = mode != GM_GRAD, drift = mode == GM_KICK_DRIFT;
     const int pos = pa.pos[i];
     const double A = pa.lk[i];
+    const double d0 = upd ? pa.d[i] : 0.0;
+    const double pd0 = (upd && S.sample_d) ? pa.pd[i] : 0.0;
+    const double rx = drift ? pa.rx[i] : 0.0, ry = drift ? pa.ry[i] : 0.0;
     PtRec<T>* rec = static_cast<PtRec<T>*>(pa.rec);
     double gd;
-    if (!isfinite(A)) {
-      psi_i = A;
-      rec[pos].r = (T)0;
-      gd = 0.0;
-    } else if constexpr (sizeof(T) == 4) {
+    if constexpr (sizeof(T) == 4) {
       // FP32 path: the six FP32 partials summed with TwoSum, then the
       // velocity term in FP32 (v_obs - u is a few hundred km/s, kept to
       // ~1e-7 relative); Psi_i and the gradient go to FP64 for the sums and
       // the distance update
-      const float* part = static_cast<const float*>(pa.part);
-      HalfSqAcc<float> su, sdu;
-#pragma unroll
-      for (int k = 0; k < 6; ++k) {
-        su.add(part[(long long)k * nt + pos]);
-        sdu.add(part[(long long)(6 + k) * nt + pos]);
-      }
-      const float u = su.hi + su.lo, du = sdu.hi + sdu.lo;
       const float* f = reinterpret_cast<const float*>(pa.lk + nt);
       const float Ap = f[i], vo = f[nt + i], vop = f[2 * nt + i], ik2 = f[3 * nt + i], k2p = f[4 * nt + i];
-      const float res_v = vo - u;
-      const float r2k = res_v * res_v * ik2;
-      psi_i = A + (double)(0.5f * r2k);
-      rec[pos].r = -res_v * ik2;
-      if (ssig) gsig = (double)((float)cs[c].sig * ik2 * (1.0f - r2k));
-      gd = (double)(Ap + res_v * (vop - du) * ik2 - 0.5f * r2k * k2p * ik2);
-    } else {
-      const T* part = static_cast<const T*>(pa.part);
-      double u = 0.0, du = 0.0;
+      const float* part = static_cast<const float*>(pa.part);
+      float pu[6], pdu[6];
 #pragma unroll
       for (int k = 0; k < 6; ++k) {
-        u += (double)part[(long long)k * nt + pos];
-        du += (double)part[(long long)(6 + k) * nt + pos];
+        pu[k] = part[(long long)k * nt + pos];
+        pdu[k] = part[(long long)(6 + k) * nt + pos];
       }
-      const double vo = pa.lk[2 * nt + i], vop = pa.lk[3 * nt + i];
+      if (!isfinite(A)) {
+        psi_i = A;
+        rec[pos].r = 0.0f;
+        gd = 0.0;
+      } else {
+        HalfSqAcc<float> su, sdu;
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+          su.add(pu[k]);
+          sdu.add(pdu[k]);
+        }
+        const float u = su.hi + su.lo, du = sdu.hi + sdu.lo;
+        const float res_v = vo - u;
+        const float r2k = res_v * res_v * ik2;
+        psi_i = A + (double)(0.5f * r2k);
+        rec[pos].r = -res_v * ik2;
+        if (ssig) gsig = (double)((float)S.sig * ik2 * (1.0f - r2k));
+        gd = (double)(Ap + res_v * (vop - du) * ik2 - 0.5f * r2k * k2p * ik2);
+      }
+    } else {
+      const double Ap = pa.lk[nt + i], vo = pa.lk[2 * nt + i], vop = pa.lk[3 * nt + i];
       const double ik2 = pa.lk[4 * nt + i], k2p = pa.lk[5 * nt + i];
-      const double res_v = vo - u;
-      psi_i = A + 0.5 * res_v * res_v * ik2;
-      rec[pos].r = (T)(-res_v * ik2);
-      if (ssig) gsig = cs[c].sig * ik2 * (1.0 - res_v * res_v * ik2);
-      gd = pa.lk[nt + i] + res_v * (vop - du) * ik2 - 0.5 * res_v * res_v * k2p * ik2 * ik2;
+      const T* part = static_cast<const T*>(pa.part);
+      double pu[6], pdu[6];
+#pragma unroll
+      for (int k = 0; k < 6; ++k) {
+        pu[k] = (double)part[(long long)k * nt + pos];
+        pdu[k] = (double)part[(long long)(6 + k) * nt + pos];
+      }
+      if (!isfinite(A)) {
+        psi_i = A;
+        rec[pos].r = (T)0;
+        gd = 0.0;
+      } else {
+        double u = 0.0, du = 0.0;
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+          u += pu[k];
+          du += pdu[k];
+        }
+        const double res_v = vo - u;
+        psi_i = A + 0.5 * res_v * res_v * ik2;
+        rec[pos].r = (T)(-res_v * ik2);
+        if (ssig) gsig = S.sig * ik2 * (1.0 - res_v * res_v * ik2);
+        gd = Ap + res_v * (vop - du) * ik2 - 0.5 * res_v * res_v * k2p * ik2 * ik2;
+      }
     }
     pa.gd[i] = gd;
-    if (mode != GM_GRAD) {
+    if (upd) {
       // leapfrog update of the distance (the rest of this evaluation no
       // longer reads d: the plane records were formed from the old one)
-      double d = pa.d[i];
-      const ChainScal& S = cs[c];
+      double d = d0;
       if (S.sample_d) {
-        const double ck = (mode == GM_KICK_DRIFT) ? S.eps : 0.5 * S.eps;
-        const double p = pa.pd[i] - ck * gd;
+        const double p = pd0 - (drift ? S.eps : 0.5 * S.eps) * gd;
         pa.pd[i] = p;
-        if (mode == GM_KICK_DRIFT) {
+        if (drift) {
           d = d + S.eps * P.minv_d * p;
           pa.d[i] = d;
+        } else {
+          kin = 0.5 * P.minv_d * p * p;   // summed after the last half kick only
         }
-        kin = 0.5 * P.minv_d * p * p;
       }
-      if (mode == GM_KICK_DRIFT) {
+      if (drift) {
         // buckets of the new distance, for the next evaluation
-        const int key = bucket_key(P, d, pa.rx[i], pa.ry[i]);
+        const int key = bucket_key(P, d, rx, ry);
         pa.cx[i] = key;
         pa.slot[i] = atomicAdd(&pa.cnt_next[c * P.N * P.ksplit + key], 1);
       }
     }
   }
-  const double s = block_sum(psi_i, red);
-  if (threadIdx.x == 0) pts_part[(long long)c * part_stride + blockIdx.x] = s;
-  if (mode == GM_KICK_LAST) {
-    const double k = block_sum(kin, red);
-    if (threadIdx.x == 0) kin_part[(long long)c * part_stride + blockIdx.x] = k;
+  // the block's sums of Psi_i, of the kinetic term and of dPsi/dsigma_NL in
+  // one pass (each a fixed shuffle tree per warp, then the warps in order)
+  const bool last = mode == GM_KICK_LAST;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    psi_i += __shfl_down_sync(0xffffffffu, psi_i, o);
+    if (last) kin += __shfl_down_sync(0xffffffffu, kin, o);
+    if (ssig) gsig += __shfl_down_sync(0xffffffffu, gsig, o);
   }
-  if (ssig) {
-    const double g = block_sum(gsig, red);
-    if (threadIdx.x == 0) gsig_part[(long long)c * part_stride + blockIdx.x] = g;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) {
+    red[0][wid] = psi_i;
+    red[1][wid] = kin;
+    red[2][wid] = gsig;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double sp = 0.0, sk = 0.0, sg = 0.0;
+    for (int w = 0; w < kPtsNT / 32; ++w) {
+      sp += red[0][w];
+      sk += red[1][w];
+      sg += red[2][w];
+    }
+    const long long k = (long long)c * part_stride + blockIdx.x;
+    pts_part[k] = sp;
+    if (last) kin_part[k] = sk;
+    if (ssig) gsig_part[k] = sg;
   }
 }
 
-// Cells only (bit-exact index work), for the sort and for tests.
+// Cells only (bit-exact index work), for the sort and for tests; formed by
+// the double-float screen with its FP64 fallback, as the bucketing and the
+// FP32 path's placement form them.
 __global__ void k_cells(const PointParams* __restrict__ pp, PointArrays pa, const double* __restrict__ d,
                         int* __restrict__ cell_out) {
   const int c = blockIdx.y;
@@ -440,7 +480,7 @@ __global__ void k_cells(const PointParams* __restrict__ pp, PointArrays pa, cons
   const long long il = (long long)blockIdx.x * kPtsNT + threadIdx.x;
   if (il >= P.pt_n) return;
   const long long i = P.pt_off + il;
-  const CellPos cp = cell_of(P, d[i], pa.rx[i], pa.ry[i], pa.rz[i]);
+  const CellPos cp = cell_of_f32(P, d[i], pa.rx[i], pa.ry[i], pa.rz[i]);
   cell_out[i] = (cp.ix * P.N + cp.iy) * P.N + cp.iz;
 }
 
@@ -531,16 +571,10 @@ cudaError_t launch_points_prep(int n_chains, int max_pts, const PointParams* pp,
 
 cudaError_t launch_points_place(int prec, int n_chains, int max_pts, const PointParams* pp,
                                 PointArrays pa, ChainScal* cs, cudaStream_t st) {
-  // runs even without points: block 0 writes the (empty) bucket offsets.
-  // On the FP32 path the d-only terms run in FP32 when the launch covers
-  // several chains and in FP64 for one chain: this kernel runs on a side
-  // stream beside the plane passes, and on GB300 the shorter FP32 form sped
-  // the 16-chain 128^3 evaluation up by 5 % but slowed the one-chain
-  // trajectory by 4 % (same box, same bench; the output is the same layout)
+  // runs even without points: block 0 writes the (empty) bucket offsets
   if (prec == 0)
-    return launch_k<PDL_POINTS>(k_points_place<float>, pts_grid(n_chains, max_pts), dim3(kPtsNT), 0, st, pp, pa, cs,
-                                n_chains > 1 ? 1 : 0);
-  return launch_k<PDL_POINTS>(k_points_place<double>, pts_grid(n_chains, max_pts), dim3(kPtsNT), 0, st, pp, pa, cs, 0);
+    return launch_k<PDL_POINTS>(k_points_place<float>, pts_grid(n_chains, max_pts), dim3(kPtsNT), 0, st, pp, pa, cs);
+  return launch_k<PDL_POINTS>(k_points_place<double>, pts_grid(n_chains, max_pts), dim3(kPtsNT), 0, st, pp, pa, cs);
 }
 
 cudaError_t launch_points_lik(int prec, int n_chains, int max_pts, const PointParams* pp, PointArrays pa,

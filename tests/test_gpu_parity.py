@@ -231,6 +231,39 @@ def test_cells_and_sort_bit_exact(H, N):
     assert np.array_equal(perm.cpu().numpy(), order)
 
 
+@pytest.mark.parametrize("N,L", [(64, 500.0), (128, 500.0), (256, 1000.0)])
+def test_cells_next_to_cell_faces_bit_exact(H, N, L):
+    """Distances that put a point on a cell face, a few ulp and 1e-12..1e-6
+    (relative) to either side of one, and far outside the box (|x/Delta| up
+    to ~2600 cells): the cells must still be floor((o + d r)/Delta) mod N
+    bit for bit, where the fast screen cannot decide as well as where it can."""
+    spec, cat, gp, op, w = make_case(H, N, L, 4000, "fp32", 12)
+    r = cat["rhat"]
+    rng = np.random.default_rng(N)
+    n = r.shape[0]
+    ax = np.argmax(np.abs(r), axis=1)
+    ra = r[np.arange(n), ax]
+    o = op.observer[ax]
+    delta = op.delta
+    # a face k Delta ahead of the observer along the point's main axis
+    steps = rng.integers(1, int(0.3 * N), size=n)
+    k = np.where(ra > 0, np.ceil(o / delta) + steps, np.floor(o / delta) - steps)
+    d_face = (k * delta - o) / ra
+    ds = [d_face]
+    for u in (1, 2, 3, 8):
+        ds.append(d_face + u * np.spacing(d_face))
+        ds.append(d_face - u * np.spacing(d_face))
+    for rel_ in (1e-12, 1e-9, 1e-6):
+        ds.append(d_face * (1.0 + rel_))
+        ds.append(d_face * (1.0 - rel_))
+    ds.append(rng.uniform(1.0e3, 1.0e4, size=n))      # far outside the box: the FP64 fallback
+    ds.append(rng.uniform(0.0, 1.0e-3, size=n))       # at the observer
+    for d in ds:
+        cell, _ = gp.cells(torch.tensor(d, device="cuda"), sort=False)
+        lin, _ = O.cell_sort_order(op, d)
+        assert np.array_equal(cell.cpu().numpy(), lin)
+
+
 def test_philox_words_bit_exact(H):
     n = 4099
     got = H.philox(0x1234_5678_9ABC, n, 7, 3, 1).cpu().numpy().view(np.uint32).reshape(n, 4)
