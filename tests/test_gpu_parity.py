@@ -520,6 +520,21 @@ def test_logpost_grad_256_two_pass_planes(H):
     assert np.all(np.isfinite(tr[:, 0]["H_new"]))
 
 
+def test_trajectory_256_bench_workload_vs_oracle(H):
+    """The 256^3 workload bench.py times (box 1000 Mpc/h, 1e5 points with r^2
+    to 160 Mpc/h, its catalogue seed and chain seed, eps = 0.01): after 3
+    warm-up trajectories, one graph-replayed trajectory against the oracle's
+    from the same state; 4 leapfrog steps a trajectory rather than the
+    bench's 20 keep the oracle's 256^3 transforms to about a minute."""
+    spec = mock.MockSpec(N=256, L=1000.0, n_points=100000, r_max=160.0, mask_deg=10.0, sigma_mu=(0.2, 0.45),
+                         sigma_nl=250.0, seed=1007)
+    cat = mock.make_catalog(spec)
+    gp = H.Problem.from_mock(spec, cat)
+    op = O.problem_from_catalog(spec.N, spec.L, mock.spec_dict(spec)["cosmo"], spec.sigma_nl, cat)
+    _one_trajectory_vs_oracle(H, gp, op, cat["d_init"], seed=5, n_burn=3, eps=0.01, n_steps=4,
+                              tag="trajectory 256^3/100000/fp32/4 steps", tol=1e-5, tol_pd=1e-4)
+
+
 def test_no_bounded_device_wait_gave_up(H):
     """The x pass at FP32 N = 256 waits for tensor copies with a bounded
     poll; after the transforms, gradients and chains above (and one more
