@@ -57,6 +57,10 @@ def parse():
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-256", action="store_true", help="skip the 256^3 one-chain measurement")
     ap.add_argument("--no-fft-ref", action="store_true", help="skip the cuFFT reference timing")
+    ap.add_argument("--serve-only", action="store_true",
+                    help="run only the serving mix (64^3/128^3/256^3, 1e3-1e5 points) and print its JSON")
+    ap.add_argument("--serve-jobs", type=int, default=60, help="jobs in the serving mix")
+    ap.add_argument("--serve-trajectories", type=int, default=50, help="timed trajectories per served job")
     ap.add_argument("--accept-target", type=float, default=0.70,
                     help="acceptance the batched and served chains' step sizes are tuned to (dual averaging)")
     ap.add_argument("--tune-eps", action="store_true", help="print acceptance for a sweep of eps and exit")
@@ -629,6 +633,12 @@ def main():
         print(json.dumps(run_batched(args, args.eps, L, use_graph)), flush=True)
         return
 
+    if args.serve_only:
+        print(json.dumps(run_serving(args.eps, L, args.accept_target, n_jobs=args.serve_jobs,
+                                     n_timed=args.serve_trajectories, grid_slots={256: 2},
+                                     grid_priority={64: -2, 128: -1})), flush=True)
+        return
+
     stream = torch.cuda.current_stream()
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
@@ -820,7 +830,8 @@ def main():
         # the paper-scale serving mix; 256^3 chains fill the GPU alone, so their
         # group batches at most two, and the smaller grids' groups run on
         # higher-priority streams
-        serving = run_serving(args.eps, L, args.accept_target, grid_slots={256: 2}, grid_priority={64: -2, 128: -1})
+        serving = run_serving(args.eps, L, args.accept_target, n_jobs=args.serve_jobs, n_timed=args.serve_trajectories,
+                              grid_slots={256: 2}, grid_priority={64: -2, 128: -1})
         serving["grid_128_only"] = run_serving(args.eps, L, args.accept_target, grids=(128,), n_range=(3e3, 3e4),
                                                n_jobs=48, n_timed=12)
 
