@@ -1081,7 +1081,7 @@ int hm_state_create_batch(hm_problem* const* problems, int32_t n_problems, int32
   s->max_pts = maxp;
   s->pts_blocks = points_blocks(maxp);
   s->nparts_f = field_parts(s->n3);
-  s->nparts_p = std::max(1, std::min(64, (maxp / 2 + 255) / 256));
+  s->nparts_p = traj_begin_points_blocks(maxp);
   const size_t C = n_chains, rs = s->rsz;
   HM_TRY(s->w.alloc(rs * C * s->n3));
   HM_TRY(s->pw.alloc(rs * C * s->n3));
@@ -1532,7 +1532,7 @@ int hm_slots_create(hm_problem* templ, int32_t n_slots, int64_t max_points, uint
   s->max_pts = (int)max_points;
   s->pts_blocks = points_blocks(s->max_pts);
   s->nparts_f = field_parts(s->n3);
-  s->nparts_p = std::max(1, std::min(64, (s->max_pts / 2 + 255) / 256));
+  s->nparts_p = traj_begin_points_blocks(s->max_pts);
   const size_t C = n_slots, rs = s->rsz;
   DevBuf* grids[] = {&s->w, &s->pw, &s->gw, &s->w0, &s->gw0};
   for (DevBuf* b : grids) HM_TRY(b->alloc(rs * C * s->n3));

@@ -172,14 +172,17 @@ k_traj_begin_field(long long n3, T* __restrict__ w, T* __restrict__ pw, const T*
   }
 }
 
-// Trajectory start, distance part: p_d ~ N(0, (H0/sigma_v)^2).
-__global__ void __launch_bounds__(kEwNT)
+// Trajectory start, distance part: p_d ~ N(0, (H0/sigma_v)^2).  Small
+// blocks (kBpNT threads, one point pair each), so that the FP64 Box-Muller
+// of a catalogue spreads over every SM's FP64 unit.
+constexpr int kBpNT = 64;
+__global__ void __launch_bounds__(kBpNT)
 k_traj_begin_points(const PointParams* __restrict__ pp, PointArrays pa, double* __restrict__ d0,
                     double* __restrict__ gd0, unsigned long long seed, const int* __restrict__ chain_id,
                     double* __restrict__ kin_part, int draw, ChainScal* __restrict__ cs) {
   pdl_wait();
   pdl_trigger();
-  __shared__ double red[kEwNT / 32];
+  __shared__ double red[kBpNT / 32];
   const int c = blockIdx.y;
   const PointParams& P = pp[c];
   const double eps = cs[c].eps;
@@ -188,8 +191,8 @@ k_traj_begin_points(const PointParams* __restrict__ pp, PointArrays pa, double* 
   const int sd = cs[c].sample_d;
   double kin = 0.0;
   const long long npair = (P.pt_n + 1) / 2;
-  for (long long q = (long long)blockIdx.x * kEwNT + threadIdx.x; q < npair;
-       q += (long long)gridDim.x * kEwNT) {
+  for (long long q = (long long)blockIdx.x * kBpNT + threadIdx.x; q < npair;
+       q += (long long)gridDim.x * kBpNT) {
     double nn[2] = {0.0, 0.0};
     if (draw) normal_pair(seed, (unsigned)q, traj, cid, 1u, nn[0], nn[1]);
 #pragma unroll
@@ -228,7 +231,7 @@ k_traj_begin_points(const PointParams* __restrict__ pp, PointArrays pa, double* 
 // then a fixed shuffle tree; lane 0 gets the result.
 __device__ __forceinline__ double warp_sum_fixed(const double* __restrict__ x, int n) {
   double s = 0.0;
-  for (int i = threadIdx.x; i < n; i += 32) s += x[i];
+  for (int i = threadIdx.x & 31; i < n; i += 32) s += x[i];
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
   return s;
@@ -243,16 +246,20 @@ __global__ void k_finalize(const double* __restrict__ prior_part, int n_prior,
   pdl_wait();
   pdl_trigger();
   const int c = blockIdx.x;
-  double a = 0.0, b = 0.0, k = 0.0, kp = 0.0;
-  if (what & FIN_PSI) {
-    a = warp_sum_fixed(prior_part + (long long)c * n_prior, n_prior);
-    b = warp_sum_fixed(pts_part + (long long)c * n_pts, n_pts);
-  }
-  if (what & (FIN_HOLD | FIN_ACCEPT | FIN_KIN)) {
-    k = warp_sum_fixed(kin_part + (long long)c * n_kin, n_kin);
-    kp = warp_sum_fixed(kin_pts_part + (long long)c * n_kin_pts, n_kin_pts);
-  }
+  // the four sums, one warp each (the same fixed order as one warp doing
+  // them one after another), met in shared memory
+  __shared__ double sums[4];
+  const int wid = threadIdx.x >> 5;
+  const bool psi = (what & FIN_PSI) != 0, kin = (what & (FIN_HOLD | FIN_ACCEPT | FIN_KIN)) != 0;
+  double v = 0.0;
+  if (wid == 0 && psi) v = warp_sum_fixed(prior_part + (long long)c * n_prior, n_prior);
+  if (wid == 1 && psi) v = warp_sum_fixed(pts_part + (long long)c * n_pts, n_pts);
+  if (wid == 2 && kin) v = warp_sum_fixed(kin_part + (long long)c * n_kin, n_kin);
+  if (wid == 3 && kin) v = warp_sum_fixed(kin_pts_part + (long long)c * n_kin_pts, n_kin_pts);
+  if ((threadIdx.x & 31) == 0) sums[wid] = v;
+  __syncthreads();
   if (threadIdx.x != 0) return;
+  const double a = sums[0], b = sums[1], k = sums[2], kp = sums[3];
   ChainScal& S = cs[c];
   if (what & FIN_PSI) {
     S.psi_prior = a;
@@ -445,13 +452,15 @@ cudaError_t launch_traj_begin_field(int prec, int n_chains, long long n3, void* 
                   (const double*)gw, (double*)w0, (double*)gw0, seed, chain_id, kin_part, draw, cs);
 }
 
+int traj_begin_points_blocks(int max_pts) { return std::max(1, std::min(512, (max_pts / 2 + kBpNT - 1) / kBpNT)); }
+
 cudaError_t launch_traj_begin_points(int n_chains, int /*max_pts*/, const PointParams* pp,
                                      PointArrays pa, double* d0, double* gd0,
                                      unsigned long long seed, const int* chain_id,
                                      double* kin_part, int nparts, int draw, ChainScal* cs,
                                      cudaStream_t st) {
   dim3 g(nparts, n_chains);
-  return launch_k(k_traj_begin_points, g, dim3(kEwNT), 0, st, pp, pa, d0, gd0, seed, chain_id, kin_part, draw, cs);
+  return launch_k(k_traj_begin_points, g, dim3(kBpNT), 0, st, pp, pa, d0, gd0, seed, chain_id, kin_part, draw, cs);
 }
 
 cudaError_t launch_set_run(int n_chains, const double* eps, int sample_d, ChainScal* cs,
@@ -463,7 +472,7 @@ cudaError_t launch_finalize(int n_chains, const double* prior_part, int n_prior,
                             int n_pts, const double* kin_part, int n_kin, const double* kin_pts_part,
                             int n_kin_pts, int what, unsigned long long seed, const int* chain_id,
                             ChainScal* cs, void* trace_dev, cudaStream_t st) {
-  return launch_k(k_finalize, dim3(n_chains), dim3(32), 0, st, prior_part, n_prior, pts_part, n_pts, kin_part, n_kin,
+  return launch_k(k_finalize, dim3(n_chains), dim3(128), 0, st, prior_part, n_prior, pts_part, n_pts, kin_part, n_kin,
                   kin_pts_part, n_kin_pts, what, seed, chain_id, cs, static_cast<hm_trace*>(trace_dev));
 }
 

@@ -253,6 +253,9 @@ cudaError_t launch_traj_begin_field(int prec, int n_chains, long long n3, void* 
                                     const int* chain_id, double* kin_part, int nparts, int draw,
                                     ChainScal* cs, cudaStream_t st);
 // also counts the drifted distances into pa.cnt_next (zeroed beforehand)
+// Blocks of the trajectory-start kernel of the distances (and slots of its
+// kinetic partials) for a catalogue of max_pts points.
+int traj_begin_points_blocks(int max_pts);
 cudaError_t launch_traj_begin_points(int n_chains, int max_pts, const PointParams* pp,
                                      PointArrays pa, double* d0, double* gd0,
                                      unsigned long long seed, const int* chain_id,
