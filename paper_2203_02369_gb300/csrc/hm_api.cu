@@ -431,9 +431,10 @@ struct GradArgs {
 
 // The gradient evaluations of a leapfrog run (or one standalone evaluation)
 // for C chains.  Streams: the side stream `aux` places the points of
-// evaluation l+1 into x-plane buckets (and evaluates the FP64 likelihood
-// terms that depend on d alone) while the main stream runs evaluation l's
-// adjoint; the main stream of evaluation l is
+// evaluation l+1 into x-plane buckets (and evaluates the likelihood terms
+// that depend on d alone) while the main stream finishes evaluation l (its
+// adjoint, or for one chain its gradient epilogue); the main stream of
+// evaluation l is
 //   [plane r2c of w] -> x pencils with the velocity weights -> plane c2r with
 //   the CIC gather -> likelihood (+ distance kick/drift, next buckets) ->
 //   plane CIC scatter + r2c -> x pencils with the adjoint weights -> plane
@@ -478,11 +479,19 @@ static int eval_run(const GradArgs& a, int n, int last_mode, cudaStream_t st) {
             launch_points_lik(a.prec, a.C, a.max_pts, a.pp, pa, a.pts_part, a.pts_blocks, mode, a.kinl_p, a.cs,
                               a.gsig_part, st));
     if (a.sample_sig) HM_CUDA(launch_sig_update(a.C, a.gsig_part, a.pts_blocks, mode, a.cs, st));
-    if (l < n) HM_TRY(place_points(a, par ^ 1, st));   // next evaluation's buckets, off the critical path
+    // next evaluation's buckets, off the critical path: forked right after
+    // the likelihood for several chains; for one chain up to 128^3 after the
+    // adjoint pencils, so that it runs beside the gradient epilogue and the
+    // velocity pencils instead of taking SMs from the scatter pass (measured
+    // on one box: plain 128^3 trajectory 1.690 -> 1.658 ms, 32-chain batch
+    // 20.07 -> 20.18 ms, 256^3 unchanged)
+    const bool late_fork = a.C == 1 && a.N <= 128;
+    if (l < n && !late_fork) HM_TRY(place_points(a, par ^ 1, st));
     // adjoint: residuals scattered plane by plane, forward transform, weights
     HM_PROF(pf, KK_R2C_SCATTER, st, launch_plane_r2c_scatter(a.prec, a.N, pts, a.S1, a.nspec, 3 * a.C, a.tw, st));
     HM_PROF(pf, KK_PENCIL_ADJ, st,
             launch_pencil(a.prec, a.N, PM_ADJ, a.S1, a.nspec, a.S2, a.nspec, a.C, a.tw, a.amp, st, pts.off));
+    if (l < n && late_fork) HM_TRY(place_points(a, par ^ 1, st));
     FieldEpi epi{};
     epi.w = a.w;
     epi.pw = a.pw;
