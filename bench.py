@@ -751,14 +751,10 @@ def main():
             torch.cuda.synchronize()
             flush.zero_()
             s_e[k].record(stream)
-            w_d = w_h.to(dev, non_blocking=True)
-            d_d = d_h.to(dev, non_blocking=True)
-            state.set(0, w=w_d, d=d_d)
+            state.set(0, w=w_h, d=d_h)            # pinned host -> the state, one copy each
             state.refresh()
             trk = state.run_chain(1, L, args.eps, use_graph=use_graph, trace=True)
-            gg = state.get(0)
-            w_o.copy_(gg["w"], non_blocking=True)
-            d_o.copy_(gg["d"], non_blocking=True)
+            state.get(0, out={"w": w_o, "d": d_o})   # the state -> pinned host
             e_e[k].record(stream)
         torch.cuda.synchronize()
         ms_e = float(np.mean([s.elapsed_time(e) for s, e in zip(s_e, e_e)]))
@@ -766,8 +762,9 @@ def main():
         bo = bi + 48
         e2e = {"value": ws * L / (ms_e / 1e3), "unit": UNIT, "h2d_bytes_per_step": bi,
                "d2h_bytes_per_step": bo, "ms_per_step": ms_e,
-               "note": "per step: pinned H2D of (w, d), hm_state_set + hm_state_refresh (one extra gradient "
-                       "evaluation, not counted), one trajectory, D2H of (w, d) and the trace record"}
+               "note": "per step: hm_state_set from pinned host (w, d), hm_state_refresh (one extra gradient "
+                       "evaluation, not counted), one trajectory, hm_state_get of (w, d) into pinned host and the "
+                       "trace record"}
 
     # roofline of the dominant kernel (live CUDA-event times from the profiled pass)
     N, n = spec.N, spec.n_points

@@ -203,14 +203,18 @@ int hm_state_create_batch(hm_problem* const* problems, int32_t n_problems, int32
                           const double* const* d_init_host, hm_state** out);
 void hm_destroy_state(hm_state* s);
 
-/* Copy a chain's position (w, d) and/or momenta (p_w, p_d) in or out
- * (device pointers; NULL leaves that part alone).  After setting positions,
+/* Copy a chain's position (w, d) and/or momenta (p_w, p_d) in or out, as
+ * stream-ordered copies.  Each pointer may be device memory or host memory
+ * (the copy direction follows from the address under unified addressing);
+ * pinned host memory gives asynchronous copies, pageable host memory is
+ * staged by the driver.  A host buffer must stay valid until the stream has
+ * reached the copy.  NULL leaves that part alone.  After setting positions,
  * hm_state_refresh recomputes Psi and the gradient there. */
-int hm_state_set(hm_state* s, int32_t chain, const void* w_dev, const double* d_dev,
-                 const void* pw_dev, const double* pd_dev, void* stream);
-int hm_state_get(hm_state* s, int32_t chain, void* w_dev, double* d_dev, void* pw_dev,
-                 double* pd_dev, void* stream);
-int hm_state_get_grad(hm_state* s, int32_t chain, void* gw_dev, double* gd_dev, void* stream);
+int hm_state_set(hm_state* s, int32_t chain, const void* w, const double* d, const void* pw, const double* pd,
+                 void* stream);
+int hm_state_get(hm_state* s, int32_t chain, void* w, double* d, void* pw, double* pd, void* stream);
+/* (the same for the gradient (grad_w, grad_d) at the chain's position) */
+int hm_state_get_grad(hm_state* s, int32_t chain, void* gw, double* gd, void* stream);
 int hm_state_refresh(hm_state* s, void* stream);
 /* Per-chain scalars: Psi at the current position, kinetic energy of the
  * current momenta, trajectory counter (synchronises the stream). */

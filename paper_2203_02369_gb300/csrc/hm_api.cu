@@ -1191,10 +1191,10 @@ int hm_state_set(hm_state* s, int32_t chain, const void* w, const double* d, con
   HM_CUDA(cudaSetDevice(s->device));
   const size_t gb = s->rsz * s->n3;
   const PointParams& P = s->pp_host[chain];
-  if (w) HM_CUDA(cudaMemcpyAsync((char*)s->w.p + gb * chain, w, gb, cudaMemcpyDeviceToDevice, st));
-  if (pw) HM_CUDA(cudaMemcpyAsync((char*)s->pw.p + gb * chain, pw, gb, cudaMemcpyDeviceToDevice, st));
-  if (d && P.pt_n) HM_CUDA(cudaMemcpyAsync(s->d.as<double>() + P.pt_off, d, 8 * P.pt_n, cudaMemcpyDeviceToDevice, st));
-  if (pd && P.pt_n) HM_CUDA(cudaMemcpyAsync(s->pd.as<double>() + P.pt_off, pd, 8 * P.pt_n, cudaMemcpyDeviceToDevice, st));
+  if (w) HM_CUDA(cudaMemcpyAsync((char*)s->w.p + gb * chain, w, gb, cudaMemcpyDefault, st));
+  if (pw) HM_CUDA(cudaMemcpyAsync((char*)s->pw.p + gb * chain, pw, gb, cudaMemcpyDefault, st));
+  if (d && P.pt_n) HM_CUDA(cudaMemcpyAsync(s->d.as<double>() + P.pt_off, d, 8 * P.pt_n, cudaMemcpyDefault, st));
+  if (pd && P.pt_n) HM_CUDA(cudaMemcpyAsync(s->pd.as<double>() + P.pt_off, pd, 8 * P.pt_n, cudaMemcpyDefault, st));
   return HM_OK;
 }
 
@@ -1204,10 +1204,10 @@ int hm_state_get(hm_state* s, int32_t chain, void* w, double* d, void* pw, doubl
   HM_CUDA(cudaSetDevice(s->device));
   const size_t gb = s->rsz * s->n3;
   const PointParams& P = s->pp_host[chain];
-  if (w) HM_CUDA(cudaMemcpyAsync(w, (char*)s->w.p + gb * chain, gb, cudaMemcpyDeviceToDevice, st));
-  if (pw) HM_CUDA(cudaMemcpyAsync(pw, (char*)s->pw.p + gb * chain, gb, cudaMemcpyDeviceToDevice, st));
-  if (d && P.pt_n) HM_CUDA(cudaMemcpyAsync(d, s->d.as<double>() + P.pt_off, 8 * P.pt_n, cudaMemcpyDeviceToDevice, st));
-  if (pd && P.pt_n) HM_CUDA(cudaMemcpyAsync(pd, s->pd.as<double>() + P.pt_off, 8 * P.pt_n, cudaMemcpyDeviceToDevice, st));
+  if (w) HM_CUDA(cudaMemcpyAsync(w, (char*)s->w.p + gb * chain, gb, cudaMemcpyDefault, st));
+  if (pw) HM_CUDA(cudaMemcpyAsync(pw, (char*)s->pw.p + gb * chain, gb, cudaMemcpyDefault, st));
+  if (d && P.pt_n) HM_CUDA(cudaMemcpyAsync(d, s->d.as<double>() + P.pt_off, 8 * P.pt_n, cudaMemcpyDefault, st));
+  if (pd && P.pt_n) HM_CUDA(cudaMemcpyAsync(pd, s->pd.as<double>() + P.pt_off, 8 * P.pt_n, cudaMemcpyDefault, st));
   return HM_OK;
 }
 
@@ -1217,8 +1217,8 @@ int hm_state_get_grad(hm_state* s, int32_t chain, void* gw, double* gd, void* st
   HM_CUDA(cudaSetDevice(s->device));
   const size_t gb = s->rsz * s->n3;
   const PointParams& P = s->pp_host[chain];
-  if (gw) HM_CUDA(cudaMemcpyAsync(gw, (char*)s->gw.p + gb * chain, gb, cudaMemcpyDeviceToDevice, st));
-  if (gd && P.pt_n) HM_CUDA(cudaMemcpyAsync(gd, s->gd.as<double>() + P.pt_off, 8 * P.pt_n, cudaMemcpyDeviceToDevice, st));
+  if (gw) HM_CUDA(cudaMemcpyAsync(gw, (char*)s->gw.p + gb * chain, gb, cudaMemcpyDefault, st));
+  if (gd && P.pt_n) HM_CUDA(cudaMemcpyAsync(gd, s->gd.as<double>() + P.pt_off, 8 * P.pt_n, cudaMemcpyDefault, st));
   return HM_OK;
 }
 

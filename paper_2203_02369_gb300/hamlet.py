@@ -249,13 +249,35 @@ class State:
         return self.problems[self.chain_problem[c]].n
 
     def set(self, chain=0, w=None, d=None, pw=None, pd=None):
-        conv = lambda t, dt: None if t is None else t.to(self.device, dt).contiguous()
+        """Copy a chain's position and/or momenta in.  Device tensors, or host
+        tensors (pinned ones are copied asynchronously on the current stream;
+        the state keeps a reference to them until the next set)."""
+        def conv(t, dt):
+            if t is None:
+                return None
+            if t.device.type == "cpu":
+                return t.to(dt).contiguous()
+            return t.to(self.device, dt).contiguous()
         w, pw = conv(w, self.dtype), conv(pw, self.dtype)
         d, pd = conv(d, torch.float64), conv(pd, torch.float64)
         check(self.lib.hm_state_set(self.h, chain, _ptr(w), _ptr(d), _ptr(pw), _ptr(pd), _stream()))
         self._keep = (w, d, pw, pd)
 
-    def get(self, chain=0):
+    def get(self, chain=0, out=None):
+        """A chain's position and momenta as new device tensors, or, with out
+        (a dict of contiguous tensors keyed by some of "w", "d", "pw", "pd", on
+        the device or on the host), copied into those only (asynchronous on
+        the current stream for device and pinned host tensors)."""
+        if out is not None:
+            want = {"w": self.dtype, "pw": self.dtype, "d": torch.float64, "pd": torch.float64}
+            size = {"w": self.N ** 3, "pw": self.N ** 3, "d": self._n(chain), "pd": self._n(chain)}
+            for k, t in out.items():
+                if k not in want or t.dtype != want[k] or not t.is_contiguous() or t.numel() != size[k]:
+                    raise ValueError(f"out[{k!r}] must be a contiguous {want.get(k)} tensor of {size.get(k)} "
+                                     "elements")
+            p = {k: (_ptr(out[k]) if k in out else None) for k in want}
+            check(self.lib.hm_state_get(self.h, chain, p["w"], p["d"], p["pw"], p["pd"], _stream()))
+            return out
         N = self.N
         w = torch.empty((N,) * 3, dtype=self.dtype, device=self.device)
         pw = torch.empty_like(w)

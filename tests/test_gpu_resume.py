@@ -77,3 +77,32 @@ def test_restore_rejects_another_stream_or_grid(H, tmp_path):
         fh.truncate(100)
     with pytest.raises(H.HamletError):
         a.restore(path)
+
+
+def test_state_io_with_host_buffers(H):
+    """hm_state_set / hm_state_get take host memory as well as device
+    memory: pinned and pageable host tensors give the same chain state as the
+    device path, in both directions."""
+    spec = mock.MockSpec(N=32, L=300.0, n_points=700, r_max=96.0, mask_deg=0.0, sigma_mu=(0.2, 0.45),
+                         sigma_nl=250.0, seed=9, precision="fp32")
+    cat = mock.make_catalog(spec)
+    gp = H.Problem.from_mock(spec, cat)
+    st = H.State(gp, [cat["d_init"]], seed=4)
+    st.run_chain(2, 5, 0.02, use_graph=False, trace=False)
+    ref = {k: v.cpu() for k, v in st.get(0).items()}
+    for pin in (True, False):
+        out = {k: (torch.empty_like(v).pin_memory() if pin else torch.empty_like(v)) for k, v in ref.items()}
+        st.get(0, out=out)
+        torch.cuda.synchronize()
+        for k in ref:
+            assert torch.equal(out[k], ref[k]), k
+        # write a modified state from host memory and read it back on the device
+        w = ref["w"] * 0.5
+        d = ref["d"] + 0.25
+        st.set(0, w=w.pin_memory() if pin else w, d=d.pin_memory() if pin else d)
+        g = st.get(0)
+        torch.cuda.synchronize()
+        assert torch.equal(g["w"].cpu(), w) and torch.equal(g["d"].cpu(), d)
+        st.set(0, w=ref["w"].cuda(), d=ref["d"].cuda())
+    with pytest.raises(ValueError):
+        st.get(0, out={"w": torch.empty(5)})
