@@ -1,8 +1,10 @@
-// Point-side kernels of the HAMLET posterior: positions and cells, the
-// cloud-in-cell gather of the linear velocity field at each point's sampled
-// distance, the FP64 likelihood terms with their gradients (eqs. lmu, vrobs,
-// lvr, kappa, D), the adjoint CIC scatter of the residuals, and the leapfrog
-// update of the distances (mass matrix eq. M_ab: (sigma_v/H0)^2 for d).
+// Point-side kernels of the HAMLET posterior: positions and cells (bit-exact
+// index work), the bucketing of the points by x-plane for the plane passes
+// that run the CIC gather and scatter (hm_fft_kernels.cu), the likelihood
+// terms with their gradients (eqs. lmu, vrobs, lvr, kappa, D; FP32 terms
+// with FP64 sums on the FP32 path, FP64 throughout on the FP64 path), the
+// leapfrog update of the distances (mass matrix eq. M_ab: (sigma_v/H0)^2 for
+// d) and the stable cell sort.
 #include "hm_fft.cuh"
 #include "hm_internal.h"
 #include "hm_device.cuh"
