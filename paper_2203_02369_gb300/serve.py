@@ -263,8 +263,10 @@ class BatchedServingLoop:
     gains little from sharing launches and pays for it in trajectory
     latency, so it can be held to one or two slots while small grids batch
     up to max_slots.  grid_priority maps N to its group's CUDA stream
-    priority (lower is higher): short small-grid trajectories need not wait
-    behind the CTAs of a large grid's kernels."""
+    priority (lower is higher): the group's job loads, refreshes and step
+    adaptation go ahead of a large grid's kernels.  The trajectories
+    themselves replay from captured graphs on the slotted state's own stream,
+    at the default priority."""
 
     def __init__(self, max_slots=8, max_points=100_000, reserve_bytes=2 << 30, device=0, use_graph=True,
                  keep_state=False, seed=0, backend_factory=None, prepare=None, free_bytes=None, prep_threads=2,
