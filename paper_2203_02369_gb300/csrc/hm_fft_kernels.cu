@@ -26,7 +26,7 @@ template <int N> struct PlaneCfg {
   static constexpr int ZP = N + 1;                 // odd pitch of a packed z row
   static constexpr int NT = N >= 128 ? 512 : (N >= 64 ? 256 : 128);
   static constexpr int SIZE = NR * ZP;             // complex elements of the plane buffer
-  static constexpr int MINB = N >= 128 ? 2 : 1;    // CTAs per SM the register budget aims at
+  static constexpr int MINB = N >= 128 ? 2 : (N == 64 ? 4 : 1);   // CTAs per SM the register budget aims at
 };
 
 template <typename T, int N> constexpr size_t plane_smem_bytes() {
