@@ -21,10 +21,12 @@ using namespace hm;
 namespace hm {
 bool pdl_enabled(int cat) {
   static const int mask = [] {
-    // default: the x pencils only (measured on the 128^3 trajectory: pencils
-    // 1.725 ms, none 1.750, plane passes 1.887, point kernels 2.047, all 2.312)
+    // default: the x pencils and the per-trajectory kernels (measured on the
+    // 128^3 trajectory: pencils 1.725 ms, none 1.750, plane passes 1.887,
+    // point kernels 2.047, all 2.312; later, pencils 1.650 vs pencils and
+    // per-trajectory kernels 1.648, and 19.92 vs 19.85 ms for 32 chains)
     const char* e = std::getenv("HM_PDL");
-    return e ? std::atoi(e) : (int)PDL_PENCIL;
+    return e ? std::atoi(e) : (int)(PDL_PENCIL | PDL_OTHER);
   }();
   return (mask & cat) != 0;
 }

@@ -9,7 +9,8 @@ namespace hm {
 // Kernel launch, optionally with programmatic stream serialisation (the
 // kernel may start while its predecessor in the stream finishes; it calls
 // pdl_wait before reading the predecessor's output), for the categories
-// that HM_PDL selects (default: the x pencils).  Launching the plane passes
+// that HM_PDL selects (default: the x pencils and the per-trajectory
+// kernels: start, finalize, restore).  Launching the plane passes
 // or the point kernels early made the 128^3 trajectory slower: the early
 // CTAs wait on SMs that the predecessor's last CTAs or the side stream need.
 // Launch categories for the programmatic-dependent-launch switch: the
