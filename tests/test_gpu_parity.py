@@ -140,6 +140,52 @@ def test_logpost_grad_128_fp64(H):
     check("grad_d 128^3/10000/fp64", gd, rgd, 1e-12)
 
 
+def test_logpost_grad_128_1e5_points(H):
+    """The largest 128^3 job of the serving mix (10^5 points, r^2 to 160
+    Mpc/h in the 500 Mpc/h box): every plane carries thousands of points."""
+    spec, cat, gp, op, w = make_case(H, 128, 500.0, 100000, "fp32", 31, mask=10.0, r_max=160.0)
+    d = cat["d_init"]
+    psi, gw, gd = gp.logpost_grad(torch.tensor(w, device="cuda"), torch.tensor(d, device="cuda"))
+    rpsi, rgw, rgd = O.logpost_grad(op, w, d)
+    check_scalar("psi 128^3/100000/fp32", psi.item(), rpsi, 1e-5)
+    check("grad_w 128^3/100000/fp32", gw, rgw, 1e-5)
+    check("grad_d 128^3/100000/fp32", gd, rgd, 1e-5)
+
+
+@pytest.mark.parametrize("N,L,prec", [(64, 500.0, "fp32"), (128, 500.0, "fp32"), (32, 300.0, "fp64"),
+                                      (256, 1000.0, "fp32")])
+def test_all_points_on_one_x_plane(H, N, L, prec):
+    """A degenerate catalogue: every direction lies (almost) in the y-z plane
+    through the observer (0 <= rhat_x < 1e-3), so every point's lower CIC
+    corner is on the observer's x-plane and one bucket (or one plane's slab
+    buckets at 256^3) holds the whole catalogue, a tenth of the directions
+    exactly in the plane (the points sit on the cell face, fx = 0)."""
+    n = 4000
+    spec = mock.MockSpec(N=N, L=L, n_points=n, r_max=0.3 * L, mask_deg=0.0, sigma_mu=(0.2, 0.45),
+                         sigma_nl=250.0, seed=17, precision=prec)
+    cat = mock.make_catalog(spec)
+    rng = np.random.default_rng(N)
+    rx = rng.uniform(0.0, 1e-3, n)
+    rx[: n // 10] = 0.0
+    phi = rng.uniform(0.0, 2.0 * np.pi, n)
+    s_ = np.sqrt(1.0 - rx * rx)
+    cat["rhat"] = np.ascontiguousarray(np.stack([rx, s_ * np.cos(phi), s_ * np.sin(phi)], axis=1))
+    gp = H.Problem.from_mock(spec, cat)
+    op = O.problem_from_catalog(N, L, mock.spec_dict(spec)["cosmo"], spec.sigma_nl, cat)
+    cell, _ = O.cic_cells(op, cat["d_init"])
+    assert np.all(cell[:, 0] == N // 2)
+    w = mock.white_field(N, 5)
+    if prec == "fp32":
+        w = w.astype(np.float32).astype(np.float64)
+    d = cat["d_init"]
+    psi, gw, gd = gp.logpost_grad(torch.tensor(w, device="cuda"), torch.tensor(d, device="cuda"))
+    rpsi, rgw, rgd = O.logpost_grad(op, w, d)
+    tag = f"one plane {N}^3/{n}/{prec}"
+    check_scalar(f"psi {tag}", psi.item(), rpsi, TOL[prec])
+    check(f"grad_w {tag}", gw, rgw, TOL[prec])
+    check(f"grad_d {tag}", gd, rgd, TOL[prec])
+
+
 def test_default_prior_is_the_redshift_distance_histogram(H):
     """Section "Priors": without a caller table the library builds eq. D from
     the catalogue's observed redshifts (d_z by eq. e:dz) at hm_set_catalog;
