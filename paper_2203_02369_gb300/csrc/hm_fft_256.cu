@@ -298,6 +298,9 @@ k_z_c2r(const C* __restrict__ in, long long in_stride, float* __restrict__ out, 
     const float ck = (mode == GM_KICK_DRIFT) ? eps : 0.5f * eps;
     const bool fuse_next = next != nullptr && mode == GM_KICK_DRIFT;
     const bool kick = mode != GM_GRAD;
+    // the prior and kinetic sums are read only at the trajectory's end point
+    // (and for GM_GRAD): an intermediate leapfrog evaluation skips them
+    const bool sums = mode != GM_KICK_DRIFT, last = mode == GM_KICK_LAST;
     HalfSqAcc<float> aw, ap;
     constexpr int U = 4;   // items per thread per round, loads issued before stores
     static_assert(ITEMS % (U * NT) == 0, "no ragged round");
@@ -324,13 +327,13 @@ k_z_c2r(const C* __restrict__ in, long long in_stride, float* __restrict__ out, 
           const int o = (2 * r + h) * N + z;
           const float w0 = wv[u][h];
           const float g0 = w0 + (h == 0 ? g2.x : g2.y);
-          aw.add_half_sq(w0);
+          if (sums) aw.add_half_sq(w0);
           nv[h] = w0;
           if (mode == GM_GRAD || mode == GM_KICK_LAST) gw[o] = g0;
           if (kick) {
             const float p0 = pv[u][h] - ck * g0;
             pw[o] = p0;
-            ap.add_half_sq(p0);
+            if (last) ap.add_half_sq(p0);
             if (mode == GM_KICK_DRIFT) {
               nv[h] = w0 + eps * p0;
               w[o] = nv[h];
@@ -341,16 +344,19 @@ k_z_c2r(const C* __restrict__ in, long long in_stride, float* __restrict__ out, 
       }
     }
     // deterministic block reduction: a fixed shuffle tree per warp, then
-    // thread 0 over the warps in order
-    aw.warp_reduce();
-    ap.warp_reduce();
+    // thread 0 over the warps in order (the barrier also completes the
+    // drifted rows in B before the forward transform reads them)
+    if (sums) {
+      aw.warp_reduce();
+      if (last) ap.warp_reduce();
+    }
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    if (lane == 0) {
+    if (sums && lane == 0) {
       red[0][wid] = aw.value();
       red[1][wid] = ap.value();
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
+    if (sums && threadIdx.x == 0) {
       double a = 0.0, bsum = 0.0;
       for (int i = 0; i < NT / 32; ++i) {
         a += red[0][i];

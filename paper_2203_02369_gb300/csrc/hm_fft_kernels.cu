@@ -455,6 +455,9 @@ k_plane_c2r(const cplx<T>* __restrict__ in, long long in_stride, T* __restrict__
     const T ck = (mode == GM_KICK_DRIFT) ? eps : (T)0.5 * eps;
     const bool fuse_next = next != nullptr && mode == GM_KICK_DRIFT;
     const bool kick = mode != GM_GRAD;
+    // the prior and kinetic sums are read only at the trajectory's end point
+    // (and for GM_GRAD): an intermediate leapfrog evaluation skips them
+    const bool sums = mode != GM_KICK_DRIFT, last = mode == GM_KICK_LAST;
     HalfSqAcc<T> aw, ap;
     // U items per thread per round: all their global loads are issued before
     // any store, so their latencies overlap
@@ -485,13 +488,13 @@ k_plane_c2r(const cplx<T>* __restrict__ in, long long in_stride, T* __restrict__
           const int o = (2 * r + h) * N + z;
           const T w0 = wv[u][h];
           const T g0 = w0 + (h == 0 ? g2.x : g2.y);
-          aw.add_half_sq(w0);
+          if (sums) aw.add_half_sq(w0);
           nv[h] = w0;
           if (mode == GM_GRAD || mode == GM_KICK_LAST) gw[o] = g0;
           if (kick) {
             const T p0 = pv[u][h] - ck * g0;
             pw[o] = p0;
-            ap.add_half_sq(p0);
+            if (last) ap.add_half_sq(p0);
             if (mode == GM_KICK_DRIFT) {
               nv[h] = w0 + eps * p0;
               w[o] = nv[h];
@@ -502,16 +505,19 @@ k_plane_c2r(const cplx<T>* __restrict__ in, long long in_stride, T* __restrict__
       }
     }
     // deterministic block reduction: a fixed shuffle tree per warp, then
-    // thread 0 over the warps in order
-    aw.warp_reduce();
-    ap.warp_reduce();
+    // thread 0 over the warps in order (the barrier also completes the
+    // drifted rows in B before the forward transform reads them)
+    if (sums) {
+      aw.warp_reduce();
+      if (last) ap.warp_reduce();
+    }
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    if (lane == 0) {
+    if (sums && lane == 0) {
       red[0][wid] = aw.value();
       red[1][wid] = ap.value();
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
+    if (sums && threadIdx.x == 0) {
       double a = 0.0, b = 0.0;
       for (int i = 0; i < NT / 32; ++i) {
         a += red[0][i];

@@ -343,6 +343,10 @@ k_points_lik(const PointParams* __restrict__ pp, PointArrays pa, double* __restr
   const long long il = (long long)blockIdx.x * kPtsNT + threadIdx.x;
   double psi_i = 0.0, kin = 0.0, gsig = 0.0;
   const bool ssig = S.sample_sig != 0;
+  // Psi and dPsi/dd at an intermediate leapfrog point (GM_KICK_DRIFT) are
+  // used only for the kick done here: the energy sums and the stored
+  // gradient are those of the trajectory's end point (and of GM_GRAD)
+  const bool upd = mode != GM_GRAD, drift = mode == GM_KICK_DRIFT;
   if (il < P.pt_n) {
     const long long i = P.pt_off + il;
     const long long nt = pa.ntot;
@@ -350,7 +354,6 @@ k_points_lik(const PointParams* __restrict__ pp, PointArrays pa, double* __restr
     // (the arrays are not restrict-qualified, so the compiler keeps loads
     // after stores in program order): one round of latency for all of them,
     // then the partials at the bucket position
-    const bool upd = mode != GM_GRAD, drift = mode == GM_KICK_DRIFT;
     const int pos = pa.pos[i];
     const double A = pa.lk[i];
     const double d0 = upd ? pa.d[i] : 0.0;
@@ -386,7 +389,7 @@ k_points_lik(const PointParams* __restrict__ pp, PointArrays pa, double* __restr
         const float u = su.hi + su.lo, du = sdu.hi + sdu.lo;
         const float res_v = vo - u;
         const float r2k = res_v * res_v * ik2;
-        psi_i = A + (double)(0.5f * r2k);
+        if (!drift) psi_i = A + (double)(0.5f * r2k);
         rec[pos].r = -res_v * ik2;
         if (ssig) gsig = (double)((float)S.sig * ik2 * (1.0f - r2k));
         gd = (double)(Ap + res_v * (vop - du) * ik2 - 0.5f * r2k * k2p * ik2);
@@ -413,13 +416,13 @@ k_points_lik(const PointParams* __restrict__ pp, PointArrays pa, double* __restr
           du += pdu[k];
         }
         const double res_v = vo - u;
-        psi_i = A + 0.5 * res_v * res_v * ik2;
+        if (!drift) psi_i = A + 0.5 * res_v * res_v * ik2;
         rec[pos].r = (T)(-res_v * ik2);
         if (ssig) gsig = S.sig * ik2 * (1.0 - res_v * res_v * ik2);
         gd = Ap + res_v * (vop - du) * ik2 - 0.5 * res_v * res_v * k2p * ik2 * ik2;
       }
     }
-    pa.gd[i] = gd;
+    if (!drift) pa.gd[i] = gd;
     if (upd) {
       // leapfrog update of the distance (the rest of this evaluation no
       // longer reads d: the plane records were formed from the old one)
@@ -445,9 +448,10 @@ k_points_lik(const PointParams* __restrict__ pp, PointArrays pa, double* __restr
   // the block's sums of Psi_i, of the kinetic term and of dPsi/dsigma_NL in
   // one pass (each a fixed shuffle tree per warp, then the warps in order)
   const bool last = mode == GM_KICK_LAST;
+  if (drift && !ssig) return;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
-    psi_i += __shfl_down_sync(0xffffffffu, psi_i, o);
+    if (!drift) psi_i += __shfl_down_sync(0xffffffffu, psi_i, o);
     if (last) kin += __shfl_down_sync(0xffffffffu, kin, o);
     if (ssig) gsig += __shfl_down_sync(0xffffffffu, gsig, o);
   }
@@ -466,7 +470,7 @@ k_points_lik(const PointParams* __restrict__ pp, PointArrays pa, double* __restr
       sg += red[2][w];
     }
     const long long k = (long long)c * part_stride + blockIdx.x;
-    pts_part[k] = sp;
+    if (!drift) pts_part[k] = sp;
     if (last) kin_part[k] = sk;
     if (ssig) gsig_part[k] = sg;
   }
