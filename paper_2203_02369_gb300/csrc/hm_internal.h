@@ -101,11 +101,14 @@ struct ChainScal {
 
 enum : int { STATUS_DOMAIN = 1, STATUS_NONFINITE = 2 };
 
-// Epilogue modes of the last c2r pass of the gradient.
+// Epilogue modes of the last c2r pass of the gradient.  The energy partials
+// (prior, kinetic, Psi_i) are formed only where they are read: a standalone
+// gradient and the trajectory's end point; the intermediate leapfrog
+// evaluations skip them.
 enum GradMode : int {
   GM_GRAD = 0,        // grad_w = w + g, prior partials (no momentum update)
-  GM_KICK_DRIFT = 1,  // p -= eps*grad; w += eps*p
-  GM_KICK_LAST = 2,   // p -= eps/2*grad; store grad; kinetic partials
+  GM_KICK_DRIFT = 1,  // p -= eps*grad; w += eps*p (no energy partials)
+  GM_KICK_LAST = 2,   // p -= eps/2*grad; store grad; prior and kinetic partials
 };
 
 struct FieldEpi {
@@ -234,10 +237,12 @@ cudaError_t launch_points_prep(int n_chains, int max_pts, const PointParams* pp,
 // kappa, prior) with their derivatives; clears pa.cnt_next
 cudaError_t launch_points_place(int prec, int n_chains, int max_pts, const PointParams* pp,
                                 PointArrays pa, ChainScal* cs, cudaStream_t st);
-// u, du from the plane partials, the velocity term, residuals, distance
-// gradient and Psi partials; then (mode != GM_GRAD) the leapfrog update of
-// p_d and d, the kinetic partials (GM_KICK_LAST) and the bucket counts of
-// the new distances into pa.cnt_next (GM_KICK_DRIFT).
+// u, du from the plane partials, the velocity term, residuals and distance
+// gradient, with the Psi partials and the stored gradient except in
+// GM_KICK_DRIFT; then (mode != GM_GRAD) the leapfrog update of p_d and d,
+// the kinetic partials (GM_KICK_LAST) and the bucket counts of the new
+// distances into pa.cnt_next (GM_KICK_DRIFT).  dPsi/dsigma_NL partials in
+// every mode when sigma_NL is sampled.
 cudaError_t launch_points_lik(int prec, int n_chains, int max_pts, const PointParams* pp, PointArrays pa,
                               double* pts_part, int part_stride, int mode, double* kin_part, ChainScal* cs,
                               double* gsig_part, cudaStream_t st);
